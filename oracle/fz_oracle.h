@@ -1,0 +1,112 @@
+/*
+ * fz_oracle.h -- plain, slow, single-threaded CPU oracle for the FZ-GPU
+ * compression path (Zhang, Tian et al., HPDC'23, arXiv 2304.12557).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check of the package
+ * entry module and the CPU-baseline leg of the benchmark may load this code.
+ * The product path (the CUDA library) neither includes this header nor links
+ * this library, and this oracle includes nothing from the product path.
+ *
+ * What it computes, step by step (paper sections):
+ *   eb derivation ........... Sec. 4.1 (value-range-relative error bound)
+ *   pre-quantization ........ Sec. 2.3 (error-control equation)
+ *   chunked Lorenzo residual  Sec. 2.2-2.3 (independent chunks), Sec. 3.1
+ *   sign-magnitude u16 code . Sec. 3.2
+ *   bitshuffle .............. Sec. 3.3 (32x32 u32 tile, planes written column-wise)
+ *   zero-block flags ........ Sec. 3.4 (Listing 1: 16-byte blocks, bit flags)
+ *   prefix-sum compaction ... Sec. 3.4 (Listing 2: copy block k to PreSum[k]
+ *                             when PreSum[k+1] != PreSum[k])
+ *   decompression ........... Sec. 4.4 (pipeline run backwards)
+ * Readings where the paper is silent are listed in the repository's design
+ * notes and restated at each function below.
+ */
+#ifndef FZ_ORACLE_H
+#define FZ_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes (same numeric values as the product library's, by design of
+ * the format; the oracle defines its own copies) */
+#define FZO_OK            0
+#define FZO_ERR_ARG      -1
+#define FZO_ERR_CAPACITY -2
+#define FZO_ERR_NONFINITE -3
+#define FZO_ERR_EB_RANGE -4
+#define FZO_ERR_CORRUPT  -6
+
+#define FZO_EB_ABS 0
+#define FZO_EB_REL 1
+
+#define FZO_HEADER_BYTES 64
+#define FZO_TILE_CODES 2048
+#define FZO_TILES_PER_CHUNK 4
+#define FZO_QMAX 4194303   /* 2^22 - 1: largest |q| accepted */
+
+/* --- individual steps (exported so the tests can pin each one) --- */
+
+/* Sec. 4.1: absolute bound from the request.  Writes eb_f, ebx2, ebx2_r.
+ * Returns FZO_OK or FZO_ERR_EB_RANGE (bound not a positive normal float). */
+int fzo_derive_eb(int mode, double eb_req, float fmin, float fmax,
+                  float *eb_f, float *ebx2, float *ebx2_r);
+
+/* Sec. 2.3: q = round-half-even(fl32(x * ebx2_r)).  Returns 0 and writes *q
+ * when |q| <= FZO_QMAX, else returns FZO_ERR_EB_RANGE. */
+int fzo_prequant1(float x, float ebx2_r, int32_t *q);
+
+/* chunk shape for ndim (x, y, z extents) */
+void fzo_chunk_shape(int ndim, uint32_t chunk[3]);
+
+/* Chunk-local first-order Lorenzo residual of an integer field q laid out
+ * x-fastest with extents dims[0..2] (unused dims = 1). */
+void fzo_lorenzo(const int32_t *q, const uint32_t dims[3], int ndim,
+                 int32_t *delta);
+
+/* Inverse of fzo_lorenzo by the predictor recurrence q = delta + pred(q). */
+void fzo_lorenzo_inverse(const int32_t *delta, const uint32_t dims[3],
+                         int ndim, int64_t *q);
+
+/* Sec. 3.2 sign-magnitude code; 0x8000 (negative zero) marks an escape. */
+uint16_t fzo_encode(int32_t delta);
+int32_t fzo_decode(uint16_t code);     /* escape decodes to 0 */
+
+/* field coordinates of code position p (0..2047) of tile `tile`; returns 1
+ * when the position lies inside the field, 0 when it is padding */
+int fzo_tile_coord(int ndim, const uint32_t dims[3], uint64_t tile,
+                   uint32_t p, uint32_t xyz[3]);
+uint64_t fzo_num_tiles(int ndim, const uint32_t dims[3]);
+
+/* Sec. 3.3: out[32*b + g] bit t = bit b of in[32*g + t] (1024 words) */
+void fzo_bitshuffle(const uint32_t in[1024], uint32_t out[1024]);
+void fzo_bitunshuffle(const uint32_t out[1024], uint32_t in[1024]);
+
+/* Sec. 3.4 Listing 1: flag of 16-byte block k (words 4k..4k+3) is 1 when any
+ * word is non-zero; flags[j] bit t = flag of block 32*j + t. */
+void fzo_block_flags(const uint32_t out[1024], uint32_t flags[8]);
+
+/* --- whole pipeline --- */
+
+/* Worst-case stream size (every block non-zero, every code an escape). */
+uint64_t fzo_compress_bound(int ndim, const uint32_t dims[3]);
+
+/* Compress x (dims x-fastest).  Returns FZO_OK and writes *out_size, or an
+ * error (with *out_size = required size on FZO_ERR_CAPACITY, else 0). */
+int fzo_compress(const float *x, const uint32_t dims[3], int ndim, int mode,
+                 double eb, uint8_t *out, uint64_t cap, uint64_t *out_size);
+
+/* Decompress a stream into x (capacity in elements). */
+int fzo_decompress(const uint8_t *in, uint64_t in_size, float *x,
+                   uint64_t cap_elems);
+
+/* The reconstruction's plain definition: xr[i] = fl32(float(q_i) * ebx2). */
+int fzo_reconstruct_closed_form(const float *x, uint64_t n, float ebx2_r,
+                                float ebx2, float *xr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
