@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 FZ-GPU compression path.
+
+A step is one pass of the whole path over one field: fz_compress (value-
+range-relative bound: range pass + fused compression kernel) followed by
+fz_decompress, through the C ABI.  The workload is the 512^3 float32
+lognormal Gaussian-random-field (spectrum k^-11/3) at relative bound 1e-3
+(the stand-in for the paper's Nyx 512^3 field, Table 1), resident in HBM
+before timing.  The field (512 MiB) is larger than L2 (129 MB), so
+iterations need no L2 flush.
+
+Printed (rank 0, one JSON line): round-trip GB/s of fp32 input (both
+directions, 2 * 4N bytes per step over the device-timed step), compress and
+decompress GB/s with p50/p99 latency, the dominant kernel's roofline
+fraction against the measured HBM copy bandwidth, the end-to-end figure
+through the host-buffer C-ABI calls, and the CPU oracle timed on a bounded
+sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs its own field (independent problems: weak
+scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("compress+decompress GB/s of fp32 input (round trip, rel eb 1e-3); "
+          "compress/decompress GB/s and p50/p99 latency alongside")
+WORKLOAD = "cosmo3d_512"
+WORKLOAD_DESC = ("512x512x512 float32 lognormal density exp(0.5 g), g a unit-std "
+                 "Gaussian random field with power spectrum k^-11/3 (seed 3); "
+                 "value-range-relative error bound 1e-3")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = (len(xs) - 1) * q
+    lo, hi = int(k), min(int(k) + 1, len(xs) - 1)
+    return xs[lo] + (xs[hi] - xs[lo]) * (k - lo)
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks and throttle)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fz_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9])
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_field(slab=None, size=512):
+    from paper_2304_12557_gb300 import fields
+    x = fields.cosmo3d(size)
+    if slab is not None:
+        x = x[:slab].copy()
+    return x
+
+
+def cpu_oracle_round_trip(x, reps=1):
+    """Time the CPU oracle (as it stands, one thread) compress+decompress."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        st, s = oracle.compress(x, 3, oracle.EB_REL, 1e-3)
+        assert st == oracle.OK
+        st, _ = oracle.decompress(s)
+        assert st == oracle.OK
+    return time.perf_counter() - t0, len(s)
+
+
+def run_reference(args, rank):
+    """The reference arm: the CPU oracle timed on the host cores on a bounded
+    slab of the same workload per step (rank 0 only)."""
+    if rank != 0:
+        return
+    slab = 16
+    x = make_field(slab)
+    n = x.size
+    for _ in range(args.warmup):
+        cpu_oracle_round_trip(x)
+    times = []
+    for _ in range(args.steps):
+        t, _ = cpu_oracle_round_trip(x)
+        times.append(t)
+    ms = 1e3 * sum(times) / len(times)
+    value = 2 * 4 * n / (ms / 1e3) / 1e9
+    sample = f"512x512x{slab} slab of the 512^3 field, compress+decompress per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank, dist):
+    import numpy as np
+    import torch
+
+    import paper_2304_12557_gb300 as fz
+    from paper_2304_12557_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    x_h = make_field(size=args.size)
+    n = x_h.size
+    S = args.size
+    field_bytes = 4 * n
+    x_d = torch.from_numpy(x_h).to(dev)
+    codec = fz.Codec(local_rank)
+    codec.set_profiling(True)
+    stream = torch.cuda.current_stream(dev)
+    cap = fz.stream_min_bytes((S, S, S), 3) + 16 * 256 * (n // 2048 + 64)
+    s_d = torch.empty(cap, dtype=torch.uint8, device=dev)
+    y_d = torch.empty_like(x_d)
+
+    def step(rec):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        st, size = codec.compress_into(x_d, s_d, "rel", 1e-3, 3)
+        kc = codec.kernel_times_ms()
+        e1.record(stream)
+        codec.decompress_into(s_d, y_d, nbytes=size)
+        kd = codec.kernel_times_ms()
+        e2.record(stream)
+        if rec is not None:
+            rec.append((e0, e1, e2, kc, kd, size))
+        return size
+
+    for _ in range(max(args.warmup, 3)):
+        size = step(None)
+    torch.cuda.synchronize()
+    # correctness gate on the timed configuration (stream header sanity and
+    # the pointwise bound on a sample); full parity lives in the tests
+    info = fz.inspect(s_d[:64].cpu().numpy().tobytes())
+    idx = torch.randint(0, n, (1 << 20,), device=dev, generator=torch.Generator(dev).manual_seed(1))
+    err = (x_d.view(-1)[idx] - y_d.view(-1)[idx]).abs().max().item()
+    assert err <= info["eb"] * (1 + 1e-5) + 2 ** -22 * float(x_d.abs().max()), err
+
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ
+                           else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    recs = []
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(recs)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+
+    comp_ms = [a.elapsed_time(b) for a, b, _, _, _, _ in recs]
+    dec_ms = [b.elapsed_time(c) for _, b, c, _, _, _ in recs]
+    k_range = [kc[0] for _, _, _, kc, _, _ in recs]
+    k_comp = [kc[1] for _, _, _, kc, _, _ in recs]
+    k_out = [kc[2] for _, _, _, kc, _, _ in recs]
+    k_dec = [kd[3] for _, _, _, _, kd, _ in recs]
+    size = recs[-1][5]
+    launches = sum(2 + (1 if kc[2] > 0 else 0) + 1 for _, _, _, kc, _, _ in recs)
+
+    # roofline of the dominant kernel (algorithmic bytes per launch)
+    mean = lambda v: sum(v) / len(v)
+    kern = {
+        "compress_kernel": (mean(k_comp), field_bytes + size),
+        "decompress_kernel": (mean(k_dec), size + field_bytes),
+        "range_kernel": (mean(k_range), field_bytes),
+    }
+    dom = max(kern, key=lambda k: kern[k][0])
+    peak, peak_kind = peaks()
+    achieved = kern[dom][1] / (kern[dom][0] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"{peak_kind} hbm_gbs",
+            "algorithmic_bytes_per_launch": kern[dom][1],
+            "kernels": {k: {"ms": v[0], "GB/s": v[1] / (v[0] / 1e3) / 1e9,
+                            "frac": v[1] / (v[0] / 1e3) / 1e9 / peak}
+                        for k, v in kern.items()}}
+
+    # end to end through the host-buffer calls (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(codec, x_h, cap, world, field_bytes, args, torch)
+
+    cpu = None
+    if rank == 0 and world >= 1 and not args.no_cpu_baseline:
+        slab = S // 2
+        t, _ = cpu_oracle_round_trip(x_h[:slab].copy())
+        cpu = {"value": 2 * 4 * x_h[:slab].size / t / 1e9, "unit": "GB/s",
+               "cores": 1, "kind": "oracle",
+               "sample": f"{S}x{S}x{slab} slab (half) of the same field, "
+                         "one compress+decompress, single-threaded C oracle",
+               "seconds": t}
+    value = world * 2 * field_bytes / (ms_step / 1e3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.size == 512 else f"cosmo3d_{args.size}",
+                       "desc": WORKLOAD_DESC.replace("512x512x512", f"{args.size}^3"),
+                       "field_bytes": field_bytes, "eb_mode": "rel", "eb": 1e-3,
+                       "l2": "inputs larger than L2 (512 MiB field), no flush",
+                       "parallelism": f"{world} independent field(s), one per GPU"},
+            "compress_gbs": field_bytes / (statistics.mean(comp_ms) / 1e3) / 1e9,
+            "decompress_gbs": field_bytes / (statistics.mean(dec_ms) / 1e3) / 1e9,
+            "compress_ms": {"p50": percentile(comp_ms, 0.5), "p99": percentile(comp_ms, 0.99)},
+            "decompress_ms": {"p50": percentile(dec_ms, 0.5), "p99": percentile(dec_ms, 0.99)},
+            "kernel_ms": {"range": mean(k_range), "compress": mean(k_comp),
+                          "outliers": mean(k_out), "decompress": mean(k_dec)},
+            "ratio": field_bytes / size, "stream_bytes": size,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    codec.close()
+
+
+
+
+def run_e2e(codec, x_h, cap, world, field_bytes, args, torch):
+    xh_pin = torch.from_numpy(x_h).pin_memory()
+    sh_pin = torch.empty(cap, dtype=torch.uint8).pin_memory()
+    yh_pin = torch.empty(x_h.shape, dtype=torch.float32).pin_memory()
+    xh_np, sh_np, yh_np = xh_pin.numpy(), sh_pin.numpy(), yh_pin.numpy()
+    codec.set_profiling(False)
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        s_np = codec.compress_host(xh_np, "rel", 1e-3, 3, out=sh_np)
+        codec.decompress_host(s_np, out=yh_np)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s_np = codec.compress_host(xh_np, "rel", 1e-3, 3, out=sh_np)
+        codec.decompress_host(s_np, out=yh_np)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world * 2 * field_bytes / e2e_s / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": field_bytes + int(s_np.size),
+           "d2h_bytes_per_step": int(s_np.size) + field_bytes,
+           "ms_per_step": 1e3 * e2e_s}
+    return e2e
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=512,
+                    help="edge of the cubic field (512 = the workload; smaller "
+                         "sizes only for profiling captures)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as d
+        torch.cuda.set_device(local_rank)
+        d.init_process_group("nccl")
+        dist = d
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

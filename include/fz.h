@@ -1,0 +1,158 @@
+/*
+ * fz.h -- C ABI of the GB300 (sm_103a) FZ-GPU compression library.
+ *
+ * Method: FZ-GPU (Zhang, Tian et al., HPDC'23, arXiv 2304.12557).  A float32
+ * field already resident in GPU memory is compressed on the GPU (Sec. 2.4:
+ * data produced on the GPU is compressed from GPU memory, the compressed
+ * bytes are kept in GPU memory or copied out through the CPU, and
+ * decompressed on the GPU when needed):
+ *   1. dual-quantisation (Sec. 2.3, 3.2): q = round(x / 2eb), then the
+ *      chunk-local Lorenzo residual of q, as 16-bit sign-magnitude codes;
+ *   2. bitshuffle of the codes in tiles of 32x32 u32 words (Sec. 3.3);
+ *   3. zero-block encoding: 16-byte blocks, bit flags and prefix-sum
+ *      compaction of the non-zero blocks (Sec. 3.4, Listings 1-2);
+ *   4. the matching decompressor (Sec. 4.4: symmetric pipeline).
+ *
+ * Conventions for every entry point:
+ *  - Plain pointers and sizes only.  "d_" pointers are device pointers on the
+ *    context's device, "h_" pointers are host pointers.  `stream` is a
+ *    cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - The caller owns every input and output buffer.  The library owns only
+ *    the context's scratch (look-back status words, counters, a small
+ *    result block), allocated by fz_create and grown when a larger field
+ *    arrives; no other call allocates device memory.
+ *  - Calls are stream-ordered and return after a synchronisation of
+ *    `stream` (they report sizes and status to the host).  A context serves
+ *    one call at a time: use one context per concurrently used stream.
+ *  - Status: FZ_OK (0) or a negative FZ_ERR_* code.  On error no output size
+ *    is reported (0), except FZ_ERR_CAPACITY, which reports the size needed.
+ *  - Dims are given fastest-varying first: dims[0] = x (contiguous),
+ *    dims[1] = y, dims[2] = z; entries beyond ndim are ignored.  The element
+ *    (x,y,z) lives at index x + dims[0]*(y + dims[1]*z).
+ */
+#ifndef FZ_GB300_H
+#define FZ_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status */
+#define FZ_OK               0
+#define FZ_ERR_ARG         -1  /* bad pointer, ndim, dims, eb, alignment   */
+#define FZ_ERR_CAPACITY    -2  /* output buffer too small                  */
+#define FZ_ERR_NONFINITE   -3  /* NaN or Inf in the input field            */
+#define FZ_ERR_EB_RANGE    -4  /* some |x|/(2eb) rounds beyond 2^22-1, or
+                                  the derived bound is not a normal float   */
+#define FZ_ERR_CORRUPT     -6  /* stream fails a structural check          */
+#define FZ_ERR_TIMEOUT     -7  /* a bounded device wait gave up            */
+#define FZ_ERR_CUDA        -8  /* a CUDA runtime call failed               */
+
+/* error-bound modes (Sec. 4.1) */
+#define FZ_EB_ABS 0   /* eb is the absolute bound                          */
+#define FZ_EB_REL 1   /* eb is relative to the field's value range         */
+
+#define FZ_HEADER_BYTES 64
+
+typedef struct fz_ctx fz_ctx;
+
+/* Stream facts decoded from a 64-byte header (fz_inspect). */
+typedef struct fz_info {
+  int32_t ndim;           /* 1..3                                          */
+  int32_t mode;           /* FZ_EB_ABS or FZ_EB_REL                        */
+  uint64_t dims[3];       /* fastest first; unused dims = 1                */
+  double eb_requested;    /* the eb argument of fz_compress                */
+  float eb;               /* absolute bound in effect (fp32, <= request)   */
+  float ebx2;             /* 2*eb                                          */
+  float ebx2_r;           /* fl(1/(2eb)), the quantiser's multiplier       */
+  float range_min;        /* field min/max in relative mode, else 0        */
+  float range_max;
+  uint64_t n_tiles;       /* 2048-code tiles                               */
+  uint64_t nnz_blocks;    /* non-zero 16-byte blocks in the payload        */
+  uint64_t n_outliers;    /* escaped residuals                             */
+  uint64_t stream_bytes;  /* 64 + 32*n_tiles + 16*nnz_blocks + 8*n_outliers*/
+} fz_info;
+
+/* Create a context on CUDA device `device`: allocates the scratch used by
+ * the prefix-sum look-back and the result block.  Returns FZ_OK,
+ * FZ_ERR_ARG (ctx == NULL) or FZ_ERR_CUDA. */
+int fz_create(fz_ctx **ctx, int device);
+
+/* Release a context and its scratch.  NULL is allowed. */
+void fz_destroy(fz_ctx *ctx);
+
+/* Worst-case stream size in bytes for a field of these dims (every 16-byte
+ * block non-zero and every code escaped).  0 for invalid dims. */
+uint64_t fz_compress_bound(const uint64_t dims[3], int ndim);
+
+/* Size of the stream's fixed part (header + flags): any stream of these dims
+ * is at least this large.  0 for invalid dims. */
+uint64_t fz_stream_min_bytes(const uint64_t dims[3], int ndim);
+
+/* Compress a float32 field (Sec. 3.1 pipeline).
+ *   d_in      device pointer to prod(dims[0..ndim)) floats, x fastest
+ *   dims/ndim field extents, fastest first, 1 <= ndim <= 3; the field must
+ *             have fewer than 2^32 codes after padding to whole tiles
+ *   mode/eb   FZ_EB_ABS: eb is the absolute bound; FZ_EB_REL: eb times the
+ *             field's value range (Sec. 4.1); eb finite and > 0
+ *   d_out     device pointer, 16-byte aligned, out_capacity bytes
+ *   out_size  host pointer; receives the stream size on success
+ * The stream is a pure function of (input bytes, dims, mode, eb).
+ * Errors: FZ_ERR_ARG, FZ_ERR_NONFINITE, FZ_ERR_EB_RANGE, FZ_ERR_CAPACITY
+ * (*out_size = bytes needed), FZ_ERR_TIMEOUT, FZ_ERR_CUDA. */
+int fz_compress(fz_ctx *ctx, const float *d_in, const uint64_t dims[3],
+                int ndim, int mode, double eb, void *d_out,
+                uint64_t out_capacity, uint64_t *out_size, void *stream);
+
+/* Decompress a stream made by fz_compress (Sec. 4.4).
+ *   d_in       device pointer to the stream, 16-byte aligned, in_size bytes
+ *   d_out      device pointer to out_capacity_elems floats
+ * Writes every element of the field; the reconstruction x' satisfies
+ * x' = fl(q * 2eb) with q the pre-quantised value of the original x.
+ * Errors: FZ_ERR_ARG, FZ_ERR_CORRUPT (header, sizes, flags or outlier list
+ * inconsistent), FZ_ERR_CAPACITY, FZ_ERR_TIMEOUT, FZ_ERR_CUDA. */
+int fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_size,
+                  float *d_out, uint64_t out_capacity_elems, void *stream);
+
+/* Host-buffer forms of the two calls: copy h_in to the device, run the
+ * device call on context-owned staging buffers (grown as needed), copy the
+ * result back to h_out.  Same arguments and errors as the device forms. */
+int fz_compress_host(fz_ctx *ctx, const float *h_in, const uint64_t dims[3],
+                     int ndim, int mode, double eb, void *h_out,
+                     uint64_t out_capacity, uint64_t *out_size, void *stream);
+int fz_decompress_host(fz_ctx *ctx, const void *h_in, uint64_t in_size,
+                       float *h_out, uint64_t out_capacity_elems,
+                       void *stream);
+
+/* Decode a host copy of a stream's first n >= 64 bytes.  FZ_OK or
+ * FZ_ERR_CORRUPT / FZ_ERR_ARG. */
+int fz_inspect(const void *h_header, uint64_t n, fz_info *out);
+
+/* Static English message for a status code. */
+const char *fz_strerror(int status);
+
+/* Bound, in nanoseconds, on every device-side wait of this context (the
+ * prefix-sum look-back and the tile-load barrier).  Default 2e9. */
+int fz_set_wait_limit_ns(fz_ctx *ctx, uint64_t ns);
+
+/* Fault injection for tests of the bounded waits: the chunk with this
+ * index skips publishing its look-back aggregate, so its successors' waits
+ * run out and the call returns FZ_ERR_TIMEOUT.  UINT64_MAX disables. */
+int fz_debug_skip_publish(fz_ctx *ctx, uint64_t chunk);
+
+/* Kernel timing for profiling (off by default).  When on, each call
+ * records CUDA events around every kernel it launches, on the call's
+ * stream, and fz_get_kernel_times fills ms[0..3] with the last call's
+ * durations in milliseconds: [0] range pass, [1] compression kernel,
+ * [2] outlier pass, [3] decompression kernel (0 for kernels not run).
+ * Returns FZ_OK, FZ_ERR_ARG or FZ_ERR_CUDA. */
+int fz_set_profiling(fz_ctx *ctx, int on);
+int fz_get_kernel_times(fz_ctx *ctx, double ms[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,292 @@
+"""GB300 (sm_103a) implementation of the FZ-GPU compression path
+(Zhang, Tian et al., HPDC'23, arXiv 2304.12557).
+
+This module is a thin ctypes binding over the C ABI in ``include/fz.h``
+(``_build/libfz_gb300.so``).  It only marshals arguments: every step of
+compression and decompression runs in the library's CUDA kernels.  PyTorch
+is used for device memory and streams.  There is no CPU fallback: if the
+library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = ["Codec", "FZError", "load_library", "library_path", "EB_ABS",
+           "EB_REL", "OK", "ERR_ARG", "ERR_CAPACITY", "ERR_NONFINITE",
+           "ERR_EB_RANGE", "ERR_CORRUPT", "ERR_TIMEOUT", "ERR_CUDA",
+           "compress_bound", "stream_min_bytes", "inspect", "C_API"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libfz_gb300.so")
+
+OK = 0
+ERR_ARG = -1
+ERR_CAPACITY = -2
+ERR_NONFINITE = -3
+ERR_EB_RANGE = -4
+ERR_CORRUPT = -6
+ERR_TIMEOUT = -7
+ERR_CUDA = -8
+EB_ABS = 0
+EB_REL = 1
+
+# every entry point declared in include/fz.h
+C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
+         "fz_compress", "fz_decompress", "fz_compress_host",
+         "fz_decompress_host", "fz_inspect", "fz_strerror",
+         "fz_set_wait_limit_ns", "fz_debug_skip_publish",
+         "fz_set_profiling", "fz_get_kernel_times"]
+
+_lib = None
+_lock = threading.Lock()
+_u64 = ctypes.c_uint64
+_vp = ctypes.c_void_p
+
+
+class FZError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = load_library().fz_strerror(status).decode()
+        super().__init__(f"{what}: {msg} ({status})" if what else msg)
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("dims", _u64 * 3), ("eb_requested", ctypes.c_double),
+                ("eb", ctypes.c_float), ("ebx2", ctypes.c_float),
+                ("ebx2_r", ctypes.c_float), ("range_min", ctypes.c_float),
+                ("range_max", ctypes.c_float), ("n_tiles", _u64),
+                ("nnz_blocks", _u64), ("n_outliers", _u64),
+                ("stream_bytes", _u64)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"CUDA library not built ({p}); run __graft_entry__.build() "
+                "or python -m paper_2304_12557_gb300.build")
+        L = ctypes.CDLL(p)
+        dims_t = ctypes.POINTER(_u64)
+        L.fz_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+        L.fz_destroy.argtypes = [_vp]
+        L.fz_destroy.restype = None
+        L.fz_compress_bound.argtypes = [dims_t, ctypes.c_int]
+        L.fz_compress_bound.restype = _u64
+        L.fz_stream_min_bytes.argtypes = [dims_t, ctypes.c_int]
+        L.fz_stream_min_bytes.restype = _u64
+        L.fz_compress.argtypes = [_vp, _vp, dims_t, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_double, _vp, _u64,
+                                  ctypes.POINTER(_u64), _vp]
+        L.fz_decompress.argtypes = [_vp, _vp, _u64, _vp, _u64, _vp]
+        L.fz_compress_host.argtypes = L.fz_compress.argtypes
+        L.fz_decompress_host.argtypes = L.fz_decompress.argtypes
+        L.fz_inspect.argtypes = [_vp, _u64, ctypes.POINTER(_Info)]
+        L.fz_strerror.argtypes = [ctypes.c_int]
+        L.fz_strerror.restype = ctypes.c_char_p
+        L.fz_set_wait_limit_ns.argtypes = [_vp, _u64]
+        L.fz_debug_skip_publish.argtypes = [_vp, _u64]
+        L.fz_set_profiling.argtypes = [_vp, ctypes.c_int]
+        L.fz_get_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+        _lib = L
+        return L
+
+
+def _dims(dims):
+    d = [int(v) for v in dims] + [1] * (3 - len(dims))
+    return (_u64 * 3)(*d)
+
+
+def compress_bound(dims, ndim: int | None = None) -> int:
+    ndim = ndim or len(dims)
+    return int(load_library().fz_compress_bound(_dims(dims), ndim))
+
+
+def stream_min_bytes(dims, ndim: int | None = None) -> int:
+    ndim = ndim or len(dims)
+    return int(load_library().fz_stream_min_bytes(_dims(dims), ndim))
+
+
+def inspect(header: bytes) -> dict:
+    info = _Info()
+    buf = ctypes.create_string_buffer(bytes(header[:64]), 64)
+    st = load_library().fz_inspect(buf, len(header[:64]), ctypes.byref(info))
+    if st != OK:
+        raise FZError(st, "fz_inspect")
+    return {"ndim": info.ndim, "mode": info.mode,
+            "dims": tuple(int(v) for v in info.dims),
+            "eb_requested": info.eb_requested, "eb": info.eb,
+            "ebx2": info.ebx2, "ebx2_r": info.ebx2_r,
+            "range_min": info.range_min, "range_max": info.range_max,
+            "n_tiles": info.n_tiles, "nnz_blocks": info.nnz_blocks,
+            "n_outliers": info.n_outliers, "stream_bytes": info.stream_bytes}
+
+
+def _mode(mode) -> int:
+    if mode in ("abs", EB_ABS):
+        return EB_ABS
+    if mode in ("rel", EB_REL):
+        return EB_REL
+    raise ValueError(f"mode must be 'abs' or 'rel', got {mode!r}")
+
+
+class Codec:
+    """A library context bound to one CUDA device.
+
+    Fields are torch tensors (float32, contiguous) indexed [z, y, x] with x
+    fastest; their dims go to the library fastest-first.  One Codec serves one
+    stream at a time.
+    """
+
+    def __init__(self, device: int = 0):
+        self._L = load_library()
+        self._ctx = _vp()
+        self.device = device
+        st = self._L.fz_create(ctypes.byref(self._ctx), device)
+        if st != OK:
+            raise FZError(st, "fz_create")
+
+    def close(self):
+        if self._ctx:
+            self._L.fz_destroy(self._ctx)
+            self._ctx = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ options
+    def set_wait_limit_ns(self, ns: int):
+        st = self._L.fz_set_wait_limit_ns(self._ctx, int(ns))
+        if st != OK:
+            raise FZError(st, "fz_set_wait_limit_ns")
+
+    def debug_skip_publish(self, chunk: int | None):
+        v = (1 << 64) - 1 if chunk is None else int(chunk)
+        st = self._L.fz_debug_skip_publish(self._ctx, v)
+        if st != OK:
+            raise FZError(st, "fz_debug_skip_publish")
+
+    def set_profiling(self, on: bool):
+        st = self._L.fz_set_profiling(self._ctx, int(bool(on)))
+        if st != OK:
+            raise FZError(st, "fz_set_profiling")
+
+    def kernel_times_ms(self):
+        """[range, compress, outliers, decompress] of the last call (ms)."""
+        ms = (ctypes.c_double * 4)()
+        st = self._L.fz_get_kernel_times(self._ctx, ms)
+        if st != OK:
+            raise FZError(st, "fz_get_kernel_times")
+        return list(ms)
+
+    # ------------------------------------------------------------ device
+    @staticmethod
+    def _stream(stream):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return _vp(s.cuda_stream)
+
+    def compress_into(self, x, out, mode="rel", eb=1e-3, ndim=None,
+                      stream=None, raise_on_error=True):
+        """Compress device tensor x into the uint8 device tensor out.
+        Returns (status, size)."""
+        ndim = ndim or x.dim()
+        dims = list(x.shape[::-1])[:ndim]
+        assert x.is_cuda and x.is_contiguous(), "x must be a contiguous CUDA tensor"
+        size = _u64(0)
+        st = self._L.fz_compress(self._ctx, _vp(x.data_ptr()), _dims(dims), ndim,
+                                 _mode(mode), float(eb), _vp(out.data_ptr()),
+                                 out.numel() * out.element_size(),
+                                 ctypes.byref(size), self._stream(stream))
+        if st != OK and raise_on_error:
+            raise FZError(st, "fz_compress")
+        return st, int(size.value)
+
+    def compress(self, x, mode="rel", eb=1e-3, ndim=None, stream=None):
+        """Compress a float32 CUDA tensor; returns the stream as a uint8 CUDA
+        tensor (a view of a buffer sized for the worst case)."""
+        import torch
+        ndim = ndim or x.dim()
+        dims = list(x.shape[::-1])[:ndim]
+        cap = stream_min_bytes(dims, ndim) + 16 * 256 * (x.numel() // 2048 + 4)
+        out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+        st, size = self.compress_into(x, out, mode, eb, ndim, stream, False)
+        if st == ERR_CAPACITY:
+            out = torch.empty(size, dtype=torch.uint8, device=x.device)
+            st, size = self.compress_into(x, out, mode, eb, ndim, stream, False)
+        if st != OK:
+            raise FZError(st, "fz_compress")
+        return out[:size]
+
+    def decompress_into(self, stream_t, out, nbytes=None, stream=None,
+                        raise_on_error=True):
+        n = int(nbytes if nbytes is not None else stream_t.numel())
+        st = self._L.fz_decompress(self._ctx, _vp(stream_t.data_ptr()), n,
+                                   _vp(out.data_ptr()), out.numel(),
+                                   self._stream(stream))
+        if st != OK and raise_on_error:
+            raise FZError(st, "fz_decompress")
+        return st
+
+    def decompress(self, stream_t, stream=None):
+        """Decompress a uint8 CUDA tensor; returns a float32 CUDA tensor
+        shaped [z, y, x] (trailing unit dims dropped per the stream's ndim)."""
+        import torch
+        info = inspect(stream_t[:64].cpu().numpy().tobytes())
+        d = info["dims"][: info["ndim"]]
+        out = torch.empty(tuple(d[::-1]), dtype=torch.float32,
+                          device=stream_t.device)
+        self.decompress_into(stream_t, out, stream=stream)
+        return out
+
+    # ------------------------------------------------------------ host
+    def compress_host(self, x_np, mode="rel", eb=1e-3, ndim=None,
+                      capacity=None, stream=None, out=None):
+        """Host-buffer form (copies in and out inside the library).  x_np is a
+        C-contiguous float32 numpy array; returns the stream as bytes."""
+        import numpy as np
+        ndim = ndim or x_np.ndim
+        dims = list(x_np.shape[::-1])[:ndim]
+        cap = capacity or (stream_min_bytes(dims, ndim) +
+                           16 * 256 * (x_np.size // 2048 + 4))
+        buf = out if out is not None else np.empty(cap, np.uint8)
+        size = _u64(0)
+        st = self._L.fz_compress_host(self._ctx, _vp(x_np.ctypes.data),
+                                      _dims(dims), ndim, _mode(mode), float(eb),
+                                      _vp(buf.ctypes.data), buf.size,
+                                      ctypes.byref(size), self._stream(stream))
+        if st != OK:
+            raise FZError(st, "fz_compress_host")
+        return buf[: size.value]
+
+    def decompress_host(self, stream_np, out=None, stream=None):
+        import numpy as np
+        info = inspect(bytes(stream_np[:64]))
+        d = info["dims"][: info["ndim"]]
+        res = out if out is not None else np.empty(tuple(d[::-1]), np.float32)
+        st = self._L.fz_decompress_host(self._ctx, _vp(stream_np.ctypes.data),
+                                        stream_np.size, _vp(res.ctypes.data),
+                                        res.size, self._stream(stream))
+        if st != OK:
+            raise FZError(st, "fz_decompress_host")
+        return res

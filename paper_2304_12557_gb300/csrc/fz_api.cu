@@ -1,0 +1,581 @@
+// fz_api.cu -- the C ABI declared in include/fz.h: context and scratch
+// management, argument checks, TMA descriptors, launches and status mapping.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/fz.h"
+#include "fz_device.cuh"
+#include "fz_kernels.h"
+
+using fz::RangeResult;
+using fz::SetScratch;
+
+struct fz_ctx {
+  int device = 0;
+  int num_sms = 1;
+  int dec_blocks_per_sm = 1;
+  // scratch: two alternating sets (see SetScratch)
+  SetScratch *sets = nullptr;          // [2]
+  uint64_t *status = nullptr;          // [2][cap]
+  uint32_t *out_prefix = nullptr;      // [cap]
+  uint32_t *out_count = nullptr;       // [cap]
+  uint64_t cap = 0;
+  RangeResult *range = nullptr;
+  float2 *partial = nullptr;
+  int range_blocks = 0;
+  SetScratch *h_res = nullptr;         // pinned
+  RangeResult *h_range = nullptr;      // pinned
+  int cur = 0;
+  uint64_t dirty_hi[2] = {0, 0};
+  bool hdr_dirty[2] = {false, false};
+  uint64_t wait_limit_ns = 2000000000ull;
+  uint64_t skip_publish = ~0ull;
+  // host-call staging
+  void *stage_in = nullptr;
+  uint64_t stage_in_cap = 0;
+  void *stage_out = nullptr;
+  uint64_t stage_out_cap = 0;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  // profiling: events around each kernel of the last call
+  bool profiling = false;
+  cudaEvent_t ev[8] = {};
+  bool ev_used[4] = {false, false, false, false};
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+constexpr uint64_t kMaxCodes = 0xFFFFFFFFull;
+
+struct Shape {
+  int ndim;
+  uint64_t d[3];
+  uint64_t ncx, ncy, ncz, n_chunks, n_tiles, n_elems;
+};
+
+bool make_shape(const uint64_t dims[3], int ndim, Shape *s) {
+  if (!dims || ndim < 1 || ndim > 3) return false;
+  s->ndim = ndim;
+  for (int i = 0; i < 3; ++i) {
+    s->d[i] = i < ndim ? dims[i] : 1;
+    if (s->d[i] == 0 || s->d[i] > 0xFFFFFFFFull) return false;
+  }
+  const uint64_t cx = ndim == 1 ? 8192 : (ndim == 2 ? 64 : 32);
+  const uint64_t cy = ndim == 1 ? 1 : (ndim == 2 ? 128 : 32);
+  const uint64_t cz = ndim == 3 ? 8 : 1;
+  s->ncx = (s->d[0] + cx - 1) / cx;
+  s->ncy = (s->d[1] + cy - 1) / cy;
+  s->ncz = (s->d[2] + cz - 1) / cz;
+  // guard the products against overflow before the code-count limit
+  if (s->ncx > kMaxCodes || s->ncy > kMaxCodes || s->ncz > kMaxCodes) return false;
+  const unsigned __int128 nc = (unsigned __int128)s->ncx * s->ncy * s->ncz;
+  if (nc * fz::kChunkCodes > kMaxCodes) return false;
+  s->n_chunks = (uint64_t)nc;
+  s->n_tiles = s->n_chunks * fz::kTilesPerChunk;
+  s->n_elems = s->d[0] * s->d[1] * s->d[2];
+  return true;
+}
+
+void free_scratch(fz_ctx *c) {
+  cudaFree(c->sets); cudaFree(c->status); cudaFree(c->out_prefix);
+  cudaFree(c->out_count);
+  c->sets = nullptr; c->status = nullptr; c->out_prefix = nullptr;
+  c->out_count = nullptr; c->cap = 0;
+}
+
+int ensure_cap(fz_ctx *c, uint64_t n) {
+  if (n <= c->cap && c->sets) return FZ_OK;
+  uint64_t cap = c->cap ? c->cap : 4096;
+  while (cap < n) cap *= 2;
+  free_scratch(c);
+  if (cudaMalloc(&c->sets, 2 * sizeof(SetScratch)) != cudaSuccess ||
+      cudaMalloc(&c->status, 2 * cap * sizeof(uint64_t)) != cudaSuccess ||
+      cudaMalloc(&c->out_prefix, cap * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&c->out_count, cap * sizeof(uint32_t)) != cudaSuccess) {
+    free_scratch(c);
+    return FZ_ERR_CUDA;
+  }
+  if (cudaMemset(c->sets, 0, 2 * sizeof(SetScratch)) != cudaSuccess ||
+      cudaMemset(c->status, 0, 2 * cap * sizeof(uint64_t)) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    free_scratch(c);
+    return FZ_ERR_CUDA;
+  }
+  c->cap = cap;
+  c->dirty_hi[0] = c->dirty_hi[1] = 0;
+  c->hdr_dirty[0] = c->hdr_dirty[1] = false;
+  return FZ_OK;
+}
+
+// make the current set clean before a launch
+int prepare_set(fz_ctx *c, cudaStream_t s) {
+  const int A = c->cur;
+  if (c->dirty_hi[A] > 0) {
+    if (cudaMemsetAsync(c->status + A * c->cap, 0, c->dirty_hi[A] * sizeof(uint64_t), s) !=
+        cudaSuccess)
+      return FZ_ERR_CUDA;
+    c->dirty_hi[A] = 0;
+  }
+  if (c->hdr_dirty[A]) {
+    if (cudaMemsetAsync(c->sets + A, 0, sizeof(SetScratch), s) != cudaSuccess)
+      return FZ_ERR_CUDA;
+    c->hdr_dirty[A] = false;
+  }
+  return FZ_OK;
+}
+
+// after a launch that used `used` status entries of the current set and
+// zeroed the first `zeroed` entries (and the header) of the other set
+void retire_set(fz_ctx *c, uint64_t used, uint64_t zeroed) {
+  const int A = c->cur, B = 1 - A;
+  c->dirty_hi[A] = used;
+  c->hdr_dirty[A] = true;
+  if (c->dirty_hi[B] <= zeroed) c->dirty_hi[B] = 0;
+  c->hdr_dirty[B] = false;
+  c->cur = B;
+}
+
+void mark_all_dirty(fz_ctx *c) {
+  c->dirty_hi[0] = c->dirty_hi[1] = c->cap;
+  c->hdr_dirty[0] = c->hdr_dirty[1] = true;
+}
+
+int range_pass(fz_ctx *c, const float *x, uint64_t n, cudaStream_t s) {
+  const uint64_t want = (n / 4 + 255) / 256;
+  int nb = (int)(want < (uint64_t)c->range_blocks ? (want ? want : 1) : c->range_blocks);
+  fz::launch_range(x, n, c->partial, nb, c->range, s);
+  return cudaGetLastError() == cudaSuccess ? FZ_OK : FZ_ERR_CUDA;
+}
+
+bool encode_tmap(fz_ctx *c, const Shape &sh, const float *x, CUtensorMap *tm) {
+  if (!c->encode) return false;
+  cuuint64_t gdim[3] = {sh.d[0], sh.d[1], sh.d[2]};
+  cuuint64_t gstr[2] = {sh.d[0] * 4, sh.d[0] * sh.d[1] * 4};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r;
+  if (sh.ndim == 3) {
+    cuuint32_t box[3] = {32, 32, 8};
+    r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(x), gdim, gstr,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint32_t box[2] = {32, 128};
+    r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(x), gdim, gstr,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  return r == CUDA_SUCCESS;
+}
+
+int read_set(fz_ctx *c, int set, cudaStream_t s) {
+  if (cudaMemcpyAsync(c->h_res, c->sets + set, sizeof(SetScratch), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  return FZ_OK;
+}
+
+// the input's finiteness decides between NONFINITE and EB_RANGE
+int classify_range_error(fz_ctx *c, const float *x, uint64_t n, cudaStream_t s) {
+  if (range_pass(c, x, n, s) != FZ_OK) return FZ_ERR_CUDA;
+  if (cudaMemcpyAsync(c->h_range, c->range, sizeof(RangeResult), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  return c->h_range->nonfinite ? FZ_ERR_NONFINITE : FZ_ERR_EB_RANGE;
+}
+
+// events k (start) / k+4 (end) bracket kernel k when profiling is on
+void prof_begin(fz_ctx *c, int k, cudaStream_t s) {
+  if (c->profiling) cudaEventRecord(c->ev[k], s);
+}
+void prof_end(fz_ctx *c, int k, cudaStream_t s) {
+  if (c->profiling) {
+    cudaEventRecord(c->ev[k + 4], s);
+    c->ev_used[k] = true;
+  }
+}
+void prof_reset(fz_ctx *c) {
+  for (bool &u : c->ev_used) u = false;
+}
+
+uint32_t rd32(const uint8_t *p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) |
+         ((uint32_t)p[3] << 24);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fz_strerror(int st) {
+  switch (st) {
+    case FZ_OK: return "success";
+    case FZ_ERR_ARG: return "invalid argument";
+    case FZ_ERR_CAPACITY: return "output buffer too small";
+    case FZ_ERR_NONFINITE: return "input contains NaN or Inf";
+    case FZ_ERR_EB_RANGE: return "error bound too small for the data range";
+    case FZ_ERR_CORRUPT: return "corrupt or inconsistent stream";
+    case FZ_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case FZ_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int fz_create(fz_ctx **out, int device) {
+  if (!out) return FZ_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return FZ_ERR_CUDA;
+  DeviceGuard guard(device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  fz_ctx *c = new (std::nothrow) fz_ctx();
+  if (!c) return FZ_ERR_CUDA;
+  c->device = device;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (c->num_sms < 1) c->num_sms = 1;
+  c->dec_blocks_per_sm = fz::decompress_blocks_per_sm();
+  c->range_blocks = c->num_sms * 8;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) == cudaSuccess &&
+      q == cudaDriverEntryPointSuccess)
+    c->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  if (cudaMalloc(&c->range, sizeof(RangeResult)) != cudaSuccess ||
+      cudaMemset(c->range, 0, sizeof(RangeResult)) != cudaSuccess ||
+      cudaMalloc(&c->partial, c->range_blocks * sizeof(float2)) != cudaSuccess ||
+      cudaMallocHost(&c->h_res, sizeof(SetScratch)) != cudaSuccess ||
+      cudaMallocHost(&c->h_range, sizeof(RangeResult)) != cudaSuccess ||
+      ensure_cap(c, 4096) != FZ_OK) {
+    fz_destroy(c);
+    return FZ_ERR_CUDA;
+  }
+  for (cudaEvent_t &e : c->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      fz_destroy(c);
+      return FZ_ERR_CUDA;
+    }
+  }
+  *out = c;
+  return FZ_OK;
+}
+
+void fz_destroy(fz_ctx *c) {
+  if (!c) return;
+  DeviceGuard guard(c->device);
+  free_scratch(c);
+  cudaFree(c->range);
+  cudaFree(c->partial);
+  cudaFree(c->stage_in);
+  cudaFree(c->stage_out);
+  if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->h_range) cudaFreeHost(c->h_range);
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+uint64_t fz_stream_min_bytes(const uint64_t dims[3], int ndim) {
+  Shape sh;
+  if (!make_shape(dims, ndim, &sh)) return 0;
+  return 64 + 32 * sh.n_tiles;
+}
+
+uint64_t fz_compress_bound(const uint64_t dims[3], int ndim) {
+  Shape sh;
+  if (!make_shape(dims, ndim, &sh)) return 0;
+  return 64 + 32 * sh.n_tiles + 16 * 256 * sh.n_tiles + 8 * (uint64_t)fz::kTileCodes * sh.n_tiles;
+}
+
+int fz_set_wait_limit_ns(fz_ctx *c, uint64_t ns) {
+  if (!c || ns == 0) return FZ_ERR_ARG;
+  c->wait_limit_ns = ns;
+  return FZ_OK;
+}
+
+int fz_set_profiling(fz_ctx *c, int on) {
+  if (!c) return FZ_ERR_ARG;
+  c->profiling = on != 0;
+  prof_reset(c);
+  return FZ_OK;
+}
+
+int fz_get_kernel_times(fz_ctx *c, double ms[4]) {
+  if (!c || !ms) return FZ_ERR_ARG;
+  DeviceGuard guard(c->device);
+  for (int k = 0; k < 4; ++k) {
+    ms[k] = 0.0;
+    if (!c->ev_used[k]) continue;
+    float t = 0.f;
+    if (cudaEventSynchronize(c->ev[k + 4]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 4]) != cudaSuccess)
+      return FZ_ERR_CUDA;
+    ms[k] = t;
+  }
+  return FZ_OK;
+}
+
+int fz_debug_skip_publish(fz_ctx *c, uint64_t chunk) {
+  if (!c) return FZ_ERR_ARG;
+  c->skip_publish = chunk;
+  return FZ_OK;
+}
+
+int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, int mode,
+                double eb, void *d_out, uint64_t cap, uint64_t *out_size, void *stream) {
+  if (out_size) *out_size = 0;
+  Shape sh;
+  if (!c || !d_in || !d_out || !out_size || !make_shape(dims, ndim, &sh)) return FZ_ERR_ARG;
+  if (mode != FZ_EB_ABS && mode != FZ_EB_REL) return FZ_ERR_ARG;
+  if (!(eb > 0.0) || !std::isfinite(eb)) return FZ_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 15u) || (reinterpret_cast<uintptr_t>(d_in) & 3u))
+    return FZ_ERR_ARG;
+  const uint64_t min_bytes = 64 + 32 * sh.n_tiles;
+  if (cap < min_bytes) {
+    *out_size = min_bytes;
+    return FZ_ERR_CAPACITY;
+  }
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = ensure_cap(c, sh.n_chunks);
+  if (st) return st;
+  if ((st = prepare_set(c, s))) return st;
+  prof_reset(c);
+  if (mode == FZ_EB_REL) {
+    prof_begin(c, 0, s);
+    if ((st = range_pass(c, d_in, sh.n_elems, s))) return st;
+    prof_end(c, 0, s);
+  }
+
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  const bool tma = sh.ndim >= 2 && (sh.d[0] % 4 == 0) &&
+                   (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0 && encode_tmap(c, sh, d_in, &tm);
+  const int A = c->cur;
+  fz::CompressArgs a{};
+  a.x = d_in;
+  for (int i = 0; i < 3; ++i) a.dims[i] = sh.d[i];
+  a.ncx = (uint32_t)sh.ncx;
+  a.ncy = (uint32_t)sh.ncy;
+  a.n_chunks = sh.n_chunks;
+  a.mode = mode;
+  a.eb_req = eb;
+  a.range = c->range;
+  a.set_cur = c->sets + A;
+  a.set_next = c->sets + (1 - A);
+  a.status_cur = c->status + A * c->cap;
+  a.status_next = c->status + (1 - A) * c->cap;
+  a.chunk_out_prefix = c->out_prefix;
+  a.chunk_out_count = c->out_count;
+  a.out = static_cast<uint8_t *>(d_out);
+  a.out_capacity = cap;
+  a.wait_limit_ns = c->wait_limit_ns;
+  a.skip_publish_chunk = c->skip_publish;
+  prof_begin(c, 1, s);
+  if (fz::launch_compress(sh.ndim, tma, a, tm, s) != cudaSuccess) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  prof_end(c, 1, s);
+  retire_set(c, sh.n_chunks, sh.n_chunks);
+  if ((st = read_set(c, A, s))) {
+    mark_all_dirty(c);
+    return st;
+  }
+  const SetScratch r = *c->h_res;
+  if (r.err & fz::kErrNonFinite) return FZ_ERR_NONFINITE;
+  if (r.err & (fz::kErrEbParam | fz::kErrRange)) {
+    if (mode == FZ_EB_ABS) return classify_range_error(c, d_in, sh.n_elems, s);
+    return FZ_ERR_EB_RANGE;
+  }
+  if (r.err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
+  const uint64_t total = min_bytes + 16 * r.nnz + 8 * r.nout;
+  if ((r.err & fz::kErrCapacity) || total > cap) {
+    *out_size = total;
+    return FZ_ERR_CAPACITY;
+  }
+  if (r.nout > 0) {
+    // rare path: write the escaped residuals behind the payload
+    if ((st = prepare_set(c, s))) return st;
+    a.set_cur = c->sets + c->cur;
+    prof_begin(c, 2, s);
+    if (fz::launch_outliers(sh.ndim, tma, a, tm, min_bytes + 16 * r.nnz, s) != cudaSuccess) {
+      mark_all_dirty(c);
+      return FZ_ERR_CUDA;
+    }
+    prof_end(c, 2, s);
+    const int B = c->cur;
+    c->hdr_dirty[B] = true;
+    if ((st = read_set(c, B, s))) return st;
+    if (c->h_res->err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
+    if (c->h_res->err & fz::kErrCapacity) {
+      *out_size = total;
+      return FZ_ERR_CAPACITY;
+    }
+  }
+  *out_size = total;
+  return FZ_OK;
+}
+
+int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
+                  uint64_t cap_elems, void *stream) {
+  if (!c || !d_in || !d_out) return FZ_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_in) & 15u) || (reinterpret_cast<uintptr_t>(d_out) & 3u))
+    return FZ_ERR_ARG;
+  if (in_size < 64) return FZ_ERR_CORRUPT;
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // every chunk carries 128 bytes of flags, which bounds the chunk count
+  uint64_t bound = (in_size - 64) / 128;
+  const uint64_t max_chunks = kMaxCodes / fz::kChunkCodes + 1;
+  if (bound > max_chunks) bound = max_chunks;
+  int st = ensure_cap(c, bound ? bound : 1);
+  if (st) return st;
+  if ((st = prepare_set(c, s))) return st;
+  const int A = c->cur;
+  fz::DecompressArgs a{};
+  a.in = static_cast<const uint8_t *>(d_in);
+  a.in_size = in_size;
+  a.out = d_out;
+  a.out_cap_elems = cap_elems;
+  a.set_cur = c->sets + A;
+  a.set_next = c->sets + (1 - A);
+  a.status_cur = c->status + A * c->cap;
+  a.status_next = c->status + (1 - A) * c->cap;
+  a.status_cap = c->cap;
+  a.wait_limit_ns = c->wait_limit_ns;
+  a.skip_publish_chunk = c->skip_publish;
+  const int grid = c->num_sms * c->dec_blocks_per_sm;
+  prof_reset(c);
+  prof_begin(c, 3, s);
+  if (fz::launch_decompress(a, grid, s) != cudaSuccess) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  prof_end(c, 3, s);
+  if ((st = read_set(c, A, s))) {
+    mark_all_dirty(c);
+    return st;
+  }
+  const SetScratch r = *c->h_res;
+  retire_set(c, r.n_chunks ? r.n_chunks : c->cap, r.n_chunks);
+  // a timed-out wait leaves later offsets unreliable, so it takes precedence
+  if (r.err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
+  if (r.err & fz::kErrCorrupt) return FZ_ERR_CORRUPT;
+  if (r.err & fz::kErrCapacity) return FZ_ERR_CAPACITY;
+  if (r.nout != r.hdr_nout) return FZ_ERR_CORRUPT;
+  return FZ_OK;
+}
+
+static int grow(void **p, uint64_t *cap, uint64_t need) {
+  if (need <= *cap && *p) return FZ_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, need ? need : 16) != cudaSuccess) return FZ_ERR_CUDA;
+  *cap = need;
+  return FZ_OK;
+}
+
+int fz_compress_host(fz_ctx *c, const float *h_in, const uint64_t dims[3], int ndim, int mode,
+                     double eb, void *h_out, uint64_t cap, uint64_t *out_size, void *stream) {
+  if (out_size) *out_size = 0;
+  Shape sh;
+  if (!c || !h_in || !h_out || !out_size || !make_shape(dims, ndim, &sh)) return FZ_ERR_ARG;
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st;
+  if ((st = grow(&c->stage_in, &c->stage_in_cap, sh.n_elems * 4))) return st;
+  uint64_t dcap = cap;
+  const uint64_t bound = fz_compress_bound(dims, ndim);
+  if (dcap > bound) dcap = bound;
+  if ((st = grow(&c->stage_out, &c->stage_out_cap, dcap))) return st;
+  if (cudaMemcpyAsync(c->stage_in, h_in, sh.n_elems * 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  uint64_t size = 0;
+  st = fz_compress(c, static_cast<const float *>(c->stage_in), dims, ndim, mode, eb, c->stage_out,
+                   dcap, &size, stream);
+  *out_size = size;
+  if (st) return st;
+  if (cudaMemcpyAsync(h_out, c->stage_out, size, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  return FZ_OK;
+}
+
+int fz_decompress_host(fz_ctx *c, const void *h_in, uint64_t in_size, float *h_out,
+                       uint64_t cap_elems, void *stream) {
+  if (!c || !h_in || !h_out) return FZ_ERR_ARG;
+  fz_info info;
+  int st = fz_inspect(h_in, in_size, &info);
+  if (st) return st;
+  if (info.stream_bytes != in_size) return FZ_ERR_CORRUPT;
+  const uint64_t n = info.dims[0] * info.dims[1] * info.dims[2];
+  if (cap_elems < n) return FZ_ERR_CAPACITY;
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((st = grow(&c->stage_in, &c->stage_in_cap, in_size))) return st;
+  if ((st = grow(&c->stage_out, &c->stage_out_cap, n * 4))) return st;
+  if (cudaMemcpyAsync(c->stage_in, h_in, in_size, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  st = fz_decompress(c, c->stage_in, in_size, static_cast<float *>(c->stage_out), n, stream);
+  if (st) return st;
+  if (cudaMemcpyAsync(h_out, c->stage_out, n * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  return FZ_OK;
+}
+
+int fz_inspect(const void *hdr, uint64_t n, fz_info *out) {
+  if (!hdr || !out) return FZ_ERR_ARG;
+  if (n < 64) return FZ_ERR_CORRUPT;
+  const uint8_t *p = static_cast<const uint8_t *>(hdr);
+  if (p[0] != 'F' || p[1] != 'Z' || p[2] != 'G' || p[3] != '1' || p[4] != 1 || p[7] != 0)
+    return FZ_ERR_CORRUPT;
+  const int ndim = p[5], mode = p[6];
+  if (ndim < 1 || ndim > 3 || mode > 1) return FZ_ERR_CORRUPT;
+  uint64_t dims[3] = {rd32(p + 8), rd32(p + 12), rd32(p + 16)};
+  for (int i = ndim; i < 3; ++i)
+    if (dims[i] != 1) return FZ_ERR_CORRUPT;
+  Shape sh;
+  if (!make_shape(dims, ndim, &sh)) return FZ_ERR_CORRUPT;
+  if (rd32(p + 20) != sh.n_tiles) return FZ_ERR_CORRUPT;
+  out->ndim = ndim;
+  out->mode = mode;
+  for (int i = 0; i < 3; ++i) out->dims[i] = dims[i];
+  std::memcpy(&out->eb_requested, p + 24, 8);
+  std::memcpy(&out->eb, p + 32, 4);
+  std::memcpy(&out->ebx2, p + 36, 4);
+  std::memcpy(&out->ebx2_r, p + 40, 4);
+  out->nnz_blocks = rd32(p + 44);
+  out->n_outliers = rd32(p + 48);
+  std::memcpy(&out->range_min, p + 52, 4);
+  std::memcpy(&out->range_max, p + 56, 4);
+  out->n_tiles = sh.n_tiles;
+  out->stream_bytes = 64 + 32 * sh.n_tiles + 16 * out->nnz_blocks + 8 * out->n_outliers;
+  return FZ_OK;
+}
+
+}  // extern "C"

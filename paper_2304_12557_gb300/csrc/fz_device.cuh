@@ -1,0 +1,358 @@
+// fz_device.cuh -- device-side building blocks shared by the GB300 kernels.
+//
+// Format geometry (a chunk = the Lorenzo independence unit of Sec. 2.3 =
+// 4 tiles of 2048 codes; a tile = one 32x32 u32 bitshuffle unit of Sec. 3.3;
+// a brick = one 64-code group of a tile, owned by one thread):
+//   ndim  chunk            tile (march axis)   brick        bricks/tile
+//   1     8192             2048 (x)            64           32 x 1
+//   2     64 x 128         64 x 32 (y)         8 x 8        8 x 4
+//   3     32 x 32 x 8      32 x 32 x 2 (z)     8 x 4 x 2    4 x 8
+// group g = bx + NBX * by; codes x-fastest inside a brick.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fz {
+
+constexpr int kTileCodes = 2048;
+constexpr int kTilesPerChunk = 4;
+constexpr int kChunkCodes = kTileCodes * kTilesPerChunk;
+constexpr int kThreads = 128;            // 4 warps, warp t = tile t
+constexpr int kBoxBytes = kChunkCodes * 4;   // one chunk of fp32
+
+// quantiser constants.  fl(v + 1.5*2^23) rounds v to the nearest integer
+// (ties to even) in the low mantissa bits whenever |v| <= 2^22; the float's
+// bit pattern minus 0x4B000001 is then q + 2^22 - 1, which lies in
+// [0, 2^23 - 2] exactly when |q| <= 2^22 - 1 (the stream's limit).
+constexpr float kRoundMagic = 12582912.0f;     // 1.5 * 2^23
+constexpr uint32_t kMagicBits = 0x4B400000u;   // bits of kRoundMagic
+constexpr uint32_t kBiasBits = 0x4B000001u;
+constexpr int32_t kPadBiased = 0x3FFFFF;       // biased form of q = 0
+constexpr uint32_t kBiasedMax = 0x7FFFFEu;     // biased form of q = 2^22-1
+
+// error bits gathered in device memory, mapped to FZ_ERR_* on the host
+constexpr uint32_t kErrRange = 1u;     // |q| too large or non-finite input
+constexpr uint32_t kErrEbParam = 2u;   // derived bound not representable
+constexpr uint32_t kErrTimeout = 4u;   // bounded wait ran out
+constexpr uint32_t kErrCapacity = 8u;  // payload would pass out_capacity
+constexpr uint32_t kErrCorrupt = 16u;  // decompressor: inconsistent stream
+constexpr uint32_t kErrNonFinite = 32u;
+
+// look-back status word: [63:62] flag, [61:32] blocks, [31:0] outliers
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagInc = 2ull << 62;
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+
+template <int NDIM> struct Geo;
+template <> struct Geo<1> {
+  static constexpr int BX = 64, BY = 1, BZ = 1, NBX = 32, NBY = 1;
+  static constexpr int CX = 8192, CY = 1, CZ = 1;
+};
+template <> struct Geo<2> {
+  static constexpr int BX = 8, BY = 8, BZ = 1, NBX = 8, NBY = 4;
+  static constexpr int CX = 64, CY = 128, CZ = 1;
+};
+template <> struct Geo<3> {
+  static constexpr int BX = 8, BY = 4, BZ = 2, NBX = 4, NBY = 8;
+  static constexpr int CX = 32, CY = 32, CZ = 8;
+};
+
+// The 64-byte stream header, little-endian (matches the host's reader).
+struct __align__(16) StreamHeader {
+  uint8_t magic[4];        // "FZG1"
+  uint8_t version, ndim, mode, reserved0;
+  uint32_t dims[3];
+  uint32_t n_tiles;
+  double eb_requested;
+  float eb, ebx2, ebx2_r;
+  uint32_t nnz_blocks, n_outliers;
+  float range_min, range_max;
+  uint32_t reserved1;
+};
+static_assert(sizeof(StreamHeader) == 64, "header is 64 bytes");
+
+// Per-call scratch that alternates between two sets so that a call can
+// zero the set the next call will use (no memset launch per call).
+struct SetScratch {
+  uint32_t ticket;      // dynamic chunk ticket
+  uint32_t err;         // error bits
+  uint64_t nnz;         // compressor: total blocks; decompressor: header's
+  uint64_t nout;        // compressor: total outliers; decompressor: matched
+  uint64_t n_chunks;    // decompressor: chunks found in the stream header
+  uint32_t hdr_nout;    // decompressor: the header's outlier count
+  uint32_t pad[7];
+};
+static_assert(sizeof(SetScratch) == 64, "scratch block is 64 bytes");
+
+struct RangeResult {
+  float fmin, fmax;
+  uint32_t nonfinite;
+  uint32_t counter;     // last-block detection, self-resetting
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v)
+               : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
+               : "=l"(v)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile(
+      "mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Returns false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar,
+                                                  uint32_t parity,
+                                                  uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = global_timer();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 63u && global_timer() - t0 > limit_ns) return false;
+  }
+}
+
+// TMA tile loads (plain, no multicast) completing on an mbarrier.
+__device__ __forceinline__ void tma_load_3d(void *smem_dst, const void *tmap,
+                                            uint64_t *bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::"
+      "complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const void *tmap,
+                                            uint64_t *bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::"
+      "complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bulk copy shared -> global (both 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_store(void *gdst, const void *smem_src,
+                                           uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::
+                   "l"(gdst),
+               "r"(smem_u32(smem_src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 128-byte swizzle of a box row of 32 floats: 16-byte chunk c of row r sits
+// at chunk position c ^ (r % 8) (the TMA SWIZZLE_128B layout for a
+// 1024-byte aligned box).
+__device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t chunk) {
+  return row * 128u + ((chunk ^ (row & 7u)) << 4);
+}
+
+// ------------------------------------------------------------ warp helpers
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Decoupled look-back (single-pass prefix sum over chunks in ticket order).
+// Executed by one full warp.  `agg` is this chunk's (blocks<<32 | outliers)
+// and the return value the exclusive prefix over chunks < c.  Every wait is
+// bounded by limit_ns; on time-out the error bit is raised and the prefix
+// found so far is used (all later writes stay bounds-checked).
+__device__ __forceinline__ uint64_t lookback(uint64_t *status, uint64_t c,
+                                             uint64_t agg, bool publish,
+                                             uint32_t *err, uint64_t limit_ns) {
+  const int lane = threadIdx.x & 31;
+  if (c == 0) {
+    if (lane == 0 && publish) st_release(&status[0], kFlagInc | agg);
+    return 0;
+  }
+  if (lane == 0 && publish) st_release(&status[c], kFlagAgg | agg);
+  uint64_t excl = 0;
+  int64_t j = (int64_t)c - 1;
+  uint64_t t0 = global_timer();
+  bool timed_out = false;
+  while (true) {
+    int64_t idx = j - lane;
+    uint64_t v = idx >= 0 ? ld_acquire(&status[idx]) : kFlagInc;
+    uint32_t it = 0;
+    while (true) {                        // every exit is warp-uniform
+      const bool pending = (v >> 62) == 0;
+      if (!__any_sync(0xffffffffu, pending)) break;
+      if (pending) {
+        __nanosleep(32);
+        v = ld_acquire(&status[idx]);
+      }
+      if ((++it & 31u) == 0) {
+        const bool late = global_timer() - t0 > limit_ns;
+        if (__any_sync(0xffffffffu, late)) {
+          timed_out = true;
+          break;
+        }
+      }
+    }
+    if (timed_out) break;
+    uint32_t pmask = __ballot_sync(0xffffffffu, (v >> 62) == 2);
+    if (pmask) {
+      int p = __ffs(pmask) - 1;        // nearest predecessor with a prefix
+      excl += warp_sum_u64(lane <= p ? (v & kValMask) : 0);
+      break;
+    }
+    excl += warp_sum_u64(v & kValMask);
+    j -= 32;
+  }
+  if (timed_out && lane == 0) atomicOr(err, kErrTimeout);
+  if (lane == 0 && publish) st_release(&status[c], kFlagInc | (excl + agg));
+  return excl;
+}
+
+// ------------------------------------------------------------ bit transpose
+// byte select of the pair (x, y): result byte i = byte (sel >> 4i) & 7 of
+// the 8-byte value y:x (PRMT on the device; a plain loop on the host, where
+// the transpose is unit-tested)
+__host__ __device__ __forceinline__ uint32_t byte_perm(uint32_t x, uint32_t y,
+                                                       uint32_t sel) {
+#ifdef __CUDA_ARCH__
+  return __byte_perm(x, y, sel);
+#else
+  const uint64_t v = (uint64_t)y << 32 | x;
+  uint32_t r = 0;
+  for (int i = 0; i < 4; ++i)
+    r |= (uint32_t)((v >> (8 * ((sel >> (4 * i)) & 7u))) & 0xFFu) << (8 * i);
+  return r;
+#endif
+}
+
+// In-register 32x32 bit-matrix transpose (block-swap recursion, LSB-first):
+// afterwards bit t of a[b] equals bit b of the input a[t].  The 16- and
+// 8-bit stages move whole bytes and use byte permutes.
+__host__ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    uint32_t x = a[k], y = a[k + 16];
+    a[k] = byte_perm(x, y, 0x5410);
+    a[k + 16] = byte_perm(x, y, 0x7632);
+  }
+#pragma unroll
+  for (int k0 = 0; k0 < 32; k0 += 16) {
+#pragma unroll
+    for (int k = k0; k < k0 + 8; ++k) {
+      uint32_t x = a[k], y = a[k + 8];
+      a[k] = byte_perm(x, y, 0x6240);
+      a[k + 8] = byte_perm(x, y, 0x7351);
+    }
+  }
+#pragma unroll
+  for (int k0 = 0; k0 < 32; k0 += 8) {
+#pragma unroll
+    for (int k = k0; k < k0 + 4; ++k) {
+      uint32_t x = a[k], y = a[k + 4];
+      a[k] = (x & 0x0F0F0F0Fu) | ((y << 4) & 0xF0F0F0F0u);
+      a[k + 4] = ((x >> 4) & 0x0F0F0F0Fu) | (y & 0xF0F0F0F0u);
+    }
+  }
+#pragma unroll
+  for (int k0 = 0; k0 < 32; k0 += 4) {
+#pragma unroll
+    for (int k = k0; k < k0 + 2; ++k) {
+      uint32_t x = a[k], y = a[k + 2];
+      a[k] = (x & 0x33333333u) | ((y << 2) & 0xCCCCCCCCu);
+      a[k + 2] = ((x >> 2) & 0x33333333u) | (y & 0xCCCCCCCCu);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 32; k += 2) {
+    uint32_t x = a[k], y = a[k + 1];
+    a[k] = (x & 0x55555555u) | ((y << 1) & 0xAAAAAAAAu);
+    a[k + 1] = ((x >> 1) & 0x55555555u) | (y & 0xAAAAAAAAu);
+  }
+}
+
+// ------------------------------------------------------------ eb derivation
+// Sec. 4.1: the absolute bound from the request (relative bounds scale the
+// value range).  Same rules as the stream format: double arithmetic, the
+// fp32 bound rounded toward zero, 1/(2eb) rounded to fp32 from double.
+struct EbParams {
+  float eb, ebx2, ebx2_r;
+  bool ok;
+};
+
+__device__ __forceinline__ EbParams derive_eb(int mode, double eb_req,
+                                              float fmin, float fmax) {
+  EbParams p{0.f, 0.f, 0.f, false};
+  double eb_d = eb_req;
+  if (mode == 1) {
+    double range = __dsub_rn((double)fmax, (double)fmin);
+    if (range == 0.0) {
+      range = fabs((double)fmax);
+      if (range == 0.0) range = 1.0;
+    }
+    eb_d = __dmul_rn(eb_req, range);
+  }
+  if (!(eb_d > 0.0) || !isfinite(eb_d)) return p;
+  float e = __double2float_rz(eb_d);
+  if (!(e >= 1.17549435e-38f)) return p;
+  float e2 = __fmul_rn(2.0f, e);
+  if (isinf(e2)) return p;
+  p.eb = e;
+  p.ebx2 = e2;
+  p.ebx2_r = __double2float_rn(__ddiv_rn(1.0, (double)e2));
+  p.ok = true;
+  return p;
+}
+
+}  // namespace fz

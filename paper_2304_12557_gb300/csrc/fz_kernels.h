@@ -1,0 +1,54 @@
+// fz_kernels.h -- launch interface between the C ABI (fz_api.cu) and the
+// kernels (fz_compress.cu, fz_decompress.cu).  Internal to the library.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace fz {
+
+struct SetScratch;
+struct RangeResult;
+
+struct CompressArgs {
+  const float *x;
+  uint64_t dims[3];            // unused dims = 1
+  uint32_t ncx, ncy;           // chunk grid (x, y)
+  uint64_t n_chunks;
+  int mode;                    // 0 abs, 1 rel
+  double eb_req;
+  const RangeResult *range;    // relative mode: min/max/non-finite
+  SetScratch *set_cur, *set_next;
+  uint64_t *status_cur, *status_next;
+  uint32_t *chunk_out_prefix;  // per chunk: exclusive outlier prefix
+  uint32_t *chunk_out_count;   // per chunk: outliers
+  uint8_t *out;
+  uint64_t out_capacity;
+  uint64_t wait_limit_ns;
+  uint64_t skip_publish_chunk; // fault injection for timeout tests
+};
+
+struct DecompressArgs {
+  const uint8_t *in;
+  uint64_t in_size;
+  float *out;
+  uint64_t out_cap_elems;
+  SetScratch *set_cur, *set_next;
+  uint64_t *status_cur, *status_next;
+  uint64_t status_cap;         // entries available in the status arrays
+  uint64_t wait_limit_ns;
+  uint64_t skip_publish_chunk;
+};
+
+void launch_range(const float *x, uint64_t n, float2 *partial, int nblocks,
+                  RangeResult *res, cudaStream_t s);
+size_t compress_smem_bytes();
+cudaError_t launch_compress(int ndim, bool tma, const CompressArgs &a,
+                            const CUtensorMap &tm, cudaStream_t s);
+cudaError_t launch_outliers(int ndim, bool tma, const CompressArgs &a,
+                            const CUtensorMap &tm, uint64_t out_section,
+                            cudaStream_t s);
+cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s);
+int decompress_blocks_per_sm();
+
+}  // namespace fz

@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Streams must be byte-identical to the oracle's and reconstructions
+bit-identical (integer codes and compressed bytes are exact; the only
+floating point is the fp32 quantiser multiply and the fp32 dequantiser
+multiply, which both sides perform identically).  Inputs are the seeded
+synthetic fields of paper_2304_12557_gb300.fields at the workloads' full
+sizes, plus small ragged shapes, outliers, errors and corrupt streams.
+"""
+import struct
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2304_12557_gb300 as fz
+from golden_io import expected_bytes, load
+from paper_2304_12557_gb300 import fields
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = ["g1_1d_basic.txt", "g2_1d_escape.txt", "g3_2d_basic.txt",
+          "g4_3d_rel.txt"]
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    return t
+
+
+@pytest.fixture(scope="module")
+def codec(torch):
+    from paper_2304_12557_gb300 import build
+    build.build()
+    c = fz.Codec(0)
+    yield c
+    c.close()
+
+
+def gpu_compress(codec, torch, x, ndim, mode, eb, offset=0):
+    xt = torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    if offset:
+        # an input that starts off a 16-byte boundary (generic load path)
+        buf = torch.empty(x.size + offset, dtype=torch.float32, device="cuda")
+        buf[offset:] = xt.reshape(-1)
+        xt = buf[offset:].view(x.shape)
+    s = codec.compress(xt, mode=mode, eb=eb, ndim=ndim)
+    torch.cuda.synchronize()
+    return s.cpu().numpy().tobytes()
+
+
+def gpu_decompress(codec, torch, s):
+    st = torch.from_numpy(np.frombuffer(s, np.uint8).copy()).cuda()
+    y = codec.decompress(st)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().ravel()
+
+
+def check_parity(codec, torch, x, ndim, mode, eb, offset=0):
+    ost, ostream = oracle.compress(x, ndim, mode, eb)
+    assert ost == oracle.OK
+    g = gpu_compress(codec, torch, x, ndim, mode, eb, offset)
+    assert len(g) == len(ostream)
+    if g != ostream:
+        a = np.frombuffer(g, np.uint8)
+        b = np.frombuffer(ostream, np.uint8)
+        bad = np.flatnonzero(a != b)
+        raise AssertionError(f"stream differs at {bad.size} bytes, first {bad[:8]}")
+    xr_gpu = gpu_decompress(codec, torch, g)
+    st, xr_or = oracle.decompress(ostream)
+    assert st == oracle.OK
+    np.testing.assert_array_equal(xr_gpu.view(np.uint32), xr_or.view(np.uint32))
+    return g, xr_gpu
+
+
+# ------------------------------------------------------------ hand-worked
+@pytest.mark.parametrize("name", GOLDEN)
+def test_golden_streams_on_gpu(codec, torch, name):
+    rec = load(name)
+    g = gpu_compress(codec, torch, rec["x"], rec["ndim"], rec["mode"], rec["eb"])
+    assert g == expected_bytes(rec)
+    np.testing.assert_array_equal(gpu_decompress(codec, torch, g), rec["x"].ravel())
+
+
+# ------------------------------------------------------------ small ragged
+@pytest.mark.parametrize("shape,ndim", fields.small_cases())
+@pytest.mark.parametrize("mode,eb", [(fz.EB_REL, 1e-2), (fz.EB_REL, 1e-4),
+                                     (fz.EB_ABS, 0.37)])
+def test_small_shapes(codec, torch, shape, ndim, mode, eb):
+    if min(shape) > 2:
+        x = fields.grf(shape, -3.0, 17).astype(np.float32) * 10 + 3
+    else:
+        x = np.random.default_rng(4).standard_normal(shape).astype(np.float32)
+    check_parity(codec, torch, x, ndim, mode, eb)
+
+
+@pytest.mark.parametrize("shape,ndim", [((20, 64, 96), 3), ((257, 300), 2),
+                                        ((30001,), 1)])
+def test_unaligned_input_pointer(codec, torch, shape, ndim):
+    x = fields.grf(shape, -3.0, 5).astype(np.float32)
+    check_parity(codec, torch, x, ndim, fz.EB_REL, 1e-3, offset=1)
+
+
+# ------------------------------------------------------------ full workloads
+@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
+def test_bumps3d_64(codec, torch, eb):
+    check_parity(codec, torch, fields.bumps3d(), 3, fz.EB_REL, eb)
+
+
+@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
+def test_climate2d_1800x3600(codec, torch, eb):
+    check_parity(codec, torch, fields.climate2d(), 2, fz.EB_REL, eb)
+
+
+@pytest.fixture(scope="module")
+def cosmo512():
+    return fields.cosmo3d(512)
+
+
+@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
+def test_cosmo3d_512(codec, torch, cosmo512, eb):
+    g, xr = check_parity(codec, torch, cosmo512, 3, fz.EB_REL, eb)
+    info = fz.inspect(g[:64])
+    x = cosmo512.ravel().astype(np.float64)
+    err = np.abs(x - xr.astype(np.float64))
+    slack = 2.0 ** -22 * np.maximum(np.abs(x), np.abs(xr.astype(np.float64)))
+    assert np.all(err <= info["eb"] + slack)
+
+
+# ------------------------------------------------------------ edge cases
+def test_all_zero_and_constant(codec, torch):
+    check_parity(codec, torch, np.zeros((40, 70, 33), np.float32), 3, fz.EB_ABS, 0.1)
+    check_parity(codec, torch, np.full((40, 70, 33), 7.25, np.float32), 3, fz.EB_REL, 1e-3)
+    check_parity(codec, torch, np.full((1000, 3), -2.0, np.float32), 2, fz.EB_ABS, 1e-3)
+
+
+@pytest.mark.parametrize("shape,ndim", [((24, 64, 64), 3), ((40, 67, 96), 3),
+                                        ((300, 260), 2), ((301, 259), 2),
+                                        ((40000,), 1)])
+def test_outliers(codec, torch, shape, ndim):
+    rng = np.random.default_rng(8)
+    x = rng.normal(0, 1, shape).astype(np.float32)
+    flat = x.reshape(-1)
+    idx = rng.choice(flat.size, 40, replace=False)
+    flat[idx] = rng.choice([-1, 1], 40) * rng.uniform(2e4, 9e4, 40)
+    g, _ = check_parity(codec, torch, x, ndim, fz.EB_ABS, 0.5)
+    assert fz.inspect(g[:64])["n_outliers"] >= 40
+
+
+def test_many_outliers(codec, torch):
+    rng = np.random.default_rng(9)
+    x = (rng.normal(0, 1, (16, 96, 64)) * 3e4).astype(np.float32)
+    g, _ = check_parity(codec, torch, x, 3, fz.EB_ABS, 0.5)
+    assert fz.inspect(g[:64])["n_outliers"] > 10000
+
+
+def test_deterministic(codec, torch):
+    x = fields.grf((33, 100, 70), -2.5, 2).astype(np.float32)
+    a = gpu_compress(codec, torch, x, 3, fz.EB_REL, 1e-4)
+    b = gpu_compress(codec, torch, x, 3, fz.EB_REL, 1e-4)
+    assert a == b
+
+
+# ------------------------------------------------------------ errors
+def _status(codec, torch, x, ndim, mode, eb, cap=None):
+    xt = torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    dims = list(x.shape[::-1])[:ndim]
+    cap = cap if cap is not None else fz.compress_bound(dims, ndim)
+    out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    return codec.compress_into(xt, out, mode, eb, ndim, raise_on_error=False)
+
+
+@pytest.mark.parametrize("mode", [fz.EB_ABS, fz.EB_REL])
+def test_nonfinite(codec, torch, mode):
+    for bad in (np.nan, np.inf, -np.inf):
+        x = np.ones((20, 40, 40), np.float32)
+        x[7, 3, 5] = bad
+        assert _status(codec, torch, x, 3, mode, 1e-3)[0] == fz.ERR_NONFINITE
+        assert oracle.compress(x, 3, mode, 1e-3)[0] == oracle.ERR_NONFINITE
+
+
+def test_eb_range(codec, torch):
+    x = np.ones((64, 64), np.float32)
+    x[3, 3] = 1e7
+    assert _status(codec, torch, x, 2, fz.EB_ABS, 1e-3)[0] == fz.ERR_EB_RANGE
+    assert oracle.compress(x, 2, fz.EB_ABS, 1e-3)[0] == oracle.ERR_EB_RANGE
+    # a relative bound whose absolute value underflows fp32
+    assert _status(codec, torch, x, 2, fz.EB_REL, 1e-300)[0] == fz.ERR_EB_RANGE
+
+
+def test_capacity_reports_size(codec, torch):
+    x = fields.grf((40, 64, 64), -3.0, 3).astype(np.float32)
+    ost, ostream = oracle.compress(x, 3, fz.EB_REL, 1e-4)
+    st, size = _status(codec, torch, x, 3, fz.EB_REL, 1e-4, cap=len(ostream) - 16)
+    assert st == fz.ERR_CAPACITY and size == len(ostream)
+    st, size = _status(codec, torch, x, 3, fz.EB_REL, 1e-4, cap=100)
+    assert st == fz.ERR_CAPACITY and size == fz.stream_min_bytes((64, 64, 40), 3)
+    st, size = _status(codec, torch, x, 3, fz.EB_REL, 1e-4, cap=len(ostream))
+    assert st == fz.OK and size == len(ostream)
+
+
+def _dec_status(codec, torch, s, cap=None, nbytes=None):
+    st_t = torch.from_numpy(np.frombuffer(bytes(s), np.uint8).copy()).cuda()
+    out = torch.empty(cap if cap is not None else 1 << 22, dtype=torch.float32,
+                      device="cuda")
+    return codec.decompress_into(st_t, out, nbytes=nbytes, raise_on_error=False)
+
+
+def test_corrupt_streams(codec, torch):
+    x = fields.grf((40, 70), -3.0, 3).astype(np.float32)
+    x[5, 5] = 3e4
+    _, s = oracle.compress(x, 2, fz.EB_ABS, 0.05)
+    assert _dec_status(codec, torch, s) == fz.OK
+    bad = bytearray(s); bad[0] = ord("X")
+    assert _dec_status(codec, torch, bad) == fz.ERR_CORRUPT
+    assert _dec_status(codec, torch, s, nbytes=len(s) - 16) == fz.ERR_CORRUPT
+    bad = bytearray(s); bad[64] ^= 0x01                 # a flag bit
+    assert _dec_status(codec, torch, bad) == fz.ERR_CORRUPT
+    assert _dec_status(codec, torch, s, cap=10) == fz.ERR_CAPACITY
+    if fz.inspect(s[:64])["n_outliers"]:
+        bad = bytearray(s); bad[-8] ^= 0x01              # outlier index
+        assert _dec_status(codec, torch, bad) == fz.ERR_CORRUPT
+        assert oracle.decompress(bytes(bad))[0] == oracle.ERR_CORRUPT
+
+
+def test_bounded_wait_times_out_and_recovers(codec, torch):
+    """A chunk that never publishes its look-back aggregate: the successors'
+    bounded waits give up and the call reports FZ_ERR_TIMEOUT; the context
+    and the GPU stay usable."""
+    x = fields.grf((32, 128, 128), -3.0, 6).astype(np.float32)
+    codec.set_wait_limit_ns(20_000_000)
+    codec.debug_skip_publish(5)
+    try:
+        assert _status(codec, torch, x, 3, fz.EB_REL, 1e-3)[0] == fz.ERR_TIMEOUT
+        _, s = oracle.compress(x, 3, fz.EB_REL, 1e-3)
+        assert _dec_status(codec, torch, s) == fz.ERR_TIMEOUT
+    finally:
+        codec.debug_skip_publish(None)
+        codec.set_wait_limit_ns(2_000_000_000)
+    check_parity(codec, torch, x, 3, fz.EB_REL, 1e-3)
+
+
+# ------------------------------------------------------------ host API
+def test_host_buffer_calls(codec, torch):
+    x = fields.climate2d(300, 500)
+    _, ostream = oracle.compress(x, 2, fz.EB_REL, 1e-3)
+    s = codec.compress_host(x, mode="rel", eb=1e-3)
+    assert s.tobytes() == ostream
+    y = codec.decompress_host(s)
+    _, xr = oracle.decompress(ostream)
+    np.testing.assert_array_equal(y.ravel().view(np.uint32), xr.view(np.uint32))

@@ -1,0 +1,120 @@
+"""CPU-side checks of the CUDA library: it builds, loads, exports every entry
+point include/fz.h declares, and its host-only calls behave.  No kernel runs
+here (no GPU on this machine)."""
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import paper_2304_12557_gb300 as fz
+from golden_io import expected_bytes, load
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2304_12557_gb300 import build
+    build.build()
+    return fz.load_library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fz.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fz_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_api():
+    assert declared_functions() == sorted(fz.C_API)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", fz.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (fz_\w+)", out))
+    for name in declared_functions():
+        assert name in exported, name
+        assert getattr(lib, name) is not None
+
+
+def test_strerror_and_bounds(lib):
+    import oracle
+    assert lib.fz_strerror(0) == b"success"
+    assert b"corrupt" in lib.fz_strerror(fz.ERR_CORRUPT)
+    for ndim, dims in [(1, (5,)), (2, (3600, 1800)), (3, (512, 512, 512)),
+                       (3, (33, 70, 9))]:
+        assert fz.compress_bound(dims, ndim) == oracle.compress_bound(ndim, dims)
+        nt = oracle.num_tiles(ndim, dims)
+        assert fz.stream_min_bytes(dims, ndim) == 64 + 32 * nt
+    assert fz.compress_bound((0, 4), 2) == 0
+    assert fz.compress_bound((1 << 20, 1 << 20), 2) == 0      # too many codes
+
+
+@pytest.mark.parametrize("name", ["g1_1d_basic.txt", "g2_1d_escape.txt",
+                                  "g3_2d_basic.txt", "g4_3d_rel.txt"])
+def test_inspect_golden(lib, name):
+    rec = load(name)
+    info = fz.inspect(expected_bytes(rec))
+    assert info["ndim"] == rec["ndim"] and info["mode"] == rec["mode"]
+    assert info["dims"] == tuple(rec["dims"])
+    assert info["stream_bytes"] == rec["size"]
+    assert info["nnz_blocks"] == int(rec["header"]["nnz"])
+    assert info["eb"] == float(rec["header"]["eb_f"])
+
+
+def test_inspect_rejects_corrupt(lib):
+    s = bytearray(expected_bytes(load("g1_1d_basic.txt")))
+    s[0] = ord("Q")
+    with pytest.raises(fz.FZError) as e:
+        fz.inspect(bytes(s))
+    assert e.value.status == fz.ERR_CORRUPT
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import ctypes
+    ctx = ctypes.c_void_p()
+    st = lib.fz_create(ctypes.byref(ctx), 0)
+    if st == fz.OK:                       # a GPU is present after all
+        lib.fz_destroy(ctx)
+        pytest.skip("a CUDA device is visible")
+    assert st == fz.ERR_CUDA
+
+
+def test_transpose32_host_build():
+    """The kernels' in-register 32x32 bit transpose, compiled as host code,
+    against the bitshuffle definition (bit t of out[b] = bit b of in[t])."""
+    src = r'''
+#include <cstdio>
+#include "fz_device.cuh"
+int main() {
+  unsigned s = 12345u;
+  for (int rep = 0; rep < 64; ++rep) {
+    uint32_t a[32];
+    for (int i = 0; i < 32; ++i) { s = s * 1664525u + 1013904223u; a[i] = s ^ (s >> 7) * (rep & 1); }
+    if (rep == 0) for (int i = 0; i < 32; ++i) a[i] = 1u << i;
+    for (int i = 0; i < 32; ++i) printf("%u ", a[i]);
+    fz::transpose32(a);
+    for (int i = 0; i < 32; ++i) printf("%u ", a[i]);
+    printf("\n");
+  }
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        cpp = os.path.join(d, "t.cu")
+        exe = os.path.join(d, "t")
+        open(cpp, "w").write(src)
+        inc = os.path.join(ROOT, "paper_2304_12557_gb300", "csrc")
+        subprocess.run(["nvcc", "-std=c++17", "-I", inc, "-o", exe, cpp],
+                       check=True, capture_output=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    for line in out.strip().splitlines():
+        v = np.array([int(t) for t in line.split()], dtype=np.uint64).astype(np.uint32)
+        a, b = v[:32], v[32:]
+        bits_in = np.unpackbits(a.view(np.uint8), bitorder="little").reshape(32, 32)
+        bits_out = np.unpackbits(b.view(np.uint8), bitorder="little").reshape(32, 32)
+        np.testing.assert_array_equal(bits_out, bits_in.T)
