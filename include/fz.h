@@ -152,6 +152,33 @@ int fz_debug_skip_publish(fz_ctx *ctx, uint64_t chunk);
 int fz_set_profiling(fz_ctx *ctx, int on);
 int fz_get_kernel_times(fz_ctx *ctx, double ms[4]);
 
+/* ---------------------------------------------------------------------
+ * Compression without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * GPU memory while they run, e.g. an application whose memory pool has
+ * already reserved the free HBM (a cudaMalloc would fail or fragment it),
+ * a latency-critical loop that cannot pay for cudaMalloc/cudaFree and
+ * their device-wide synchronisation, or a deployment with a memory plan
+ * fixed in advance.
+ *
+ * Same arguments, stream format and statuses as fz_compress, but with no
+ * context: the look-back and result scratch lives in one statically sized
+ * device array inside the library (about 400 KB per device, kept until the
+ * process exits).  Fields are limited to FZ_NOALLOC_MAX_CODES codes after
+ * padding to whole chunks (a 512^3 field fits); larger fields return
+ * FZ_ERR_ARG.  The call uses the calling thread's current device.  Its
+ * first call on a device looks up the array's device address, so make that
+ * first call before any stream capture.  Every call on a device shares the
+ * one array and clears the parts that must start at zero; calls whose GPU
+ * work overlaps (different streams or threads at the same time) race on it
+ * and must be serialised by the caller.  No cudaMalloc, cudaFree or other
+ * allocating routine is called. */
+#define FZ_NOALLOC_MAX_CODES 134217728ull
+int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], int ndim,
+                        int mode, double eb, void *d_out,
+                        uint64_t out_capacity, uint64_t *out_size,
+                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

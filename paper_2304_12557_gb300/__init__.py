@@ -37,7 +37,7 @@ C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
          "fz_compress", "fz_decompress", "fz_compress_host",
          "fz_decompress_host", "fz_inspect", "fz_strerror",
          "fz_set_wait_limit_ns", "fz_debug_skip_publish",
-         "fz_set_profiling", "fz_get_kernel_times"]
+         "fz_set_profiling", "fz_get_kernel_times", "fz_compress_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -99,6 +99,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_debug_skip_publish.argtypes = [_vp, _u64]
         L.fz_set_profiling.argtypes = [_vp, ctypes.c_int]
         L.fz_get_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+        L.fz_compress_noalloc.argtypes = [_vp, dims_t, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, _vp, _u64,
+                                          ctypes.POINTER(_u64), _vp]
         _lib = L
         return L
 
