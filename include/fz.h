@@ -163,7 +163,7 @@ int fz_get_kernel_times(fz_ctx *ctx, double ms[4]);
  *
  * Same arguments, stream format and statuses as fz_compress, but with no
  * context: the look-back and result scratch lives in one statically sized
- * device array inside the library (about 400 KB per device, kept until the
+ * device array inside the library (about 1.6 MB per device, kept until the
  * process exits).  Fields are limited to FZ_NOALLOC_MAX_CODES codes after
  * padding to whole chunks (a 512^3 field fits); larger fields return
  * FZ_ERR_ARG.  The call uses the calling thread's current device.  Its

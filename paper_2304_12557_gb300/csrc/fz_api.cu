@@ -1,7 +1,6 @@
 // fz_api.cu -- the C ABI declared in include/fz.h: context and scratch
-// management, argument checks, TMA descriptors, launches and status mapping.
+// management, argument checks, launches and status mapping.
 #include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -9,7 +8,7 @@
 #include <cstring>
 #include <new>
 
-#include "../../include/fz.h"
+#include "fz.h"
 #include "fz_device.cuh"
 #include "fz_kernels.h"
 
@@ -41,7 +40,6 @@ struct fz_ctx {
   uint64_t stage_in_cap = 0;
   void *stage_out = nullptr;
   uint64_t stage_out_cap = 0;
-  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   // profiling: events around each kernel of the last call
   bool profiling = false;
   cudaEvent_t ev[8] = {};
@@ -106,14 +104,14 @@ int ensure_cap(fz_ctx *c, uint64_t n) {
   while (cap < n) cap *= 2;
   free_scratch(c);
   if (cudaMalloc(&c->sets, 2 * sizeof(SetScratch)) != cudaSuccess ||
-      cudaMalloc(&c->status, 2 * cap * sizeof(uint64_t)) != cudaSuccess ||
+      cudaMalloc(&c->status, 2 * cap * fz::kStatusStride * sizeof(uint64_t)) != cudaSuccess ||
       cudaMalloc(&c->out_prefix, cap * sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&c->out_count, cap * sizeof(uint32_t)) != cudaSuccess) {
     free_scratch(c);
     return FZ_ERR_CUDA;
   }
   if (cudaMemset(c->sets, 0, 2 * sizeof(SetScratch)) != cudaSuccess ||
-      cudaMemset(c->status, 0, 2 * cap * sizeof(uint64_t)) != cudaSuccess ||
+      cudaMemset(c->status, 0, 2 * cap * fz::kStatusStride * sizeof(uint64_t)) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     free_scratch(c);
     return FZ_ERR_CUDA;
@@ -128,7 +126,8 @@ int ensure_cap(fz_ctx *c, uint64_t n) {
 int prepare_set(fz_ctx *c, cudaStream_t s) {
   const int A = c->cur;
   if (c->dirty_hi[A] > 0) {
-    if (cudaMemsetAsync(c->status + A * c->cap, 0, c->dirty_hi[A] * sizeof(uint64_t), s) !=
+    if (cudaMemsetAsync(c->status + A * c->cap * fz::kStatusStride, 0,
+                        c->dirty_hi[A] * fz::kStatusStride * sizeof(uint64_t), s) !=
         cudaSuccess)
       return FZ_ERR_CUDA;
     c->dirty_hi[A] = 0;
@@ -162,26 +161,6 @@ int range_pass(fz_ctx *c, const float *x, uint64_t n, cudaStream_t s) {
   int nb = (int)(want < (uint64_t)c->range_blocks ? (want ? want : 1) : c->range_blocks);
   fz::launch_range(x, n, c->partial, nb, c->range, s);
   return cudaGetLastError() == cudaSuccess ? FZ_OK : FZ_ERR_CUDA;
-}
-
-bool encode_tmap(fz_ctx *c, const Shape &sh, const float *x, CUtensorMap *tm) {
-  if (!c->encode) return false;
-  cuuint64_t gdim[3] = {sh.d[0], sh.d[1], sh.d[2]};
-  cuuint64_t gstr[2] = {sh.d[0] * 4, sh.d[0] * sh.d[1] * 4};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r;
-  if (sh.ndim == 3) {
-    cuuint32_t box[3] = {32, 32, 8};
-    r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(x), gdim, gstr,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  } else {
-    cuuint32_t box[2] = {32, 128};
-    r = c->encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(x), gdim, gstr,
-                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  }
-  return r == CUDA_SUCCESS;
 }
 
 int read_set(fz_ctx *c, int set, cudaStream_t s) {
@@ -253,12 +232,6 @@ int fz_create(fz_ctx **out, int device) {
   if (c->num_sms < 1) c->num_sms = 1;
   c->dec_blocks_per_sm = fz::decompress_blocks_per_sm();
   c->range_blocks = c->num_sms * 8;
-  void *fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                       &q) == cudaSuccess &&
-      q == cudaDriverEntryPointSuccess)
-    c->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   if (cudaMalloc(&c->range, sizeof(RangeResult)) != cudaSuccess ||
       cudaMemset(c->range, 0, sizeof(RangeResult)) != cudaSuccess ||
       cudaMalloc(&c->partial, c->range_blocks * sizeof(float2)) != cudaSuccess ||
@@ -356,7 +329,7 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
   DeviceGuard guard(c->device);
   if (!guard.ok) return FZ_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int st = ensure_cap(c, sh.n_chunks);
+  int st = ensure_cap(c, sh.n_tiles);             // one look-back word per tile
   if (st) return st;
   if ((st = prepare_set(c, s))) return st;
   prof_reset(c);
@@ -366,10 +339,6 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
     prof_end(c, 0, s);
   }
 
-  CUtensorMap tm;
-  std::memset(&tm, 0, sizeof(tm));
-  const bool tma = sh.ndim >= 2 && (sh.d[0] % 4 == 0) &&
-                   (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0 && encode_tmap(c, sh, d_in, &tm);
   const int A = c->cur;
   fz::CompressArgs a{};
   a.x = d_in;
@@ -382,26 +351,35 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
   a.range = c->range;
   a.set_cur = c->sets + A;
   a.set_next = c->sets + (1 - A);
-  a.status_cur = c->status + A * c->cap;
-  a.status_next = c->status + (1 - A) * c->cap;
-  a.chunk_out_prefix = c->out_prefix;
-  a.chunk_out_count = c->out_count;
+  a.status_cur = c->status + A * c->cap * fz::kStatusStride;
+  a.status_next = c->status + (1 - A) * c->cap * fz::kStatusStride;
+  a.tile_out_prefix = c->out_prefix;
+  a.tile_out_count = c->out_count;
   a.out = static_cast<uint8_t *>(d_out);
   a.out_capacity = cap;
   a.wait_limit_ns = c->wait_limit_ns;
   a.skip_publish_chunk = c->skip_publish;
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  const bool tma = fz::compress_uses_tma(sh.ndim, a) &&
+                   fz::encode_field_tmap(sh.ndim, sh.d, d_in, &tm);
   prof_begin(c, 1, s);
-  if (fz::launch_compress(sh.ndim, tma, a, tm, s) != cudaSuccess) {
+  if (fz::launch_compress(sh.ndim, a, tma ? &tm : nullptr, c->num_sms, s) != cudaSuccess) {
     mark_all_dirty(c);
     return FZ_ERR_CUDA;
   }
   prof_end(c, 1, s);
-  retire_set(c, sh.n_chunks, sh.n_chunks);
+  retire_set(c, sh.n_tiles, sh.n_tiles);
   if ((st = read_set(c, A, s))) {
     mark_all_dirty(c);
     return st;
   }
   const SetScratch r = *c->h_res;
+  if (r.err & (fz::kErrNonFinite | fz::kErrEbParam | fz::kErrRange | fz::kErrTimeout)) {
+    // the kernel may have stopped before zeroing the next call's look-back
+    // words: clear every set before the next launch
+    mark_all_dirty(c);
+  }
   if (r.err & fz::kErrNonFinite) return FZ_ERR_NONFINITE;
   if (r.err & (fz::kErrEbParam | fz::kErrRange)) {
     if (mode == FZ_EB_ABS) return classify_range_error(c, d_in, sh.n_elems, s);
@@ -418,7 +396,7 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
     if ((st = prepare_set(c, s))) return st;
     a.set_cur = c->sets + c->cur;
     prof_begin(c, 2, s);
-    if (fz::launch_outliers(sh.ndim, tma, a, tm, min_bytes + 16 * r.nnz, s) != cudaSuccess) {
+    if (fz::launch_outliers(sh.ndim, a, min_bytes + 16 * r.nnz, s) != cudaSuccess) {
       mark_all_dirty(c);
       return FZ_ERR_CUDA;
     }
@@ -460,8 +438,8 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   a.out_cap_elems = cap_elems;
   a.set_cur = c->sets + A;
   a.set_next = c->sets + (1 - A);
-  a.status_cur = c->status + A * c->cap;
-  a.status_next = c->status + (1 - A) * c->cap;
+  a.status_cur = c->status + A * c->cap * fz::kStatusStride;
+  a.status_next = c->status + (1 - A) * c->cap * fz::kStatusStride;
   a.status_cap = c->cap;
   a.wait_limit_ns = c->wait_limit_ns;
   a.skip_publish_chunk = c->skip_publish;
@@ -479,6 +457,7 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   }
   const SetScratch r = *c->h_res;
   retire_set(c, r.n_chunks ? r.n_chunks : c->cap, r.n_chunks);
+  if (r.err & fz::kErrTimeout) mark_all_dirty(c);
   // a timed-out wait leaves later offsets unreliable, so it takes precedence
   if (r.err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
   if (r.err & fz::kErrCorrupt) return FZ_ERR_CORRUPT;

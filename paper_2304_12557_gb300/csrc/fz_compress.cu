@@ -1,21 +1,26 @@
 // fz_compress.cu -- GB300 compression kernels.
 //
 //  range_kernel     value range + non-finite scan (relative bounds, Sec. 4.1)
-//  compress_kernel  one CTA per chunk (4 tiles, 8192 codes), single pass:
-//                   TMA tile load -> pre-quantisation (Sec. 2.3) -> chunk-local
-//                   Lorenzo residual (Sec. 2.3, 3.1) -> sign-magnitude codes
-//                   (Sec. 3.2) -> 32x32 bitshuffle (Sec. 3.3) -> zero-block
-//                   flags and compaction (Sec. 3.4) -> decoupled look-back for
-//                   the payload offset -> one bulk store per tile.
-//  outlier_kernel   rare path: rewrites the escaped residuals of the chunks
-//                   that had any, at offsets found by compress_kernel.
+//  compress_kernel  persistent warps, one 2048-code tile per ticket, single
+//                   pass: 32-byte row loads -> pre-quantisation (Sec. 2.3) ->
+//                   chunk-local Lorenzo residual (Sec. 2.3, 3.1) ->
+//                   sign-magnitude codes (Sec. 3.2) -> 32x32 bitshuffle
+//                   (Sec. 3.3) -> zero-block flags (Sec. 3.4, Listing 1) ->
+//                   decoupled look-back for the payload offset -> compacted
+//                   16-byte block stores (Listing 2).
+//  outlier_kernel   rare path: writes the escaped residuals of the tiles that
+//                   had any, at offsets found by compress_kernel.
 //
 // The paper splits this work into a quantisation kernel, a fused
 // bitshuffle+mark kernel, a CUB scan and an encode kernel with the codes,
 // shuffled words and byte flags passing through global memory; here one
 // kernel does all of it and global memory sees only the input and the stream.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
 
 #include "fz_device.cuh"
 #include "fz_kernels.h"
@@ -111,570 +116,554 @@ __global__ void __launch_bounds__(256) range_kernel(const float *__restrict__ x,
 }
 
 // ====================================================================
-// compression
+// compression: persistent warps, one 2048-code tile per ticket
 // ====================================================================
-template <int NDIM>
-struct Brick {
-  using G = Geo<NDIM>;
-  static constexpr int N = 64;
+//
+// Every warp is independent (no block-level barrier).  A warp takes the
+// next tile from a ticket counter in stream order and does the whole tile:
+// pre-quantisation, Lorenzo, codes, bitshuffle, flags, the decoupled
+// look-back on the tile index and the compacted stores.  Its input comes
+// either from a per-warp TMA box (the tile plus the previous plane/row the
+// first Lorenzo difference needs, loaded asynchronously one tile ahead) or,
+// for fields whose rows are not 16-byte aligned and for 1-D fields, straight
+// from global memory.
+
+constexpr int kCompWarps = 4;                   // warps per block
+// per warp: [TMA box 8 KB][plane buffer 0, 4 KB][plane buffer 1, 4 KB]
+constexpr int kBoxStride = 16384;
+constexpr int kPlaneOff = 8192;
+constexpr int kCompSmemTma = kCompWarps * kBoxStride + 64 + 1024;
+constexpr int kCompSmemLdg = kCompWarps * 8192 + 64 + 1024;
+constexpr int kHalf2D = 4096;                   // second x half of a 2-D box
+constexpr uint32_t kTileBoxBytes = 32 * 32 * 2 * 4;  // one tile (3-D: 2 planes; 2-D: 2 halves)
+
+// 8 consecutive floats from p.  V = 8: one 32-byte load (p 32-byte
+// aligned); V = 4: two 16-byte loads; V = 1: scalar loads.
+template <int V>
+__device__ __forceinline__ void load8(const float *p, float (&f)[8]) {
+  if constexpr (V == 8) {
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]),
+          "=f"(f[6]), "=f"(f[7])
+        : "l"(p));
+  } else if constexpr (V == 4) {
+    const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldcs(reinterpret_cast<const float4 *>(p) + 1);
+    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+    f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = __ldcs(p + k);
+  }
+}
+
+// fl(v + 1.5*2^23) of v = fl(x * r): the integer rint(v) sits in the low
+// mantissa bits; returned as raw bits (biased by kMagicBits).
+__device__ __forceinline__ int32_t quant_bits(float x, float r) {
+  return (int32_t)__float_as_uint(__fadd_rn(__fmul_rn(x, r), kRoundMagic));
+}
+
+struct TileGeo {
+  uint64_t x0, y0, z0;       // origin of this lane's brick
+  uint64_t cx, cy, cz;       // chunk coordinates
+  int t, bx, by;
+  bool edge;                 // the chunk reaches past the field
 };
 
-// byte offset inside the chunk box (swizzled rows of 32 floats) of the
-// chunk-local element (lx, ly, lz)
 template <int NDIM>
-__device__ __forceinline__ uint32_t box_offset(uint32_t lx, uint32_t ly,
-                                               uint32_t lz) {
+__device__ __forceinline__ TileGeo tile_geo(const CompressArgs &a, uint64_t T, int g) {
+  using G = Geo<NDIM>;
+  TileGeo q;
+  const uint64_t c = T >> 2;
+  q.t = (int)(T & 3);
+  q.cx = c % a.ncx;
+  q.cy = (c / a.ncx) % a.ncy;
+  q.cz = c / ((uint64_t)a.ncx * a.ncy);
+  q.bx = g % G::NBX;
+  q.by = g / G::NBX;
   if constexpr (NDIM == 3) {
-    uint32_t r = ly + 32u * lz;
-    return swz(r, lx >> 2) + ((lx & 3u) << 2);
+    q.x0 = q.cx * 32 + 8 * q.bx; q.y0 = q.cy * 32 + 4 * q.by; q.z0 = q.cz * 8 + 2 * q.t;
   } else if constexpr (NDIM == 2) {
-    uint32_t half = lx >> 5, col = lx & 31u;
-    return half * 16384u + swz(ly, col >> 2) + ((col & 3u) << 2);
+    q.x0 = q.cx * 64 + 8 * q.bx; q.y0 = q.cy * 128 + 32 * q.t + 8 * q.by; q.z0 = 0;
   } else {
-    uint32_t r = lx >> 5, col = lx & 31u;
-    return swz(r, col >> 2) + ((col & 3u) << 2);
+    q.x0 = q.cx * 8192 + 2048 * q.t + 64 * g; q.y0 = 0; q.z0 = 0;
+  }
+  q.edge = (q.cx + 1) * G::CX > a.dims[0] || (q.cy + 1) * G::CY > a.dims[1] ||
+           (q.cz + 1) * G::CZ > a.dims[2];
+  return q;
+}
+
+// Rows of 8 floats of a lane's brick, read from global memory.  Row
+// selectors: 3-D (p, iy) with p = -1 the previous plane, 0/1 the brick's
+// planes; 2-D (0, iy) with iy = -1 the previous row; 1-D (0, 0, xo).
+// Elements outside the field read as 0.
+template <int NDIM, int V>
+struct GlobalRows {
+  const CompressArgs &a;
+  const TileGeo &q;
+  __device__ __forceinline__ void row(int p, int iy, int xo, float (&f)[8]) const {
+    const uint64_t x = q.x0 + xo, y = q.y0 + iy, z = q.z0 + p;
+    const float *ptr = a.x + x + a.dims[0] * (y + a.dims[1] * z);
+    if (!q.edge) {
+      load8<V>(ptr, f);
+    } else {
+      const bool in = y < a.dims[1] && z < a.dims[2];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) f[k] = (in && x + k < a.dims[0]) ? __ldcs(ptr + k) : 0.0f;
+    }
+  }
+};
+
+// The same rows from the warp's TMA box (128-byte swizzled rows of 32
+// floats; the TMA unit has zero-filled everything outside the field).
+// Only the brick's own rows come from the box (p = 0, 1 / iy >= 0).
+template <int NDIM>
+struct BoxRows {
+  const uint8_t *box;
+  int bx, by;
+  __device__ __forceinline__ void row(int p, int iy, int, float (&f)[8]) const {
+    uint32_t base, r, c0;
+    if constexpr (NDIM == 3) {
+      base = 0; r = (uint32_t)(4 * by + iy + 32 * p); c0 = 2 * bx;
+    } else {
+      base = (bx >> 2) * kHalf2D; r = (uint32_t)(8 * by + iy); c0 = 2 * (bx & 3);
+    }
+    const float4 u = *reinterpret_cast<const float4 *>(box + base + swz(r, c0));
+    const float4 w = *reinterpret_cast<const float4 *>(box + base + swz(r, c0 + 1));
+    f[0] = u.x; f[1] = u.y; f[2] = u.z; f[3] = u.w;
+    f[4] = w.x; f[5] = w.y; f[6] = w.z; f[7] = w.w;
+  }
+};
+
+// The neighbours the first Lorenzo difference needs from the previous tile
+// of the chunk (3-D: the previous plane under the brick, 2-D: the row
+// before the brick for by == 0 lanes), read from global memory before the
+// tile's own data is waited for.  A chunk's first tile has none.
+template <int NDIM, int V>
+__device__ __forceinline__ void load_halo(const CompressArgs &a, const TileGeo &q,
+                                          float (&hf)[32]) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) hf[k] = 0.0f;
+  const GlobalRows<NDIM, V> src{a, q};
+  if constexpr (NDIM == 3) {
+    if (q.t > 0) {
+#pragma unroll
+      for (int iy = 0; iy < 4; ++iy) {
+        float h8[8];
+        src.row(-1, iy, 0, h8);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) hf[8 * iy + k] = h8[k];
+      }
+    }
+  } else if constexpr (NDIM == 2) {
+    if (q.t > 0 && q.by == 0) {
+      float h8[8];
+      src.row(0, -1, 0, h8);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) hf[k] = h8[k];
+    }
   }
 }
 
-// Fill the chunk box with plain loads (fields whose rows are not 16-byte
-// aligned, and every 1-D field).  Out-of-field elements read as 0.
-template <int NDIM>
-__device__ __forceinline__ void fill_box_generic(const CompressArgs &a,
-                                                 uint8_t *box, uint32_t cx,
-                                                 uint32_t cy, uint32_t cz) {
-  using G = Geo<NDIM>;
-  const uint64_t X = a.dims[0], Y = a.dims[1];
-  for (uint32_t e0 = 0; e0 < (uint32_t)kChunkCodes; e0 += kThreads * 8) {
-    float v[8];
+// Part 1 of a brick's residuals: read the brick, pre-quantise (Sec. 2.3) and
+// take the first difference against the preloaded neighbours hf (a chunk's
+// first tile has none: q = 0 there).  CHECK folds the unsigned maximum of
+// (bits - kBiasBits) into qmax, checking the value range per element
+// (absolute bounds; with a relative bound the range pass has shown that every
+// element passes).
+template <int NDIM, bool CHECK, class Src>
+__device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q, int g,
+                                                float r, const float (&hf)[32],
+                                                int32_t (&v)[64], uint32_t &qmax) {
+  const unsigned full = 0xffffffffu;
+  const int32_t pad = (int32_t)kMagicBits;           // q = 0
+  if constexpr (NDIM == 3) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      uint32_t e = e0 + k * kThreads + threadIdx.x;
-      uint32_t lx = e % G::CX, ly = (e / G::CX) % G::CY, lz = e / (G::CX * G::CY);
-      uint64_t gx = (uint64_t)cx * G::CX + lx, gy = (uint64_t)cy * G::CY + ly,
-               gz = (uint64_t)cz * G::CZ + lz;
-      bool in = gx < X && gy < a.dims[1] && gz < a.dims[2];
-      v[k] = in ? __ldcs(&a.x[gx + X * (gy + Y * gz)]) : 0.0f;
+    for (int iy = 0; iy < 4; ++iy) {                 // D_z, one row at a time
+      float p0[8], p1[8];
+      src.row(0, iy, 0, p0);
+      src.row(1, iy, 0, p1);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int32_t q0 = quant_bits(p0[k], r), q1 = quant_bits(p1[k], r);
+        const int32_t qh = q.t > 0 ? quant_bits(hf[8 * iy + k], r) : pad;
+        if (CHECK) qmax = max(qmax, max((uint32_t)q0 - kBiasBits, (uint32_t)q1 - kBiasBits));
+        v[8 * iy + k] = q0 - qh;
+        v[32 + 8 * iy + k] = q1 - q0;
+      }
+    }
+  } else if constexpr (NDIM == 2) {
+#pragma unroll
+    for (int row = 0; row < 8; ++row) {
+      float f8[8];
+      src.row(0, row, 0, f8);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        v[8 * row + k] = quant_bits(f8[k], r);
+        if (CHECK) qmax = max(qmax, (uint32_t)v[8 * row + k] - kBiasBits);
+      }
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      uint32_t e = e0 + k * kThreads + threadIdx.x;
-      uint32_t lx = e % G::CX, ly = (e / G::CX) % G::CY, lz = e / (G::CX * G::CY);
-      *reinterpret_cast<float *>(box + box_offset<NDIM>(lx, ly, lz)) = v[k];
+    for (int ix = 0; ix < 8; ++ix) {                 // D_y
+      int32_t up = __shfl_up_sync(full, v[ix + 56], 8);
+      if (q.by == 0) up = q.t > 0 ? quant_bits(hf[ix], r) : pad;
+#pragma unroll
+      for (int iy = 7; iy >= 1; --iy) v[ix + 8 * iy] -= v[ix + 8 * (iy - 1)];
+      v[ix] -= up;
     }
-  }
-}
-
-// Load a thread's brick from the box (warp t = tile t of the chunk, lane g =
-// brick g) and pre-quantise it: returns biased q (q + 2^22 - 1) and folds the
-// unsigned maximum into qmax (> kBiasedMax means out of range / non-finite).
-template <int NDIM>
-__device__ __forceinline__ void load_quant(const uint8_t *box, int t, int g,
-                                           float r, int32_t (&tq)[64],
-                                           uint32_t &qmax) {
-  using G = Geo<NDIM>;
-  const int bx = g % G::NBX, by = g / G::NBX;
+  } else {
 #pragma unroll
-  for (int iz = 0; iz < G::BZ; ++iz) {
+    for (int row = 0; row < 8; ++row) {
+      float f8[8];
+      src.row(0, 0, 8 * row, f8);
 #pragma unroll
-    for (int iy = 0; iy < G::BY; ++iy) {
-#pragma unroll
-      for (int h = 0; h < G::BX / 4; ++h) {
-        uint32_t off;
-        if constexpr (NDIM == 3) {
-          uint32_t row = (uint32_t)(4 * by + iy + 32 * (2 * t + iz));
-          off = swz(row, (uint32_t)(2 * bx + h));
-        } else if constexpr (NDIM == 2) {
-          uint32_t row = (uint32_t)(32 * t + 8 * by + iy);
-          off = (uint32_t)(bx >> 2) * 16384u + swz(row, (uint32_t)(2 * (bx & 3) + h));
-        } else {
-          uint32_t row = (uint32_t)(64 * t + 2 * g + (h >> 3));
-          off = swz(row, (uint32_t)(h & 7));
-        }
-        float4 v = *reinterpret_cast<const float4 *>(box + off);
-        float f[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int e = 4 * h + k + G::BX * (iy + G::BY * iz);
-          float s = __fadd_rn(__fmul_rn(f[k], r), kRoundMagic);
-          uint32_t b = __float_as_uint(s) - kBiasBits;
-          qmax = max(qmax, b);
-          tq[e] = (int32_t)b;
-        }
+      for (int k = 0; k < 8; ++k) {
+        v[8 * row + k] = quant_bits(f8[k], r);
+        if (CHECK) qmax = max(qmax, (uint32_t)v[8 * row + k] - kBiasBits);
       }
     }
   }
 }
 
-// Chunk-local Lorenzo residual of the thread's brick, in place on tq (biased
-// q in, residual out).  `halo` carries the neighbour values across the warp
-// boundary (previous tile of the chunk), already in biased form:
-//   3-D: the previous z plane of this brick (32 values), 2-D: the previous
-//   y row (8 values, used by by == 0 lanes), 1-D: the previous element.
-// Neighbours outside the chunk are q = 0 (biased kPadBiased) for the first
-// difference and 0 for the later ones.
+// Part 2: the remaining differences (no more input reads) and code 0 for
+// padding positions.
 template <int NDIM>
-__device__ __forceinline__ void lorenzo(int32_t (&v)[64], const int32_t *halo,
-                                        int g) {
+__device__ __forceinline__ void residuals_rest(const CompressArgs &a, const TileGeo &q, int g,
+                                               float r, int32_t (&v)[64]) {
   using G = Geo<NDIM>;
-  const int bx = g % G::NBX, by = g / G::NBX;
   const unsigned full = 0xffffffffu;
   if constexpr (NDIM == 3) {
-    // D_z (biased values; previous plane from halo)
 #pragma unroll
-    for (int e = 63; e >= 32; --e) v[e] -= v[e - 32];
-#pragma unroll
-    for (int e = 0; e < 32; ++e) v[e] -= halo[e];
-    // D_y: row iy-1 of the brick, or row iy = 3 of the brick below (lane-4)
-#pragma unroll
-    for (int iz = 0; iz < 2; ++iz) {
+    for (int iz = 0; iz < 2; ++iz) {                 // D_y
 #pragma unroll
       for (int ix = 0; ix < 8; ++ix) {
         int32_t up = __shfl_up_sync(full, v[ix + 24 + 32 * iz], 4);
-        if (by == 0) up = 0;
+        if (q.by == 0) up = 0;
 #pragma unroll
         for (int iy = 3; iy >= 1; --iy) v[ix + 8 * iy + 32 * iz] -= v[ix + 8 * (iy - 1) + 32 * iz];
         v[ix + 32 * iz] -= up;
       }
     }
-    // D_x: element ix-1, or ix = 7 of the brick to the left (lane-1)
+  }
+  if constexpr (NDIM >= 2) {
 #pragma unroll
-    for (int row = 0; row < 8; ++row) {
+    for (int row = 0; row < 8; ++row) {              // D_x
       int32_t left = __shfl_up_sync(full, v[7 + 8 * row], 1);
-      if (bx == 0) left = 0;
-#pragma unroll
-      for (int ix = 7; ix >= 1; --ix) v[ix + 8 * row] -= v[ix - 1 + 8 * row];
-      v[8 * row] -= left;
-    }
-  } else if constexpr (NDIM == 2) {
-    // D_y on biased values: row iy-1, or row 7 of the brick below (lane-8),
-    // or for by == 0 the last row of the previous tile (halo)
-#pragma unroll
-    for (int ix = 0; ix < 8; ++ix) {
-      int32_t up = __shfl_up_sync(full, v[ix + 56], 8);
-      if (by == 0) up = halo[ix];
-#pragma unroll
-      for (int iy = 7; iy >= 1; --iy) v[ix + 8 * iy] -= v[ix + 8 * (iy - 1)];
-      v[ix] -= up;
-    }
-    // D_x
-#pragma unroll
-    for (int row = 0; row < 8; ++row) {
-      int32_t left = __shfl_up_sync(full, v[7 + 8 * row], 1);
-      if (bx == 0) left = 0;
+      if (q.bx == 0) left = 0;
 #pragma unroll
       for (int ix = 7; ix >= 1; --ix) v[ix + 8 * row] -= v[ix - 1 + 8 * row];
       v[8 * row] -= left;
     }
   } else {
+    int32_t hq = (int32_t)kMagicBits;
+    if (q.t > 0 && g == 0)
+      hq = quant_bits((q.x0 - 1 < a.dims[0]) ? __ldcs(a.x + q.x0 - 1) : 0.0f, r);
     int32_t left = __shfl_up_sync(full, v[63], 1);
-    if (g == 0) left = halo[0];
+    if (g == 0) left = hq;
 #pragma unroll
     for (int e = 63; e >= 1; --e) v[e] -= v[e - 1];
     v[0] -= left;
   }
-}
-
-// zero the residuals of brick elements that lie outside the field
-template <int NDIM>
-__device__ __forceinline__ void mask_outside(int32_t (&v)[64], const CompressArgs &a,
-                                             uint32_t cx, uint32_t cy, uint32_t cz,
-                                             int t, int g) {
-  using G = Geo<NDIM>;
-  const int bx = g % G::NBX, by = g / G::NBX;
+  if (q.edge) {
+    const uint64_t X = a.dims[0];
+    const uint64_t lx = q.x0 < X ? X - q.x0 : 0;
+    const uint64_t ly = q.y0 < a.dims[1] ? a.dims[1] - q.y0 : 0;
+    const uint64_t lz = q.z0 < a.dims[2] ? a.dims[2] - q.z0 : 0;
 #pragma unroll
-  for (int e = 0; e < 64; ++e) {
-    const int ix = e % G::BX, iy = (e / G::BX) % G::BY, iz = e / (G::BX * G::BY);
-    uint64_t gx, gy = 0, gz = 0;
-    if constexpr (NDIM == 3) {
-      gx = (uint64_t)cx * 32 + 8 * bx + ix;
-      gy = (uint64_t)cy * 32 + 4 * by + iy;
-      gz = (uint64_t)cz * 8 + 2 * t + iz;
-    } else if constexpr (NDIM == 2) {
-      gx = (uint64_t)cx * 64 + 8 * bx + ix;
-      gy = (uint64_t)cy * 128 + 32 * t + 8 * by + iy;
-    } else {
-      gx = (uint64_t)cx * 8192 + 2048 * t + 64 * g + e;
+    for (int e = 0; e < 64; ++e) {
+      const int ix = e % G::BX, iy = (e / G::BX) % G::BY, iz = e / (G::BX * G::BY);
+      if (!((uint64_t)ix < lx && (uint64_t)iy < ly && (uint64_t)iz < lz)) v[e] = 0;
     }
-    if (!(gx < a.dims[0] && gy < a.dims[1] && gz < a.dims[2])) v[e] = 0;
   }
 }
 
-// byte offset of warp t's k-th 4 KB piece of the box: the rows its tile
-// occupies (3-D: planes 2t..2t+1; 2-D: rows 32t.. of both x halves; 1-D:
-// elements 2048t..)
-template <int NDIM>
-__device__ __forceinline__ uint32_t piece_offset(int t, int k) {
-  if constexpr (NDIM == 2) return (uint32_t)(k * 16384 + t * 4096);
-  return (uint32_t)(t * 8192 + k * 4096);
+// all residuals from global memory (the rare escape repack and the outlier
+// pass, when the TMA box no longer holds the tile)
+template <int NDIM, int V>
+__device__ __forceinline__ void residuals_global(const CompressArgs &a, uint64_t T, int g,
+                                                 float r, int32_t (&v)[64]) {
+  const TileGeo q = tile_geo<NDIM>(a, T, g);
+  uint32_t unused = 0;
+  float hf[32];
+  load_halo<NDIM, V>(a, q, hf);
+  residuals_first<NDIM, false>(GlobalRows<NDIM, V>{a, q}, q, g, r, hf, v, unused);
+  residuals_rest<NDIM>(a, q, g, r, v);
 }
 
-template <int NDIM>
-__device__ __forceinline__ bool chunk_is_edge(const CompressArgs &a, uint32_t cx,
-                                              uint32_t cy, uint32_t cz) {
-  using G = Geo<NDIM>;
-  return (uint64_t)(cx + 1) * G::CX > a.dims[0] ||
-         (uint64_t)(cy + 1) * G::CY > a.dims[1] ||
-         (uint64_t)(cz + 1) * G::CZ > a.dims[2];
-}
-
-// halo written by warp t for warp t+1: the part of the thread's biased q
-// that the next tile's first difference needs
-template <int NDIM>
-__device__ __forceinline__ void write_halo(int32_t *xch, const int32_t (&tq)[64],
-                                           int g) {
-  using G = Geo<NDIM>;
-  if constexpr (NDIM == 3) {
-    // last z plane of the brick: 32 values, row-swizzled per lane
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      int4 v = make_int4(tq[32 + 4 * c], tq[33 + 4 * c], tq[34 + 4 * c], tq[35 + 4 * c]);
-      *reinterpret_cast<int4 *>(xch + 32 * g + 4 * (c ^ (g & 7))) = v;
-    }
-  } else if constexpr (NDIM == 2) {
-    if (g / G::NBX == G::NBY - 1) {
-      const int bx = g % G::NBX;
-#pragma unroll
-      for (int ix = 0; ix < 8; ++ix) xch[8 * bx + ix] = tq[56 + ix];
-    }
-  } else {
-    if (g == 31) xch[0] = tq[63];
-  }
-}
-
-template <int NDIM>
-__device__ __forceinline__ void read_halo(int32_t (&halo)[32], const int32_t *xch,
-                                          int t, int g) {
-  using G = Geo<NDIM>;
-  if constexpr (NDIM == 3) {
-    if (t == 0) {
-#pragma unroll
-      for (int e = 0; e < 32; ++e) halo[e] = kPadBiased;
-    } else {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        int4 v = *reinterpret_cast<const int4 *>(xch + 32 * g + 4 * (c ^ (g & 7)));
-        halo[4 * c] = v.x; halo[4 * c + 1] = v.y; halo[4 * c + 2] = v.z; halo[4 * c + 3] = v.w;
-      }
-    }
-  } else if constexpr (NDIM == 2) {
-    const int bx = g % G::NBX;
-#pragma unroll
-    for (int ix = 0; ix < 8; ++ix) halo[ix] = t == 0 ? kPadBiased : xch[8 * bx + ix];
-  } else {
-    halo[0] = t == 0 ? kPadBiased : xch[0];
-  }
-}
-
-// residual -> 16-bit sign-magnitude code pairs (Sec. 3.2); |r| >= 2^15 gets
-// the escape code 0x8000.  Returns the OR of |r| over the brick.
-__device__ __forceinline__ uint32_t pack_codes(const int32_t (&v)[64],
-                                               uint32_t (&w)[32], bool escapes) {
+// residuals -> pairs of 16-bit sign-magnitude codes (Sec. 3.2), even code in
+// the low half.  Returns the OR of |residual| (bit 15 or above set: escapes).
+__device__ __forceinline__ uint32_t pack_codes(const int32_t (&v)[64], uint32_t (&w)[32]) {
   uint32_t orabs = 0;
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
-    int32_t d0 = v[2 * i], d1 = v[2 * i + 1];
-    uint32_t a0 = (uint32_t)abs(d0), a1 = (uint32_t)abs(d1);
+    const int32_t d0 = v[2 * i], d1 = v[2 * i + 1];
+    const uint32_t a0 = (uint32_t)abs(d0), a1 = (uint32_t)abs(d1);
     orabs |= a0 | a1;
-    uint32_t c0 = a0 | ((uint32_t)(d0 >> 16) & 0x8000u);
-    uint32_t c1 = a1 | ((uint32_t)(d1 >> 16) & 0x8000u);
-    if (escapes) {
-      c0 = a0 > 32767u ? 0x8000u : c0;
-      c1 = a1 > 32767u ? 0x8000u : c1;
-    }
-    w[i] = __byte_perm(c0, c1, 0x5410);
+    const uint32_t mag = byte_perm(a0, a1, 0x5410);             // |d0| | |d1|<<16
+    const uint32_t sgn = byte_perm((uint32_t)d0, (uint32_t)d1, 0x7030);
+    w[i] = mag | (sgn & 0x80008000u);
   }
   return orabs;
 }
 
-// one warp: everything from the box to the compacted tile in shared memory.
-// Returns this tile's block count; writes the flag bytes to global memory.
-struct TileOut {
-  uint32_t nnz;
-  uint32_t nout;
-};
-
-template <int NDIM>
-__device__ __forceinline__ void compute_residuals(const CompressArgs &a, const uint8_t *box,
-                                                  const int32_t *xch_prev, int32_t *xch_own,
-                                                  float r, uint32_t cx, uint32_t cy,
-                                                  uint32_t cz, int t, int g,
-                                                  int32_t (&v)[64], uint32_t &qmax,
-                                                  bool edge, bool sync_between) {
-  load_quant<NDIM>(box, t, g, r, v, qmax);
-  write_halo<NDIM>(xch_own, v, g);
-  if (sync_between) __syncthreads();
-  int32_t halo[32];
-  read_halo<NDIM>(halo, xch_prev, t, g);
-  lorenzo<NDIM>(v, halo, g);
-  if (edge) mask_outside<NDIM>(v, a, cx, cy, cz, t, g);
+// escape: a residual whose magnitude needs more than 15 bits gets 0x8000
+__device__ __forceinline__ uint32_t pack_codes_escaped(const int32_t (&v)[64], uint32_t (&w)[32]) {
+  uint32_t n = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int32_t d0 = v[2 * i], d1 = v[2 * i + 1];
+    const uint32_t a0 = (uint32_t)abs(d0), a1 = (uint32_t)abs(d1);
+    uint32_t c0 = a0 | ((uint32_t)(d0 >> 16) & 0x8000u);
+    uint32_t c1 = a1 | ((uint32_t)(d1 >> 16) & 0x8000u);
+    n += (a0 > 32767u) + (a1 > 32767u);
+    c0 = a0 > 32767u ? 0x8000u : c0;
+    c1 = a1 > 32767u ? 0x8000u : c1;
+    w[i] = byte_perm(c0, c1, 0x5410);
+  }
+  return n;
 }
 
-template <int NDIM, bool TMA>
-__global__ void __launch_bounds__(kThreads, 4)
-    compress_kernel(const CompressArgs a, const __grid_constant__ CUtensorMap tmap) {
-  using G = Geo<NDIM>;
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t *box = smem;                                   // 32 KB, per warp 8 KB
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kBoxBytes);
-  uint32_t *sh = reinterpret_cast<uint32_t *>(smem + kBoxBytes + 16);
-  // sh[0] ticket, sh[1..4] tile nnz, sh[5..8] tile nout, sh[9] flags,
-  // sh[10..11] base (u64), sh[12] eb ok, sh[13] r bits
-  const int tid = threadIdx.x, t = tid >> 5, g = tid & 31;
-  SetScratch *cur = a.set_cur;
+// TMA box of tile T for this warp: 3-D {32,32,2} (the tile's two planes),
+// 2-D two {32,32} x halves of the tile's 32 rows
+template <int NDIM>
+__device__ __forceinline__ void issue_box(const CompressArgs &a, const CUtensorMap *tm,
+                                          uint8_t *box, uint64_t *bar, uint64_t T) {
+  const uint64_t c = T >> 2;
+  const int t = (int)(T & 3);
+  const uint64_t cx = c % a.ncx, cy = (c / a.ncx) % a.ncy, cz = c / ((uint64_t)a.ncx * a.ncy);
+  mbar_expect_tx(bar, kTileBoxBytes);
+  if constexpr (NDIM == 3) {
+    tma_load_3d(box, tm, bar, (int)(cx * 32), (int)(cy * 32), (int)(cz * 8 + 2 * t));
+  } else {
+    const int y = (int)(cy * 128 + 32 * t);
+    tma_load_2d(box, tm, bar, (int)(cx * 64), y);
+    tma_load_2d(box + kHalf2D, tm, bar, (int)(cx * 64 + 32), y);
+  }
+}
 
-  if (tid == 0) {
-    uint32_t c = atomicAdd(&cur->ticket, 1u);
-    sh[0] = c;
-    // zero the other set's status word for this chunk (used by the next call)
-    a.status_next[c] = 0;
-    if (c == 0) {
-      SetScratch *nx = a.set_next;
-      nx->ticket = 0; nx->err = 0; nx->nnz = 0; nx->nout = 0;
-      nx->n_chunks = 0; nx->hdr_nout = 0;
-    }
-    float fmin = 0.f, fmax = 0.f;
-    bool nonfinite = false;
-    if (a.mode == 1) {
-      fmin = a.range->fmin; fmax = a.range->fmax;
-      nonfinite = a.range->nonfinite != 0;
-    }
-    EbParams p = derive_eb(a.mode, a.eb_req, fmin, fmax);
-    sh[12] = (p.ok && !nonfinite) ? 1u : 0u;
-    sh[13] = __float_as_uint(p.ebx2_r);
-    if (c == a.n_chunks - 1) {
-      // the header's static fields; the totals follow after the look-back
+// the compacted blocks of a finished tile, resolved one tile later
+struct Pending {
+  uint64_t T;          // tile index (n_tiles: none)
+  uint64_t agg;        // (blocks << 32) | outliers
+  uint32_t F, P;       // lane b: flag byte and exclusive block rank of plane b
+  uint32_t *pb;        // its plane buffer
+};
+
+// Resolve a finished tile's prefix (look-back) and store its compacted blocks
+// (Listing 2's copy: block (b, i) -> payload[PreSum]).
+template <int NDIM>
+__device__ __forceinline__ void finish_tile(const CompressArgs &a, const Pending &d,
+                                            const EbParams &p, float fmin, float fmax,
+                                            uint64_t n_tiles, uint64_t pay, int g) {
+  SetScratch *cur = a.set_cur;
+  const uint64_t excl = resolve_prefix(a.status_cur, d.T, d.agg,
+                                       (d.T >> 2) != a.skip_publish_chunk, &cur->err,
+                                       a.wait_limit_ns);
+  if (g == 0) {
+    a.tile_out_prefix[d.T] = (uint32_t)excl;
+    a.tile_out_count[d.T] = (uint32_t)d.agg;
+    if (d.T == n_tiles - 1) {
+      const uint64_t inc = excl + d.agg;
       StreamHeader *h = reinterpret_cast<StreamHeader *>(a.out);
       h->magic[0] = 'F'; h->magic[1] = 'Z'; h->magic[2] = 'G'; h->magic[3] = '1';
       h->version = 1; h->ndim = (uint8_t)NDIM; h->mode = (uint8_t)a.mode;
       h->reserved0 = 0;
       h->dims[0] = (uint32_t)a.dims[0]; h->dims[1] = (uint32_t)a.dims[1];
       h->dims[2] = (uint32_t)a.dims[2];
-      h->n_tiles = (uint32_t)(a.n_chunks * kTilesPerChunk);
+      h->n_tiles = (uint32_t)n_tiles;
       h->eb_requested = a.eb_req;
       h->eb = p.eb; h->ebx2 = p.ebx2; h->ebx2_r = p.ebx2_r;
+      h->nnz_blocks = (uint32_t)(inc >> 32);
+      h->n_outliers = (uint32_t)inc;
       h->range_min = fmin; h->range_max = fmax;
       h->reserved1 = 0;
-      if (!p.ok) atomicOr(&cur->err, kErrEbParam);
-      if (nonfinite) atomicOr(&cur->err, kErrNonFinite);
+      cur->nnz = inc >> 32;
+      cur->nout = inc & 0xffffffffull;
     }
-    if (TMA) mbar_init(bar, 1);
   }
-  __syncthreads();
-  const uint64_t c = sh[0];
-  if (sh[12] == 0) return;                 // the same decision in every CTA
-  const float r = __uint_as_float(sh[13]);
-  const uint32_t cx = (uint32_t)(c % a.ncx);
-  const uint32_t cy = (uint32_t)((c / a.ncx) % a.ncy);
-  const uint32_t cz = (uint32_t)(c / ((uint64_t)a.ncx * a.ncy));
-
-  // ---- stage the chunk in shared memory
-  bool load_ok = true;
-  if constexpr (TMA) {
-    if (tid == 0) {
-      mbar_expect_tx(bar, kBoxBytes);
-      if constexpr (NDIM == 3) {
-        tma_load_3d(box, &tmap, bar, (int)(cx * 32), (int)(cy * 32), (int)(cz * 8));
-      } else {
-        tma_load_2d(box, &tmap, bar, (int)(cx * 64), (int)(cy * 128));
-        tma_load_2d(box + 16384, &tmap, bar, (int)(cx * 64 + 32), (int)(cy * 128));
-      }
-    }
-    load_ok = mbar_wait_bounded(bar, 0, a.wait_limit_ns);
-    if (!load_ok && g == 0) atomicOr(&cur->err, kErrTimeout);
-  } else {
-    fill_box_generic<NDIM>(a, box, cx, cy, cz);
-    __syncthreads();
-  }
-
-  // ---- per warp: tile t of the chunk.  Each warp reads only its own two
-  // 4 KB pieces of the box, which it reuses afterwards as scratch.
-  uint8_t *piece_a = box + piece_offset<NDIM>(t, 0);
-  uint8_t *piece_b = box + piece_offset<NDIM>(t, 1);
-  int32_t *xch_own = reinterpret_cast<int32_t *>(
-      smem + kBoxBytes + 1024 + t * 4096); // halo handed to warp t+1
-  const int32_t *xch_prev = reinterpret_cast<const int32_t *>(
-      smem + kBoxBytes + 1024 + (t > 0 ? t - 1 : 0) * 4096);
-  const bool edge = chunk_is_edge<NDIM>(a, cx, cy, cz);
-  int32_t v[64];
-  uint32_t qmax = 0;
-  compute_residuals<NDIM>(a, box, xch_prev, xch_own, r, cx, cy, cz, t, g, v, qmax,
-                          edge, true);
-  if (__any_sync(0xffffffffu, qmax > kBiasedMax) && g == 0)
-    atomicOr(&cur->err, kErrRange);
-
-  uint32_t w[32];
-  uint32_t orabs = pack_codes(v, w, false);
-  const bool esc = (orabs >> 15) != 0;
-  uint32_t nout_lane = 0;
-  if (__any_sync(0xffffffffu, esc)) {       // rare: some |residual| >= 2^15
-#pragma unroll
-    for (int e = 0; e < 64; ++e) nout_lane += (uint32_t)abs(v[e]) > 32767u;
-    pack_codes(v, w, true);
-  }
-  __syncwarp();                             // every lane is done with the box
-  transpose32(w);                           // lane g now holds out[32b+g]
-
-  // ---- plane buffer: word (b, g) -> lane b gets plane b's 32 words
-  uint32_t *pb = reinterpret_cast<uint32_t *>(piece_a);       // 4 KB
-#pragma unroll
-  for (int b = 0; b < 32; ++b) pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)] = w[b];
-  __syncwarp();
-  uint4 blk[8];
-  uint32_t F = 0;                           // lane b: flag byte of plane b
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    blk[i] = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
-    F |= ((blk[i].x | blk[i].y | blk[i].z | blk[i].w) != 0u ? 1u : 0u) << i;
-  }
-  const uint32_t pc = __popc(F);
-  uint32_t P = pc;                          // inclusive scan over lanes
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, P, o);
-    if (g >= o) P += y;
-  }
-  const uint32_t tile_nnz = __shfl_sync(0xffffffffu, P, 31);
-  P -= pc;                                  // exclusive
-  const uint64_t tile = c * kTilesPerChunk + t;
-  a.out[64 + tile * 32 + g] = (uint8_t)F;   // flag byte b = plane b (Listing 1)
-  const uint32_t tile_nout = __reduce_add_sync(0xffffffffu, nout_lane);
-  if (g == 0) { sh[1 + t] = tile_nnz; sh[5 + t] = tile_nout; }
-  __syncthreads();                          // (B) all halos read, counts known
-
-  // ---- compaction into this warp's second piece (Listing 2:
-  // block k goes to PreSum[k] when it is non-zero)
-  uint4 *cb = reinterpret_cast<uint4 *>(piece_b);
-  {
-    uint32_t rank = P;
+  const uint32_t tile_nnz = (uint32_t)(d.agg >> 32);
+  uint64_t dst = pay + 16 * ((excl >> 32) + d.P);
+  if (pay + 16 * ((excl >> 32) + tile_nnz) <= a.out_capacity) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      if ((F >> i) & 1u) { cb[rank] = blk[i]; ++rank; }
-    }
-  }
-
-  // ---- chunk totals, look-back (warp 0), offsets
-  uint32_t off_t = 0;
-  uint64_t agg = 0;
-#pragma unroll
-  for (int k = 0; k < kTilesPerChunk; ++k) {
-    if (k < t) off_t += sh[1 + k];
-    agg += ((uint64_t)sh[1 + k] << 32) | sh[5 + k];
-  }
-  if (t == 0) {
-    const bool publish = c != a.skip_publish_chunk;
-    uint64_t excl = lookback(a.status_cur, c, agg, publish, &cur->err,
-                             a.wait_limit_ns);
-    if (g == 0) {
-      sh[10] = (uint32_t)excl;
-      sh[11] = (uint32_t)(excl >> 32);
-      a.chunk_out_prefix[c] = (uint32_t)excl;           // outlier prefix
-      a.chunk_out_count[c] = (uint32_t)agg;
-      if (c == a.n_chunks - 1) {
-        uint64_t inc = excl + agg;
-        StreamHeader *h = reinterpret_cast<StreamHeader *>(a.out);
-        h->nnz_blocks = (uint32_t)(inc >> 32);
-        h->n_outliers = (uint32_t)inc;
-        cur->nnz = inc >> 32;
-        cur->nout = inc & 0xffffffffull;
+      if ((d.F >> i) & 1u) {
+        const uint4 blk = *reinterpret_cast<const uint4 *>(d.pb + 32 * g + 4 * (i ^ (g & 7)));
+        __stcs(reinterpret_cast<uint4 *>(a.out + dst), blk);
+        dst += 16;
       }
     }
+  } else if (g == 0) {
+    atomicOr(&cur->err, kErrCapacity);
   }
-  __syncthreads();                          // (C)
-  const uint64_t base_blocks = sh[11];     // block part of the prefix
-  const uint64_t first = base_blocks + off_t;
-  const uint64_t pay = 64 + 32 * a.n_chunks * kTilesPerChunk;
-  if (tile_nnz > 0) {
-    const uint64_t end = pay + 16 * (first + tile_nnz);
-    if (end <= a.out_capacity) {
-      if (g == 0) {
-        fence_proxy_async_smem();
-        bulk_store(a.out + pay + 16 * first, cb, tile_nnz * 16);
-        bulk_commit();
-        bulk_wait_read_all();
-      }
-    } else if (g == 0) {
-      atomicOr(&cur->err, kErrCapacity);
-    }
-  }
-  (void)load_ok;
+  __syncwarp();                                      // plane buffer free again
 }
 
-// ====================================================================
-// outlier pass (only for chunks that escaped some residual)
-// ====================================================================
-template <int NDIM, bool TMA>
-__global__ void __launch_bounds__(kThreads, 4)
-    outlier_kernel(const CompressArgs a, const __grid_constant__ CUtensorMap tmap,
-                   uint64_t out_section) {
+template <int NDIM, int V, bool CHECK, bool TMA>
+__global__ void __launch_bounds__(kCompWarps * 32, 3)
+    compress_kernel(const CompressArgs a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t *box = smem;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kBoxBytes);
-  uint32_t *sh = reinterpret_cast<uint32_t *>(smem + kBoxBytes + 16);
-  const int tid = threadIdx.x, t = tid >> 5, g = tid & 31;
-  const uint64_t c = blockIdx.x;
-  if (a.chunk_out_count[c] == 0) return;
-  if (tid == 0) {
-    float fmin = 0.f, fmax = 0.f;
-    if (a.mode == 1) { fmin = a.range->fmin; fmax = a.range->fmax; }
-    EbParams p = derive_eb(a.mode, a.eb_req, fmin, fmax);
-    sh[13] = __float_as_uint(p.ebx2_r);
-    if (TMA) mbar_init(bar, 1);
+  const unsigned full = 0xffffffffu;
+  const int g = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // per warp: [TMA box 8 KB] (TMA only) [plane buffer 0][plane buffer 1]
+  constexpr int stride = TMA ? kBoxStride : 8192;
+  uint8_t *box = smem + wid * stride;
+  uint32_t *pbs[2] = {reinterpret_cast<uint32_t *>(box + (TMA ? kPlaneOff : 0)),
+                      reinterpret_cast<uint32_t *>(box + (TMA ? kPlaneOff : 0) + 4096)};
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kCompWarps * stride) + wid;
+  SetScratch *cur = a.set_cur;
+  const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
+  const uint64_t pay = 64 + 32 * n_tiles;
+
+  float fmin = 0.f, fmax = 0.f;
+  bool nonfinite = false;
+  if (a.mode == 1) {
+    fmin = a.range->fmin; fmax = a.range->fmax;
+    nonfinite = a.range->nonfinite != 0;
   }
-  __syncthreads();
-  const float r = __uint_as_float(sh[13]);
-  const uint32_t cx = (uint32_t)(c % a.ncx);
-  const uint32_t cy = (uint32_t)((c / a.ncx) % a.ncy);
-  const uint32_t cz = (uint32_t)(c / ((uint64_t)a.ncx * a.ncy));
+  const EbParams p = derive_eb(a.mode, a.eb_req, fmin, fmax);
+  bool ok = p.ok && !nonfinite;
+  if (ok && a.mode == 1) {
+    // relative bound: the element of largest magnitude is in the field, so
+    // checking it checks every element (fp multiply and rounding are monotone)
+    const float m = fmaxf(fabsf(fmin), fabsf(fmax));
+    const uint32_t b = (uint32_t)quant_bits(m, p.ebx2_r) - kBiasBits;
+    ok = b <= kBiasedMax;
+    if (!ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&cur->err, kErrRange);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!p.ok) atomicOr(&cur->err, kErrEbParam);
+    if (nonfinite) atomicOr(&cur->err, kErrNonFinite);
+    SetScratch *nx = a.set_next;                     // the next call's block
+    nx->ticket = 0; nx->err = 0; nx->nnz = 0; nx->nout = 0;
+    nx->n_chunks = 0; nx->hdr_nout = 0;
+  }
+  if (!ok) return;                                   // the same in every warp
+
+  uint64_t T = 0;
+  if (g == 0) T = atomicAdd(&cur->ticket, 1u);
+  T = __shfl_sync(full, T, 0);
+  uint32_t phase = 0;
   if constexpr (TMA) {
-    if (tid == 0) {
-      mbar_expect_tx(bar, kBoxBytes);
-      if constexpr (NDIM == 3) {
-        tma_load_3d(box, &tmap, bar, (int)(cx * 32), (int)(cy * 32), (int)(cz * 8));
-      } else {
-        tma_load_2d(box, &tmap, bar, (int)(cx * 64), (int)(cy * 128));
-        tma_load_2d(box + 16384, &tmap, bar, (int)(cx * 64 + 32), (int)(cy * 128));
-      }
+    if (g == 0) {
+      mbar_init(bar, 1);
+      if (T < n_tiles) issue_box<NDIM>(a, &tmap, box, bar, T);
     }
-    if (!mbar_wait_bounded(bar, 0, a.wait_limit_ns) && g == 0)
-      atomicOr(&a.set_cur->err, kErrTimeout);
-  } else {
-    fill_box_generic<NDIM>(a, box, cx, cy, cz);
-    __syncthreads();
+    __syncwarp();
   }
-  int32_t *xch_own = reinterpret_cast<int32_t *>(smem + kBoxBytes + 1024 + t * 4096);
-  const int32_t *xch_prev = reinterpret_cast<const int32_t *>(
-      smem + kBoxBytes + 1024 + (t > 0 ? t - 1 : 0) * 4096);
+  Pending prev{n_tiles, 0, 0, 0, pbs[1]};
+  int buf = 0;
+  while (T < n_tiles) {
+    // the next ticket is requested now; its round trip overlaps this tile
+    uint64_t T_next = 0;
+    if (g == 0) {
+      T_next = atomicAdd(&cur->ticket, 1u);
+      a.status_next[T * kStatusStride] = 0;          // for the next call
+    }
+    const TileGeo q = tile_geo<NDIM>(a, T, g);
+    float hf[32];
+    load_halo<NDIM, V>(a, q, hf);
+    int32_t v[64];
+    uint32_t qmax = 0;
+    if constexpr (TMA) {
+      if (!mbar_wait_bounded(bar, phase, a.wait_limit_ns) && g == 0)
+        atomicOr(&cur->err, kErrTimeout);
+      phase ^= 1u;
+      residuals_first<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, g, p.ebx2_r, hf, v, qmax);
+      // the box is consumed: fetch the next tile into it while this one is
+      // finished (generic-proxy reads of the box precede the async write)
+      __syncwarp();
+      T_next = __shfl_sync(full, T_next, 0);
+      if (g == 0 && T_next < n_tiles) {
+        fence_proxy_async_smem();
+        issue_box<NDIM>(a, &tmap, box, bar, T_next);
+      }
+    } else {
+      residuals_first<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, g, p.ebx2_r, hf, v, qmax);
+      T_next = __shfl_sync(full, T_next, 0);
+    }
+    residuals_rest<NDIM>(a, q, g, p.ebx2_r, v);
+    if (CHECK && __any_sync(full, qmax > kBiasedMax) && g == 0) atomicOr(&cur->err, kErrRange);
+
+    uint32_t w[32];
+    const uint32_t orabs = pack_codes(v, w);         // v is dead from here on
+    uint32_t nout_lane = 0;
+    if (__any_sync(full, (orabs >> 15) != 0)) {
+      // rare: some |residual| needs more than 15 bits; recompute the
+      // residuals (cheaper than keeping them live) and repack with escapes
+      int32_t v2[64];
+      residuals_global<NDIM, V>(a, T, g, p.ebx2_r, v2);
+      nout_lane = pack_codes_escaped(v2, w);
+    }
+    transpose32(w);                                  // lane g: out[32b + g]
+
+    // plane buffer: lane b collects plane b's 32 words (8 blocks)
+    uint32_t *pb = pbs[buf];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)] = w[b];
+    __syncwarp();
+    uint32_t F = 0;                                  // lane b: flag byte of plane b
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint4 blk = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
+      F |= ((blk.x | blk.y | blk.z | blk.w) != 0u ? 1u : 0u) << i;
+    }
+    const uint32_t pc = __popc(F);
+    uint32_t P = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(full, P, o);
+      if (g >= o) P += y;
+    }
+    const uint32_t tile_nnz = __shfl_sync(full, P, 31);
+    P -= pc;
+    const uint32_t tile_nout = __reduce_add_sync(full, nout_lane);
+    a.out[64 + T * 32 + g] = (uint8_t)F;             // Listing 1's flags
+    const uint64_t agg = ((uint64_t)tile_nnz << 32) | tile_nout;
+    publish_aggregate(a.status_cur, T, agg, (T >> 2) != a.skip_publish_chunk);
+
+    // the previous tile's prefix has had a whole tile's time to settle
+    if (prev.T < n_tiles) finish_tile<NDIM>(a, prev, p, fmin, fmax, n_tiles, pay, g);
+    prev = Pending{T, agg, F, P, pb};
+    buf ^= 1;
+    T = T_next;
+  }
+  if (prev.T < n_tiles) finish_tile<NDIM>(a, prev, p, fmin, fmax, n_tiles, pay, g);
+}
+
+// ====================================================================
+// outlier pass (only tiles that escaped some residual)
+// ====================================================================
+template <int NDIM, int V>
+__global__ void __launch_bounds__(kCompWarps * 32)
+    outlier_kernel(const CompressArgs a, uint64_t out_section) {
+  const int g = threadIdx.x & 31;
+  const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
+  const uint64_t T = (uint64_t)blockIdx.x * kCompWarps + (threadIdx.x >> 5);
+  if (T >= n_tiles || a.tile_out_count[T] == 0) return;
+  float fmin = 0.f, fmax = 0.f;
+  if (a.mode == 1) { fmin = a.range->fmin; fmax = a.range->fmax; }
+  const EbParams p = derive_eb(a.mode, a.eb_req, fmin, fmax);
   int32_t v[64];
-  uint32_t qmax = 0;
-  compute_residuals<NDIM>(a, box, xch_prev, xch_own, r, cx, cy, cz, t, g, v, qmax,
-                          chunk_is_edge<NDIM>(a, cx, cy, cz), true);
+  residuals_global<NDIM, V>(a, T, g, p.ebx2_r, v);
   uint32_t cnt = 0;
 #pragma unroll
   for (int e = 0; e < 64; ++e) cnt += (uint32_t)abs(v[e]) > 32767u;
-  // exclusive scan of the counts in (tile, lane) = stream order
   uint32_t inc = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
     if (g >= o) inc += y;
   }
-  if (g == 31) sh[1 + t] = inc;
-  __syncthreads();
-  uint32_t before = inc - cnt;
-  for (int k = 0; k < t; ++k) before += sh[1 + k];
-  uint64_t pos = (uint64_t)a.chunk_out_prefix[c] + before;
-  const uint64_t tile = c * kTilesPerChunk + t;
+  uint64_t pos = (uint64_t)a.tile_out_prefix[T] + inc - cnt;
 #pragma unroll
   for (int e = 0; e < 64; ++e) {
     if ((uint32_t)abs(v[e]) > 32767u) {
       const uint64_t at = out_section + 8 * pos;
       if (at + 8 <= a.out_capacity) {
-        uint2 rec = make_uint2((uint32_t)(tile * kTileCodes + 64 * g + e), (uint32_t)v[e]);
-        *reinterpret_cast<uint2 *>(a.out + at) = rec;
+        *reinterpret_cast<uint2 *>(a.out + at) =
+            make_uint2((uint32_t)(T * kTileCodes + 64 * g + e), (uint32_t)v[e]);
       } else {
         atomicOr(&a.set_cur->err, kErrCapacity);
       }
@@ -691,39 +680,122 @@ void launch_range(const float *x, uint64_t n, float2 *partial, int nblocks,
   range_kernel<<<nblocks, 256, 0, s>>>(x, n, partial, res);
 }
 
-size_t compress_smem_bytes() { return kBoxBytes + 1024 + 4 * 4096 + 1024; }
+// loads: 32-byte rows when every brick row starts on a 32-byte boundary,
+// 16-byte when on 16, else scalar
+static int vec_width(const CompressArgs &a) {
+  const uintptr_t p = reinterpret_cast<uintptr_t>(a.x);
+  if (a.dims[0] % 8 == 0 && p % 32 == 0) return 8;
+  if (a.dims[0] % 4 == 0 && p % 16 == 0) return 4;
+  return 1;
+}
 
-template <int NDIM, bool TMA>
-static cudaError_t launch_c(const CompressArgs &a, const CUtensorMap &tm,
-                            cudaStream_t s, bool outliers, uint64_t out_section) {
-  const size_t smem = compress_smem_bytes();
-  if (!outliers) {
-    auto k = compress_kernel<NDIM, TMA>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int NDIM, int V, bool CHECK, bool TMA>
+static cudaError_t launch_c3(const CompressArgs &a, const CUtensorMap &tm, int sms,
+                             cudaStream_t s) {
+  auto k = compress_kernel<NDIM, V, CHECK, TMA>;
+  const int smem = TMA ? kCompSmemTma : kCompSmemLdg;
+  static int per_sm = 0;                    // resident blocks per SM, once
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k<<<(unsigned)a.n_chunks, kThreads, smem, s>>>(a, tm);
-  } else {
-    auto k = outlier_kernel<NDIM, TMA>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kCompWarps * 32, smem);
     if (e != cudaSuccess) return e;
-    k<<<(unsigned)a.n_chunks, kThreads, smem, s>>>(a, tm, out_section);
+    per_sm = n > 0 ? n : 1;
+  }
+  k<<<sms * per_sm, kCompWarps * 32, smem, s>>>(a, tm);
+  return cudaGetLastError();
+}
+
+template <int NDIM, int V, bool CHECK>
+static cudaError_t launch_c2(const CompressArgs &a, const CUtensorMap *tm, int sms,
+                             cudaStream_t s) {
+  if constexpr (NDIM >= 2 && V >= 4) {
+    if (tm) return launch_c3<NDIM, V, CHECK, true>(a, *tm, sms, s);
+  }
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  return launch_c3<NDIM, V, CHECK, false>(a, none, sms, s);
+}
+
+template <int NDIM, int V>
+static cudaError_t launch_c1(const CompressArgs &a, const CUtensorMap *tm, int sms,
+                             cudaStream_t s) {
+  return a.mode == 0 ? launch_c2<NDIM, V, true>(a, tm, sms, s)
+                     : launch_c2<NDIM, V, false>(a, tm, sms, s);
+}
+
+template <int NDIM>
+static cudaError_t launch_c0(const CompressArgs &a, const CUtensorMap *tm, int sms,
+                             cudaStream_t s) {
+  switch (vec_width(a)) {
+    case 8: return launch_c1<NDIM, 8>(a, tm, sms, s);
+    case 4: return launch_c1<NDIM, 4>(a, tm, sms, s);
+    default: return launch_c1<NDIM, 1>(a, nullptr, sms, s);
+  }
+}
+
+// The field's tensor map for the per-warp TMA boxes: 3-D box {32,32,2} (a
+// tile's two planes), 2-D box {32,32} (one x half of a tile's 32 rows);
+// 128-byte swizzle, zero fill outside the field.  cuTensorMapEncodeTiled comes from the driver
+// through the runtime's entry-point query (no link-time libcuda).
+bool encode_field_tmap(int ndim, const uint64_t dims[3], const float *x, CUtensorMap *tm) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                         cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  if (!enc || ndim < 2) return false;
+  cuuint64_t gdim[3] = {dims[0], dims[1], dims[2]};
+  cuuint64_t gstr[2] = {dims[0] * 4, dims[0] * dims[1] * 4};
+  cuuint32_t estr[3] = {1, 1, 1};
+  cuuint32_t box3[3] = {32, 32, 2}, box2[2] = {32, 32};
+  const CUresult r =
+      enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ndim == 3 ? 3 : 2, const_cast<float *>(x), gdim,
+          gstr, ndim == 3 ? box3 : box2, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// FZ_LOAD_PATH=ldg in the environment (read once) selects the direct-load
+// variant even where TMA applies; used to compare the two load paths.
+bool compress_uses_tma(int ndim, const CompressArgs &a) {
+  static const bool ldg_only = [] {
+    const char *e = getenv("FZ_LOAD_PATH");
+    return e && strcmp(e, "ldg") == 0;
+  }();
+  return !ldg_only && ndim >= 2 && vec_width(a) >= 4;
+}
+
+cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *tm, int sms,
+                            cudaStream_t s) {
+  if (ndim == 3) return launch_c0<3>(a, tm, sms, s);
+  if (ndim == 2) return launch_c0<2>(a, tm, sms, s);
+  return launch_c0<1>(a, nullptr, sms, s);
+}
+
+template <int NDIM>
+static cudaError_t launch_o(const CompressArgs &a, uint64_t out_section, cudaStream_t s) {
+  const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
+  const unsigned blocks = (unsigned)((n_tiles + kCompWarps - 1) / kCompWarps);
+  switch (vec_width(a)) {
+    case 8: outlier_kernel<NDIM, 8><<<blocks, kCompWarps * 32, 0, s>>>(a, out_section); break;
+    case 4: outlier_kernel<NDIM, 4><<<blocks, kCompWarps * 32, 0, s>>>(a, out_section); break;
+    default: outlier_kernel<NDIM, 1><<<blocks, kCompWarps * 32, 0, s>>>(a, out_section); break;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_compress(int ndim, bool tma, const CompressArgs &a,
-                            const CUtensorMap &tm, cudaStream_t s) {
-  if (ndim == 3) return tma ? launch_c<3, true>(a, tm, s, false, 0) : launch_c<3, false>(a, tm, s, false, 0);
-  if (ndim == 2) return tma ? launch_c<2, true>(a, tm, s, false, 0) : launch_c<2, false>(a, tm, s, false, 0);
-  return launch_c<1, false>(a, tm, s, false, 0);
-}
-
-cudaError_t launch_outliers(int ndim, bool tma, const CompressArgs &a,
-                            const CUtensorMap &tm, uint64_t out_section,
+cudaError_t launch_outliers(int ndim, const CompressArgs &a, uint64_t out_section,
                             cudaStream_t s) {
-  if (ndim == 3) return tma ? launch_c<3, true>(a, tm, s, true, out_section) : launch_c<3, false>(a, tm, s, true, out_section);
-  if (ndim == 2) return tma ? launch_c<2, true>(a, tm, s, true, out_section) : launch_c<2, false>(a, tm, s, true, out_section);
-  return launch_c<1, false>(a, tm, s, true, out_section);
+  if (ndim == 3) return launch_o<3>(a, out_section, s);
+  if (ndim == 2) return launch_o<2>(a, out_section, s);
+  return launch_o<1>(a, out_section, s);
 }
 
 }  // namespace fz

@@ -3,12 +3,13 @@
 //
 // Persistent warps; each warp takes chunks from a ticket counter in stream
 // order and for each chunk:
-//   flags -> popcounts -> warp-level decoupled look-back (payload offset)
-//   per tile: gather the non-zero 16-byte blocks (Listing 2 backwards),
-//   inverse bitshuffle (the same register transpose), sign-magnitude decode,
-//   outlier patch (rare), chunk-local inverse Lorenzo as prefix sums along
-//   x and y (in-register + warp scans) and z/y across tiles (a carried
-//   plane/row), q * 2eb, stores.
+//   flags -> popcounts -> warp-level decoupled look-back (payload offset);
+//   all four tiles' non-zero 16-byte blocks are copied at once with
+//   asynchronous zero-filling copies into per-warp plane buffers (Listing 2
+//   backwards), then per tile: escape detection on the bit planes, inverse
+//   bitshuffle (the register transpose), sign-magnitude decode, outlier
+//   patch (rare), chunk-local inverse Lorenzo as prefix sums (in-register and
+//   warp scans, a carried plane/row across tiles), q * 2eb, 32-byte stores.
 // The header is validated on the device, so the call needs no host read of
 // the stream before the launch.
 #include <cuda_runtime.h>
@@ -17,6 +18,9 @@
 #include "fz_kernels.h"
 
 namespace fz {
+
+constexpr int kDecWarps = 4;
+constexpr int kDecSmemBytes = kDecWarps * kTilesPerChunk * 4096;
 
 struct Hdr {
   int ndim, mode;
@@ -88,19 +92,40 @@ __device__ __noinline__ bool find_outlier(const uint2 *rec, uint64_t lo, uint64_
   return true;
 }
 
-// decode 32 packed code pairs to residuals; escapes (0x8000) decode to 0 and
-// set the returned flag
-__device__ __forceinline__ bool decode_codes(const uint32_t (&w)[32], int32_t (&v)[64]) {
-  uint32_t esc = 0;
+// 16-byte asynchronous copy global -> shared; with `bytes` = 0 nothing is
+// read and the destination is zero-filled
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)),
+               "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// PRMT with sign-replicating selectors (a selector nibble with its msb set
+// copies the sign bit of the chosen byte into all 8 bits); the CUDA
+// intrinsic __byte_perm masks that bit off, hence the inline PTX.
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t x, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(0u), "r"(sel));
+  return r;
+}
+
+// decode 32 packed sign-magnitude pairs to residuals (an escape, 0x8000,
+// decodes to 0 and is patched later)
+__device__ __forceinline__ void decode_codes(const uint32_t (&w)[32], int32_t (&v)[64]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
-    uint32_t c0 = w[i] & 0xFFFFu, c1 = w[i] >> 16;
-    esc |= (c0 == 0x8000u) | (c1 == 0x8000u);
-    int32_t s0 = -(int32_t)(c0 >> 15), s1 = -(int32_t)(c1 >> 15);
-    v[2 * i] = ((int32_t)(c0 & 0x7FFFu) ^ s0) - s0;
-    v[2 * i + 1] = ((int32_t)(c1 & 0x7FFFu) ^ s1) - s1;
+    const uint32_t s0 = prmt_sign(w[i], 0x9999);   // sign of the low code, replicated
+    const uint32_t s1 = prmt_sign(w[i], 0xBBBB);   // sign of the high code
+    v[2 * i] = (int32_t)(((w[i] & 0x7FFFu) ^ s0) - s0);
+    v[2 * i + 1] = (int32_t)((((w[i] >> 16) & 0x7FFFu) ^ s1) - s1);
   }
-  return esc != 0;
 }
 
 // position of brick element e of lane g in tile t of chunk (cx,cy,cz)
@@ -127,7 +152,7 @@ template <int NDIM>
 __device__ __forceinline__ void inverse_lorenzo(int32_t (&v)[64], int32_t (&carry)[32], int g) {
   using G = Geo<NDIM>;
   const unsigned full = 0xffffffffu;
-  const int bx = g % G::NBX, by = g / G::NBX;
+  const int bx = g % G::NBX;
   if constexpr (NDIM == 3) {
     // S_x: rows of 8, then an exclusive scan of row totals over the 4 bx lanes
 #pragma unroll
@@ -138,7 +163,7 @@ __device__ __forceinline__ void inverse_lorenzo(int32_t (&v)[64], int32_t (&carr
       int32_t inc = tot;
 #pragma unroll
       for (int o = 1; o < 4; o <<= 1) {
-        int32_t y = __shfl_up_sync(full, inc, o);
+        const int32_t y = __shfl_up_sync(full, inc, o);
         if (bx >= o) inc += y;
       }
       const int32_t ex = inc - tot;
@@ -156,7 +181,7 @@ __device__ __forceinline__ void inverse_lorenzo(int32_t (&v)[64], int32_t (&carr
         int32_t inc = tot;
 #pragma unroll
         for (int o = 4; o < 32; o <<= 1) {
-          int32_t y = __shfl_up_sync(full, inc, o);
+          const int32_t y = __shfl_up_sync(full, inc, o);
           if (g >= o) inc += y;
         }
         const int32_t ex = inc - tot;
@@ -172,32 +197,30 @@ __device__ __forceinline__ void inverse_lorenzo(int32_t (&v)[64], int32_t (&carr
       carry[e] = v[e + 32];
     }
   } else if constexpr (NDIM == 2) {
-    // S_x over 8 bx lanes
 #pragma unroll
-    for (int row = 0; row < 8; ++row) {
+    for (int row = 0; row < 8; ++row) {                 // S_x over 8 bx lanes
 #pragma unroll
       for (int ix = 1; ix < 8; ++ix) v[ix + 8 * row] += v[ix - 1 + 8 * row];
       const int32_t tot = v[7 + 8 * row];
       int32_t inc = tot;
 #pragma unroll
       for (int o = 1; o < 8; o <<= 1) {
-        int32_t y = __shfl_up_sync(full, inc, o);
+        const int32_t y = __shfl_up_sync(full, inc, o);
         if (bx >= o) inc += y;
       }
       const int32_t ex = inc - tot;
 #pragma unroll
       for (int ix = 0; ix < 8; ++ix) v[ix + 8 * row] += ex;
     }
-    // S_y over 4 by lanes (lane stride 8), plus the previous tile's last row
 #pragma unroll
-    for (int ix = 0; ix < 8; ++ix) {
+    for (int ix = 0; ix < 8; ++ix) {                    // S_y over 4 by lanes
 #pragma unroll
       for (int iy = 1; iy < 8; ++iy) v[ix + 8 * iy] += v[ix + 8 * (iy - 1)];
       const int32_t tot = v[ix + 56];
       int32_t inc = tot;
 #pragma unroll
       for (int o = 8; o < 32; o <<= 1) {
-        int32_t y = __shfl_up_sync(full, inc, o);
+        const int32_t y = __shfl_up_sync(full, inc, o);
         if (g >= o) inc += y;
       }
       const int32_t ex = inc - tot + carry[ix];
@@ -212,7 +235,7 @@ __device__ __forceinline__ void inverse_lorenzo(int32_t (&v)[64], int32_t (&carr
     int32_t inc = tot;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int32_t y = __shfl_up_sync(full, inc, o);
+      const int32_t y = __shfl_up_sync(full, inc, o);
       if (g >= o) inc += y;
     }
     const int32_t ex = inc - tot + carry[0];
@@ -222,46 +245,45 @@ __device__ __forceinline__ void inverse_lorenzo(int32_t (&v)[64], int32_t (&carr
   }
 }
 
+// q (biased by the float bits of 1.5*2^23, which the chunk origin carries)
+// -> fl(float(q) * 2eb), stored row by row (8 floats per row)
 template <int NDIM>
 __device__ __forceinline__ void store_brick(const DecompressArgs &a, const Hdr &h,
-                                            const int32_t (&q)[64], uint64_t cx,
-                                            uint64_t cy, uint64_t cz, int t, int g,
-                                            bool edge, bool vec) {
-  using G = Geo<NDIM>;
+                                            const int32_t (&q)[64], uint64_t cx, uint64_t cy,
+                                            uint64_t cz, int t, int g, bool edge, int vw) {
   const float e2 = h.ebx2;
   const uint64_t X = h.dims[0], Y = h.dims[1];
-  float f[64];
 #pragma unroll
-  for (int e = 0; e < 64; ++e) {
-    // (float)q exactly for |q| < 2^22, then the stream's one multiply
-    float qf = __fsub_rn(__int_as_float(q[e] + (int32_t)kMagicBits), kRoundMagic);
-    f[e] = __fmul_rn(qf, e2);
-  }
+  for (int row = 0; row < 8; ++row) {
+    float f[8];
 #pragma unroll
-  for (int row = 0; row < 64 / G::BX; ++row) {
+    for (int k = 0; k < 8; ++k)
+      f[k] = __fmul_rn(__fsub_rn(__int_as_float(q[8 * row + k]), kRoundMagic), e2);
     uint64_t x0, y, z;
-    elem_coord<NDIM>(cx, cy, cz, t, g, row * G::BX, x0, y, z);
+    elem_coord<NDIM>(cx, cy, cz, t, g, 8 * row, x0, y, z);
     float *dst = a.out + x0 + X * (y + Y * z);
-    const bool full_row = !edge || (x0 + G::BX <= X && y < Y && z < h.dims[2]);
-    if (vec && full_row) {
-#pragma unroll
-      for (int k = 0; k < G::BX / 4; ++k)
-        __stcs(reinterpret_cast<float4 *>(dst) + k,
-               make_float4(f[row * G::BX + 4 * k], f[row * G::BX + 4 * k + 1],
-                           f[row * G::BX + 4 * k + 2], f[row * G::BX + 4 * k + 3]));
+    const bool full_row = !edge || (x0 + 8 <= X && y < Y && z < h.dims[2]);
+    if (full_row && vw == 8) {
+      asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst),
+                   "f"(f[0]), "f"(f[1]), "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]),
+                   "f"(f[6]), "f"(f[7])
+                   : "memory");
+    } else if (full_row && vw == 4) {
+      __stcs(reinterpret_cast<float4 *>(dst), make_float4(f[0], f[1], f[2], f[3]));
+      __stcs(reinterpret_cast<float4 *>(dst) + 1, make_float4(f[4], f[5], f[6], f[7]));
     } else if (full_row) {
 #pragma unroll
-      for (int k = 0; k < G::BX; ++k) __stcs(dst + k, f[row * G::BX + k]);
+      for (int k = 0; k < 8; ++k) __stcs(dst + k, f[k]);
     } else if (y < Y && z < h.dims[2]) {
 #pragma unroll
-      for (int k = 0; k < G::BX; ++k)
-        if (x0 + k < X) __stcs(dst + k, f[row * G::BX + k]);
+      for (int k = 0; k < 8; ++k)
+        if (x0 + k < X) __stcs(dst + k, f[k]);
     }
   }
 }
 
 template <int NDIM>
-__device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_t *pb,
+__device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_t *pbuf,
                                   SetScratch *cur) {
   using G = Geo<NDIM>;
   const unsigned full = 0xffffffffu;
@@ -269,23 +291,55 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
   const uint8_t *flags = a.in + 64;
   const uint8_t *payload = flags + 32 * h.n_tiles;
   const uint2 *recs = reinterpret_cast<const uint2 *>(payload + 16 * h.nnz);
-  const bool vec = ((h.dims[0] & 3u) == 0) && ((reinterpret_cast<uintptr_t>(a.out) & 15u) == 0);
+  const uintptr_t op = reinterpret_cast<uintptr_t>(a.out);
+  const int vw = (h.dims[0] % 8 == 0 && op % 32 == 0) ? 8
+                 : (h.dims[0] % 4 == 0 && op % 16 == 0) ? 4 : 1;
   while (true) {
     uint64_t c = 0;
     if (g == 0) c = atomicAdd(&cur->ticket, 1u);
     c = __shfl_sync(full, c, 0);
     if (c >= h.n_chunks) break;
-    if (g == 0) a.status_next[c] = 0;
+    if (g == 0) a.status_next[c * kStatusStride] = 0;
     const uint64_t cx = c % h.ncx, cy = (c / h.ncx) % h.ncy, cz = c / (h.ncx * h.ncy);
     // flags of the chunk's 4 tiles: lane l holds word l
     const uint32_t fw = __ldg(reinterpret_cast<const uint32_t *>(flags + 128 * c) + g);
-    const uint32_t pcw = __popc(fw);
-    const uint32_t chunk_cnt = __reduce_add_sync(full, pcw);
+    const uint32_t chunk_cnt = __reduce_add_sync(full, (uint32_t)__popc(fw));
     const bool publish = c != a.skip_publish_chunk;
     const uint64_t excl = lookback(a.status_cur, c, (uint64_t)chunk_cnt << 32, publish,
                                    &cur->err, a.wait_limit_ns) >> 32;
     if (c == h.n_chunks - 1 && g == 0 && excl + chunk_cnt != h.nnz)
       atomicOr(&cur->err, kErrCorrupt);
+
+    // gather all four tiles: lane b copies plane b's present blocks (Listing
+    // 2 backwards: block k of the tile comes from payload[PreSum[k]])
+    uint64_t base = excl;
+    bool oob = false;
+#pragma unroll
+    for (int t = 0; t < kTilesPerChunk; ++t) {
+      const uint32_t F = (__shfl_sync(full, fw, 8 * t + (g >> 2)) >> (8 * (g & 3))) & 0xFFu;
+      const uint32_t pc = __popc(F);
+      uint32_t P = pc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(full, P, o);
+        if (g >= o) P += y;
+      }
+      const uint32_t tile_cnt = __shfl_sync(full, P, 31);
+      uint64_t rank = base + P - pc;
+      uint32_t *dst = pbuf + 1024 * t + 32 * g;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const bool present = (F >> i) & 1u;
+        const bool valid = present && rank < h.nnz;
+        oob |= present && !valid;
+        cp_async16(dst + 4 * (i ^ (g & 7)), payload + 16 * (valid ? rank : 0), valid ? 16u : 0u);
+        rank += present;
+      }
+      cp_async_commit();
+      base += tile_cnt;
+    }
+    if (oob) atomicOr(&cur->err, kErrCorrupt);
+
     // outliers of this chunk (rare path)
     uint64_t o_lo = 0, o_hi = 0;
     if (h.nout) {
@@ -302,44 +356,29 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
     int32_t carry[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) carry[e] = 0;
-    uint64_t tile_base = excl;
 #pragma unroll 1
     for (int t = 0; t < kTilesPerChunk; ++t) {
-      // lane b: flag byte of plane b
-      const uint32_t F = (__shfl_sync(full, fw, 8 * t + (g >> 2)) >> (8 * (g & 3))) & 0xFFu;
-      const uint32_t pc = __popc(F);
-      uint32_t P = pc;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(full, P, o);
-        if (g >= o) P += y;
+      switch (t) {
+        case 0: cp_async_wait<3>(); break;
+        case 1: cp_async_wait<2>(); break;
+        case 2: cp_async_wait<1>(); break;
+        default: cp_async_wait<0>(); break;
       }
-      P -= pc;
-      // gather plane b's blocks into the plane buffer
-      uint32_t rank = P;
-      bool oob = false;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if ((F >> i) & 1u) {
-          const uint64_t bi = tile_base + rank;
-          if (bi < h.nnz) val = __ldcs(reinterpret_cast<const uint4 *>(payload) + bi);
-          else oob = true;
-          ++rank;
-        }
-        *reinterpret_cast<uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7))) = val;
-      }
-      if (oob) atomicOr(&cur->err, kErrCorrupt);
       __syncwarp();
+      const uint32_t *pb = pbuf + 1024 * t;
       uint32_t w[32];
 #pragma unroll
       for (int b = 0; b < 32; ++b) w[b] = pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)];
-      __syncwarp();
-      tile_base += __reduce_add_sync(full, (g >> 3) == t ? pcw : 0u);
+      // an escape (0x8000) has its sign plane set and every magnitude plane
+      // clear: find them on the planes, before the transpose
+      uint32_t lo_or = 0, hi_or = 0;
+#pragma unroll
+      for (int b = 0; b < 15; ++b) { lo_or |= w[b]; hi_or |= w[b + 16]; }
+      const uint32_t esc_even = w[15] & ~lo_or, esc_odd = w[31] & ~hi_or;
       transpose32(w);                    // lane g: the 32 code words of brick g
       int32_t v[64];
-      const bool esc = decode_codes(w, v);
-      if (__any_sync(full, esc || edge)) {
+      decode_codes(w, v);
+      if (__any_sync(full, (esc_even | esc_odd) != 0 || edge)) {
         // rare path: patch escapes from the outlier list; padding must be 0.
         // Fully unrolled so that v and w stay in registers.
         const uint64_t tile = c * kTilesPerChunk + t;
@@ -363,9 +402,12 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
         }
         if (bad) atomicOr(&cur->err, kErrCorrupt);
       }
+      // the chunk origin carries the float bias of 1.5*2^23 into every q
+      if (t == 0 && g == 0) v[0] += (int32_t)kMagicBits;
       inverse_lorenzo<NDIM>(v, carry, g);
-      store_brick<NDIM>(a, h, v, cx, cy, cz, t, g, edge, vec);
+      store_brick<NDIM>(a, h, v, cx, cy, cz, t, g, edge, vw);
     }
+    __syncwarp();                        // plane buffers free for the next chunk
     if (h.nout) {
       const uint32_t m = __reduce_add_sync(full, matched);
       if (g == 0) {
@@ -376,10 +418,10 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 3) decompress_kernel(const DecompressArgs a) {
-  __shared__ __align__(16) uint32_t plane_buf[kThreads / 32][1024];
+__global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const DecompressArgs a) {
+  extern __shared__ __align__(16) uint32_t dsmem[];
   SetScratch *cur = a.set_cur;
-  const int w = threadIdx.x >> 5, g = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
   const Hdr h = read_header(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     SetScratch *nx = a.set_next;
@@ -392,22 +434,27 @@ __global__ void __launch_bounds__(kThreads, 3) decompress_kernel(const Decompres
     cur->hdr_nout = h.ok ? (uint32_t)h.nout : 0;
   }
   if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
-  uint32_t *pb = plane_buf[w];
-  if (h.ndim == 3) decompress_chunks<3>(a, h, pb, cur);
-  else if (h.ndim == 2) decompress_chunks<2>(a, h, pb, cur);
-  else decompress_chunks<1>(a, h, pb, cur);
-  (void)g;
+  uint32_t *pbuf = dsmem + w * kTilesPerChunk * 1024;
+  if (h.ndim == 3) decompress_chunks<3>(a, h, pbuf, cur);
+  else if (h.ndim == 2) decompress_chunks<2>(a, h, pbuf, cur);
+  else decompress_chunks<1>(a, h, pbuf, cur);
 }
 
 cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s) {
-  decompress_kernel<<<grid, kThreads, 0, s>>>(a);
+  cudaError_t e = cudaFuncSetAttribute(decompress_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kDecSmemBytes);
+  if (e != cudaSuccess) return e;
+  decompress_kernel<<<grid, kDecWarps * 32, kDecSmemBytes, s>>>(a);
   return cudaGetLastError();
 }
 
 int decompress_blocks_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decompress_kernel, kThreads, 0) !=
-      cudaSuccess)
+  cudaFuncSetAttribute(decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kDecSmemBytes);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decompress_kernel, kDecWarps * 32,
+                                                    kDecSmemBytes) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
 }

@@ -18,7 +18,6 @@ constexpr int kTileCodes = 2048;
 constexpr int kTilesPerChunk = 4;
 constexpr int kChunkCodes = kTileCodes * kTilesPerChunk;
 constexpr int kThreads = 128;            // 4 warps, warp t = tile t
-constexpr int kBoxBytes = kChunkCodes * 4;   // one chunk of fp32
 
 // quantiser constants.  fl(v + 1.5*2^23) rounds v to the nearest integer
 // (ties to even) in the low mantissa bits whenever |v| <= 2^22; the float's
@@ -38,7 +37,13 @@ constexpr uint32_t kErrCapacity = 8u;  // payload would pass out_capacity
 constexpr uint32_t kErrCorrupt = 16u;  // decompressor: inconsistent stream
 constexpr uint32_t kErrNonFinite = 32u;
 
-// look-back status word: [63:62] flag, [61:32] blocks, [31:0] outliers
+// look-back status word: [63:62] flag, [61:32] blocks, [31:0] outliers.
+// Unit u's word lives at status[u * kStatusStride]: spacing the words out
+// spreads the look-back's hot reads over more L2 lines and slices.
+#ifndef FZ_STATUS_STRIDE
+#define FZ_STATUS_STRIDE 16
+#endif
+constexpr uint64_t kStatusStride = FZ_STATUS_STRIDE;
 constexpr uint64_t kFlagAgg = 1ull << 62;
 constexpr uint64_t kFlagInc = 2ull << 62;
 constexpr uint64_t kValMask = (1ull << 62) - 1;
@@ -101,14 +106,17 @@ __device__ __forceinline__ uint64_t global_timer() {
   return t;
 }
 
-__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v)
+// The look-back's status words carry their whole message in the word
+// itself (no other memory is published through them), so relaxed
+// device-scope accesses suffice and no fence is needed.
+__device__ __forceinline__ void st_relaxed(uint64_t *p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v)
                : "memory");
 }
 
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
   uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];"
                : "=l"(v)
                : "l"(p)
                : "memory");
@@ -208,56 +216,122 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
   return v;
 }
 
-// Decoupled look-back (single-pass prefix sum over chunks in ticket order).
-// Executed by one full warp.  `agg` is this chunk's (blocks<<32 | outliers)
-// and the return value the exclusive prefix over chunks < c.  Every wait is
-// bounded by limit_ns; on time-out the error bit is raised and the prefix
-// found so far is used (all later writes stay bounds-checked).
-__device__ __forceinline__ uint64_t lookback(uint64_t *status, uint64_t c,
-                                             uint64_t agg, bool publish,
-                                             uint32_t *err, uint64_t limit_ns) {
+// Decoupled look-back (single-pass prefix sum over work units in ticket
+// order), in two steps so that a caller can do other work in between:
+// publish_aggregate() posts a unit's own (blocks<<32 | outliers) as soon as
+// it is known, resolve_prefix() later finds the exclusive prefix over units
+// < c and posts the unit's inclusive prefix.  Both are executed by one full
+// warp.  Lane 0 first waits for the immediate predecessor alone; when that
+// one has already posted its inclusive prefix (the common case) no other word
+// is read.  Otherwise the warp scans back 32*K words per round (K per lane);
+// only words nearer than the nearest inclusive prefix must have posted.  Every
+// wait is bounded by limit_ns; on time-out the error bit is raised and the
+// prefix found so far is used (all later writes stay bounds-checked).
+__device__ __forceinline__ void publish_aggregate(uint64_t *st, uint64_t c, uint64_t agg,
+                                                  bool publish) {
+  if ((threadIdx.x & 31) == 0 && publish)
+    st_relaxed(&st[c * kStatusStride], (c == 0 ? kFlagInc : kFlagAgg) | agg);
+}
+
+#ifndef FZ_LOOKBACK_K
+#define FZ_LOOKBACK_K 1
+#endif
+template <int K = FZ_LOOKBACK_K>
+__device__ __forceinline__ uint64_t resolve_prefix(uint64_t *st, uint64_t c, uint64_t agg,
+                                                   bool publish, uint32_t *err,
+                                                   uint64_t limit_ns) {
   const int lane = threadIdx.x & 31;
-  if (c == 0) {
-    if (lane == 0 && publish) st_release(&status[0], kFlagInc | agg);
-    return 0;
-  }
-  if (lane == 0 && publish) st_release(&status[c], kFlagAgg | agg);
-  uint64_t excl = 0;
-  int64_t j = (int64_t)c - 1;
-  uint64_t t0 = global_timer();
+  const unsigned full = 0xffffffffu;
+  if (c == 0) return 0;                    // posted inclusive already
+  uint64_t t0 = 0;
   bool timed_out = false;
-  while (true) {
-    int64_t idx = j - lane;
-    uint64_t v = idx >= 0 ? ld_acquire(&status[idx]) : kFlagInc;
-    uint32_t it = 0;
-    while (true) {                        // every exit is warp-uniform
-      const bool pending = (v >> 62) == 0;
-      if (!__any_sync(0xffffffffu, pending)) break;
-      if (pending) {
-        __nanosleep(32);
-        v = ld_acquire(&status[idx]);
-      }
-      if ((++it & 31u) == 0) {
-        const bool late = global_timer() - t0 > limit_ns;
-        if (__any_sync(0xffffffffu, late)) {
+  // immediate predecessor, one lane
+  uint64_t pv = 0;
+  if (lane == 0) {
+    pv = ld_relaxed(&st[(c - 1) * kStatusStride]);
+    if ((pv >> 62) == 0) {
+      t0 = global_timer();
+      uint32_t ns = 32;
+      while ((pv >> 62) == 0) {
+        __nanosleep(ns);
+        if (ns < 256) ns *= 2;
+        pv = ld_relaxed(&st[(c - 1) * kStatusStride]);
+        if ((pv >> 62) == 0 && global_timer() - t0 > limit_ns) {
           timed_out = true;
           break;
         }
       }
     }
-    if (timed_out) break;
-    uint32_t pmask = __ballot_sync(0xffffffffu, (v >> 62) == 2);
-    if (pmask) {
-      int p = __ffs(pmask) - 1;        // nearest predecessor with a prefix
-      excl += warp_sum_u64(lane <= p ? (v & kValMask) : 0);
-      break;
+  }
+  pv = __shfl_sync(full, pv, 0);
+  timed_out = __shfl_sync(full, timed_out, 0);
+  uint64_t excl = 0;
+  if (!timed_out && (pv >> 62) == 2) {
+    excl = pv & kValMask;
+  } else if (!timed_out) {
+    excl = pv & kValMask;                  // predecessor's aggregate
+    int64_t j = (int64_t)c - 2;            // nearest word of the window
+    while (true) {
+      // entry k of lane L is word j - (L*K + k): nearest first
+      uint64_t v[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int64_t idx = j - lane * K - k;
+        v[k] = idx >= 0 ? ld_relaxed(&st[(uint64_t)idx * kStatusStride]) : kFlagInc;
+      }
+      int pl, fk;
+      uint32_t it = 0;
+      while (true) {
+        int first = K;
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k)
+          if ((v[k] >> 62) == 2) first = k;
+        const uint32_t pmask = __ballot_sync(full, first < K);
+        pl = pmask ? __ffs(pmask) - 1 : 32;
+        fk = __shfl_sync(full, first, pl & 31);
+        bool pending = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+          pending |= (lane < pl || (lane == pl && k < fk)) && (v[k] >> 62) == 0;
+        if (!__any_sync(full, pending)) break;  // every exit is warp-uniform
+        if (t0 == 0) t0 = global_timer();
+        if (pending) {
+          __nanosleep(64);
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            const int64_t idx = j - lane * K - k;
+            if ((lane < pl || (lane == pl && k < fk)) && (v[k] >> 62) == 0)
+              v[k] = ld_relaxed(&st[(uint64_t)idx * kStatusStride]);
+          }
+        }
+        if ((++it & 15u) == 0) {
+          const bool late = global_timer() - t0 > limit_ns;
+          if (__any_sync(full, late)) {
+            timed_out = true;
+            break;
+          }
+        }
+      }
+      if (timed_out) break;
+      uint64_t part = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        part += (lane < pl || (lane == pl && k <= fk)) ? (v[k] & kValMask) : 0;
+      excl += warp_sum_u64(part);
+      if (pl < 32) break;
+      j -= 32 * K;
     }
-    excl += warp_sum_u64(v & kValMask);
-    j -= 32;
   }
   if (timed_out && lane == 0) atomicOr(err, kErrTimeout);
-  if (lane == 0 && publish) st_release(&status[c], kFlagInc | (excl + agg));
+  if (lane == 0 && publish) st_relaxed(&st[c * kStatusStride], kFlagInc | (excl + agg));
   return excl;
+}
+
+// both steps at once
+__device__ __forceinline__ uint64_t lookback(uint64_t *st, uint64_t c, uint64_t agg,
+                                             bool publish, uint32_t *err, uint64_t limit_ns) {
+  publish_aggregate(st, c, agg, publish);
+  return resolve_prefix(st, c, agg, publish, err, limit_ns);
 }
 
 // ------------------------------------------------------------ bit transpose

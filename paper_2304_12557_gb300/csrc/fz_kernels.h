@@ -20,8 +20,8 @@ struct CompressArgs {
   const RangeResult *range;    // relative mode: min/max/non-finite
   SetScratch *set_cur, *set_next;
   uint64_t *status_cur, *status_next;
-  uint32_t *chunk_out_prefix;  // per chunk: exclusive outlier prefix
-  uint32_t *chunk_out_count;   // per chunk: outliers
+  uint32_t *tile_out_prefix;   // per tile: exclusive outlier prefix
+  uint32_t *tile_out_count;    // per tile: outliers
   uint8_t *out;
   uint64_t out_capacity;
   uint64_t wait_limit_ns;
@@ -42,11 +42,14 @@ struct DecompressArgs {
 
 void launch_range(const float *x, uint64_t n, float2 *partial, int nblocks,
                   RangeResult *res, cudaStream_t s);
-size_t compress_smem_bytes();
-cudaError_t launch_compress(int ndim, bool tma, const CompressArgs &a,
-                            const CUtensorMap &tm, cudaStream_t s);
-cudaError_t launch_outliers(int ndim, bool tma, const CompressArgs &a,
-                            const CUtensorMap &tm, uint64_t out_section,
+// True when the compression kernel for this field reads its tiles through
+// TMA (2-D/3-D fields whose rows are 16-byte aligned); the caller then
+// passes a tensor map from encode_field_tmap.
+bool compress_uses_tma(int ndim, const CompressArgs &a);
+bool encode_field_tmap(int ndim, const uint64_t dims[3], const float *x, CUtensorMap *tm);
+cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *tm, int sms,
+                            cudaStream_t s);
+cudaError_t launch_outliers(int ndim, const CompressArgs &a, uint64_t out_section,
                             cudaStream_t s);
 cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s);
 int decompress_blocks_per_sm();

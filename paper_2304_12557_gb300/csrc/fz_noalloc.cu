@@ -13,7 +13,6 @@
 // array that is part of the library image, so it allocates nothing.  The
 // caller still passes the input and output buffers.
 #include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,13 +20,13 @@
 #include <cstring>
 #include <mutex>
 
-#include "../../include/fz.h"
+#include "fz.h"
 #include "fz_device.cuh"
 #include "fz_kernels.h"
 
 namespace {
 
-constexpr uint64_t kMaxChunks = FZ_NOALLOC_MAX_CODES / fz::kChunkCodes;
+constexpr uint64_t kMaxTiles = FZ_NOALLOC_MAX_CODES / fz::kTileCodes;
 constexpr int kRangeBlocks = 1216;
 constexpr int kMaxDevices = 64;
 
@@ -37,10 +36,10 @@ struct NoAllocScratch {
   fz::RangeResult range;                  // min/max/non-finite + counter
   uint32_t pad[12];
   float2 partial[kRangeBlocks];           // per-block range partials
-  uint64_t status[2][kMaxChunks];         // look-back words (set 1 is only
+  uint64_t status[2][kMaxTiles * fz::kStatusStride];  // look-back words (set 1 is only
                                           // ever written with zeros)
-  uint32_t out_prefix[kMaxChunks];
-  uint32_t out_count[kMaxChunks];
+  uint32_t out_prefix[kMaxTiles];
+  uint32_t out_count[kMaxTiles];
 };
 static_assert(offsetof(NoAllocScratch, partial) % 64 == 0, "alignment");
 static_assert(offsetof(NoAllocScratch, status) % 64 == 0, "alignment");
@@ -90,33 +89,6 @@ bool shape_of(const uint64_t dims[3], int ndim, uint64_t d[3], uint64_t *n_chunk
   return true;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
-    void *f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
-                                         cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      f = nullptr;
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }();
-  return fn;
-}
-
-bool tensor_map(int ndim, const uint64_t d[3], const float *x, CUtensorMap *tm) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
-  if (!enc) return false;
-  cuuint64_t gdim[3] = {d[0], d[1], d[2]};
-  cuuint64_t gstr[2] = {d[0] * 4, d[0] * d[1] * 4};
-  cuuint32_t estr[3] = {1, 1, 1};
-  cuuint32_t box3[3] = {32, 32, 8}, box2[2] = {32, 128};
-  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, ndim == 3 ? 3 : 2,
-                   const_cast<float *>(x), gdim, gstr, ndim == 3 ? box3 : box2, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS;
-}
-
 int read_result(const fz::SetScratch *dev_res, fz::SetScratch *host, cudaStream_t s) {
   if (cudaMemcpyAsync(host, dev_res, sizeof(*host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -134,7 +106,7 @@ extern "C" int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], in
   uint32_t ncx = 0, ncy = 0;
   if (!d_in || !d_out || !out_size || !shape_of(dims, ndim, d, &n_chunks, &n_elems, &ncx, &ncy))
     return FZ_ERR_ARG;
-  if (n_chunks > kMaxChunks) return FZ_ERR_ARG;          // beyond the static scratch
+  if (n_chunks * fz::kTilesPerChunk > kMaxTiles) return FZ_ERR_ARG;  // beyond the scratch
   if (mode != FZ_EB_ABS && mode != FZ_EB_REL) return FZ_ERR_ARG;
   if (!(eb > 0.0) || !std::isfinite(eb)) return FZ_ERR_ARG;
   if ((reinterpret_cast<uintptr_t>(d_out) & 15u) || (reinterpret_cast<uintptr_t>(d_in) & 3u))
@@ -154,7 +126,8 @@ extern "C" int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], in
   // the array keeps the previous call's contents: clear what must start at 0
   // (both result blocks, the range counter, this field's look-back words)
   if (cudaMemsetAsync(sc, 0, offsetof(NoAllocScratch, partial), s) != cudaSuccess ||
-      cudaMemsetAsync(sc->status[0], 0, n_chunks * sizeof(uint64_t), s) != cudaSuccess)
+      cudaMemsetAsync(sc->status[0], 0, n_tiles * fz::kStatusStride * sizeof(uint64_t), s) !=
+          cudaSuccess)
     return FZ_ERR_CUDA;
   if (mode == FZ_EB_REL) {
     const uint64_t want = (n_elems / 4 + 255) / 256;
@@ -162,10 +135,6 @@ extern "C" int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], in
     fz::launch_range(d_in, n_elems, sc->partial, nb, &sc->range, s);
     if (cudaGetLastError() != cudaSuccess) return FZ_ERR_CUDA;
   }
-  CUtensorMap tm;
-  std::memset(&tm, 0, sizeof(tm));
-  const bool tma = ndim >= 2 && d[0] % 4 == 0 && (reinterpret_cast<uintptr_t>(d_in) & 15u) == 0 &&
-                   tensor_map(ndim, d, d_in, &tm);
   fz::CompressArgs a{};
   a.x = d_in;
   for (int i = 0; i < 3; ++i) a.dims[i] = d[i];
@@ -179,13 +148,19 @@ extern "C" int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], in
   a.set_next = &sc->sets[1];
   a.status_cur = sc->status[0];
   a.status_next = sc->status[1];
-  a.chunk_out_prefix = sc->out_prefix;
-  a.chunk_out_count = sc->out_count;
+  a.tile_out_prefix = sc->out_prefix;
+  a.tile_out_count = sc->out_count;
   a.out = static_cast<uint8_t *>(d_out);
   a.out_capacity = cap;
   a.wait_limit_ns = 2000000000ull;
   a.skip_publish_chunk = ~0ull;
-  if (fz::launch_compress(ndim, tma, a, tm, s) != cudaSuccess) return FZ_ERR_CUDA;
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  const bool tma = fz::compress_uses_tma(ndim, a) && fz::encode_field_tmap(ndim, d, d_in, &tm);
+  if (fz::launch_compress(ndim, a, tma ? &tm : nullptr, sms, s) != cudaSuccess)
+    return FZ_ERR_CUDA;
   fz::SetScratch r;
   int st = read_result(&sc->sets[0], &r, s);
   if (st) return st;
@@ -212,7 +187,7 @@ extern "C" int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], in
     // (zeroed above; the compression kernel only ever writes zeros to it)
     a.set_cur = &sc->sets[1];
     if (cudaMemsetAsync(&sc->sets[1], 0, sizeof(fz::SetScratch), s) != cudaSuccess ||
-        fz::launch_outliers(ndim, tma, a, tm, min_bytes + 16 * r.nnz, s) != cudaSuccess)
+        fz::launch_outliers(ndim, a, min_bytes + 16 * r.nnz, s) != cudaSuccess)
       return FZ_ERR_CUDA;
     if ((st = read_result(&sc->sets[1], &r, s))) return st;
     if (r.err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
