@@ -170,15 +170,23 @@ struct TileGeo {
   bool edge;                 // the chunk reaches past the field
 };
 
+// chunk grid divisors, built once per warp
+struct ChunkGrid {
+  FastDiv x, y;
+  __device__ explicit ChunkGrid(const CompressArgs &a) : x(a.ncx), y(a.ncy) {}
+};
+
 template <int NDIM>
-__device__ __forceinline__ TileGeo tile_geo(const CompressArgs &a, uint64_t T, int g) {
+__device__ __forceinline__ TileGeo tile_geo(const CompressArgs &a, const ChunkGrid &cg,
+                                            uint64_t T, int g) {
   using G = Geo<NDIM>;
   TileGeo q;
-  const uint64_t c = T >> 2;
+  const uint32_t c = (uint32_t)(T >> 2);             // < 2^19
   q.t = (int)(T & 3);
-  q.cx = c % a.ncx;
-  q.cy = (c / a.ncx) % a.ncy;
-  q.cz = c / ((uint64_t)a.ncx * a.ncy);
+  const uint32_t r = cg.x.div(c);
+  q.cx = c - r * cg.x.d;
+  q.cz = cg.y.div(r);
+  q.cy = r - (uint32_t)q.cz * cg.y.d;
   q.bx = g % G::NBX;
   q.by = g / G::NBX;
   if constexpr (NDIM == 3) {
@@ -276,7 +284,6 @@ __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q
                                                 float r, const float (&hf)[32],
                                                 int32_t (&v)[64], uint32_t &qmax) {
   const unsigned full = 0xffffffffu;
-  const int32_t pad = (int32_t)kMagicBits;           // q = 0
   if constexpr (NDIM == 3) {
 #pragma unroll
     for (int iy = 0; iy < 4; ++iy) {                 // D_z, one row at a time
@@ -286,7 +293,7 @@ __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int32_t q0 = quant_bits(p0[k], r), q1 = quant_bits(p1[k], r);
-        const int32_t qh = q.t > 0 ? quant_bits(hf[8 * iy + k], r) : pad;
+        const int32_t qh = quant_bits(hf[8 * iy + k], r);   // hf = 0 when t == 0: q = 0
         if (CHECK) qmax = max(qmax, max((uint32_t)q0 - kBiasBits, (uint32_t)q1 - kBiasBits));
         v[8 * iy + k] = q0 - qh;
         v[32 + 8 * iy + k] = q1 - q0;
@@ -306,7 +313,7 @@ __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q
 #pragma unroll
     for (int ix = 0; ix < 8; ++ix) {                 // D_y
       int32_t up = __shfl_up_sync(full, v[ix + 56], 8);
-      if (q.by == 0) up = q.t > 0 ? quant_bits(hf[ix], r) : pad;
+      if (q.by == 0) up = quant_bits(hf[ix], r);        // hf = 0 when t == 0: q = 0
 #pragma unroll
       for (int iy = 7; iy >= 1; --iy) v[ix + 8 * iy] -= v[ix + 8 * (iy - 1)];
       v[ix] -= up;
@@ -382,7 +389,7 @@ __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const Tile
 template <int NDIM, int V>
 __device__ __forceinline__ void residuals_global(const CompressArgs &a, uint64_t T, int g,
                                                  float r, int32_t (&v)[64]) {
-  const TileGeo q = tile_geo<NDIM>(a, T, g);
+  const TileGeo q = tile_geo<NDIM>(a, ChunkGrid(a), T, g);
   uint32_t unused = 0;
   float hf[32];
   load_halo<NDIM, V>(a, q, hf);
@@ -423,14 +430,32 @@ __device__ __forceinline__ uint32_t pack_codes_escaped(const int32_t (&v)[64], u
   return n;
 }
 
+// The rare escape path, kept out of the hot loop: recompute the lane's
+// residuals from global memory, pack them with escapes into pb[32g..32g+31]
+// and return the lane's escape count.
+template <int NDIM, int V>
+__device__ __forceinline__ uint32_t escape_repack(const CompressArgs &a, uint64_t T, int g, float r,
+                                               uint32_t *pb) {
+  int32_t v[64];
+  residuals_global<NDIM, V>(a, T, g, r, v);
+  uint32_t w[32];
+  const uint32_t n = pack_codes_escaped(v, w);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) pb[32 * g + i] = w[i];
+  __syncwarp();
+  return n;
+}
+
 // TMA box of tile T for this warp: 3-D {32,32,2} (the tile's two planes),
 // 2-D two {32,32} x halves of the tile's 32 rows
 template <int NDIM>
-__device__ __forceinline__ void issue_box(const CompressArgs &a, const CUtensorMap *tm,
-                                          uint8_t *box, uint64_t *bar, uint64_t T) {
-  const uint64_t c = T >> 2;
+__device__ __forceinline__ void issue_box(const CompressArgs &a, const ChunkGrid &cg,
+                                          const CUtensorMap *tm, uint8_t *box, uint64_t *bar,
+                                          uint64_t T) {
+  const uint32_t c = (uint32_t)(T >> 2);
   const int t = (int)(T & 3);
-  const uint64_t cx = c % a.ncx, cy = (c / a.ncx) % a.ncy, cz = c / ((uint64_t)a.ncx * a.ncy);
+  const uint32_t r = cg.x.div(c);
+  const uint32_t cx = c - r * cg.x.d, cz = cg.y.div(r), cy = r - cz * cg.y.d;
   mbar_expect_tx(bar, kTileBoxBytes);
   if constexpr (NDIM == 3) {
     tma_load_3d(box, tm, bar, (int)(cx * 32), (int)(cy * 32), (int)(cz * 8 + 2 * t));
@@ -541,6 +566,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, 3)
   }
   if (!ok) return;                                   // the same in every warp
 
+  const ChunkGrid cg(a);
   uint64_t T = 0;
   if (g == 0) T = atomicAdd(&cur->ticket, 1u);
   T = __shfl_sync(full, T, 0);
@@ -548,7 +574,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, 3)
   if constexpr (TMA) {
     if (g == 0) {
       mbar_init(bar, 1);
-      if (T < n_tiles) issue_box<NDIM>(a, &tmap, box, bar, T);
+      if (T < n_tiles) issue_box<NDIM>(a, cg, &tmap, box, bar, T);
     }
     __syncwarp();
   }
@@ -561,7 +587,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, 3)
       T_next = atomicAdd(&cur->ticket, 1u);
       a.status_next[T * kStatusStride] = 0;          // for the next call
     }
-    const TileGeo q = tile_geo<NDIM>(a, T, g);
+    const TileGeo q = tile_geo<NDIM>(a, cg, T, g);
     float hf[32];
     load_halo<NDIM, V>(a, q, hf);
     int32_t v[64];
@@ -577,7 +603,7 @@ __global__ void __launch_bounds__(kCompWarps * 32, 3)
       T_next = __shfl_sync(full, T_next, 0);
       if (g == 0 && T_next < n_tiles) {
         fence_proxy_async_smem();
-        issue_box<NDIM>(a, &tmap, box, bar, T_next);
+        issue_box<NDIM>(a, cg, &tmap, box, bar, T_next);
       }
     } else {
       residuals_first<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, g, p.ebx2_r, hf, v, qmax);
@@ -589,17 +615,18 @@ __global__ void __launch_bounds__(kCompWarps * 32, 3)
     uint32_t w[32];
     const uint32_t orabs = pack_codes(v, w);         // v is dead from here on
     uint32_t nout_lane = 0;
+    uint32_t *pb = pbs[buf];
     if (__any_sync(full, (orabs >> 15) != 0)) {
-      // rare: some |residual| needs more than 15 bits; recompute the
-      // residuals (cheaper than keeping them live) and repack with escapes
-      int32_t v2[64];
-      residuals_global<NDIM, V>(a, T, g, p.ebx2_r, v2);
-      nout_lane = pack_codes_escaped(v2, w);
+      // rare: some |residual| needs more than 15 bits; recompute and repack
+      // with escapes out of line (through the plane buffer)
+      nout_lane = escape_repack<NDIM, V>(a, T, g, p.ebx2_r, pb);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
+      __syncwarp();
     }
     transpose32(w);                                  // lane g: out[32b + g]
 
     // plane buffer: lane b collects plane b's 32 words (8 blocks)
-    uint32_t *pb = pbs[buf];
 #pragma unroll
     for (int b = 0; b < 32; ++b) pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)] = w[b];
     __syncwarp();

@@ -294,13 +294,15 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
   const uintptr_t op = reinterpret_cast<uintptr_t>(a.out);
   const int vw = (h.dims[0] % 8 == 0 && op % 32 == 0) ? 8
                  : (h.dims[0] % 4 == 0 && op % 16 == 0) ? 4 : 1;
+  const FastDiv dx((uint32_t)h.ncx), dy((uint32_t)h.ncy);
   while (true) {
     uint64_t c = 0;
     if (g == 0) c = atomicAdd(&cur->ticket, 1u);
     c = __shfl_sync(full, c, 0);
     if (c >= h.n_chunks) break;
     if (g == 0) a.status_next[c * kStatusStride] = 0;
-    const uint64_t cx = c % h.ncx, cy = (c / h.ncx) % h.ncy, cz = c / (h.ncx * h.ncy);
+    const uint32_t cr = dx.div((uint32_t)c);
+    const uint64_t cx = (uint32_t)c - cr * dx.d, cz = dy.div(cr), cy = cr - (uint32_t)cz * dy.d;
     // flags of the chunk's 4 tiles: lane l holds word l
     const uint32_t fw = __ldg(reinterpret_cast<const uint32_t *>(flags + 128 * c) + g);
     const uint32_t chunk_cnt = __reduce_add_sync(full, (uint32_t)__popc(fw));

@@ -62,6 +62,29 @@ template <> struct Geo<3> {
   static constexpr int CX = 32, CY = 32, CZ = 8;
 };
 
+// Division by a runtime constant d >= 1 for numerators below 2^31, by a
+// precomputed multiply-high: with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(n, m) + n) >> l
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994).  Replaces 64-bit division in per-tile index math.
+struct FastDiv {
+  uint32_t d, m, l;
+  __host__ __device__ FastDiv() : d(1), m(1), l(0) {}
+  __host__ __device__ explicit FastDiv(uint32_t div) : d(div) {
+    l = 0;
+    while ((1ull << l) < div) ++l;
+    m = (uint32_t)(((1ull << 32) * ((1ull << l) - div)) / div + 1);
+  }
+  __host__ __device__ uint32_t div(uint32_t n) const {
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(n, m);
+#else
+    const uint32_t t = (uint32_t)(((uint64_t)n * m) >> 32);
+#endif
+    return (t + n) >> l;
+  }
+};
+
 // The 64-byte stream header, little-endian (matches the host's reader).
 struct __align__(16) StreamHeader {
   uint8_t magic[4];        // "FZG1"

@@ -9,6 +9,7 @@ namespace fz {
 
 struct SetScratch;
 struct RangeResult;
+struct FastDiv;
 
 struct CompressArgs {
   const float *x;

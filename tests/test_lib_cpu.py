@@ -118,3 +118,45 @@ int main() {
         bits_in = np.unpackbits(a.view(np.uint8), bitorder="little").reshape(32, 32)
         bits_out = np.unpackbits(b.view(np.uint8), bitorder="little").reshape(32, 32)
         np.testing.assert_array_equal(bits_out, bits_in.T)
+
+
+def test_fastdiv_host_build():
+    """The kernels' division by a runtime constant (multiply-high), compiled
+    as host code, against exact integer division for numerators < 2^31."""
+    src = r'''
+#include <cstdio>
+#include <cstdint>
+#include "fz_device.cuh"
+int main() {
+  uint32_t ds[] = {1, 2, 3, 5, 7, 16, 17, 57, 64, 100, 127, 128, 129, 1000, 4095, 4096,
+                   65535, 65536, 524287, 524288, 1u << 30, (1u << 31) - 1};
+  uint64_t s = 88172645463325252ull, bad = 0, n_checked = 0;
+  for (uint32_t d : ds) {
+    fz::FastDiv f(d);
+    uint32_t edges[] = {0, 1, d - 1, d, d + 1, 2 * d - 1, 2 * d, 0x7FFFFFFFu, 0x7FFFFFFEu,
+                        (0x7FFFFFFFu / d) * d, (0x7FFFFFFFu / d) * d - 1};
+    for (uint32_t n : edges) {
+      if (n > 0x7FFFFFFFu) continue;
+      bad += f.div(n) != n / d; ++n_checked;
+    }
+    for (int i = 0; i < 200000; ++i) {
+      s ^= s << 13; s ^= s >> 7; s ^= s << 17;
+      uint32_t n = (uint32_t)(s & 0x7FFFFFFFu);
+      if (i & 1) n &= 0xFFFFF;
+      bad += f.div(n) != n / d; ++n_checked;
+    }
+  }
+  printf("%llu %llu\n", (unsigned long long)bad, (unsigned long long)n_checked);
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        cpp = os.path.join(d, "t.cu")
+        exe = os.path.join(d, "t")
+        open(cpp, "w").write(src)
+        inc = os.path.join(ROOT, "paper_2304_12557_gb300", "csrc")
+        subprocess.run(["nvcc", "-std=c++17", "-I", inc, "-o", exe, cpp],
+                       check=True, capture_output=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    bad, checked = (int(v) for v in out.split())
+    assert checked > 4_000_000 and bad == 0
