@@ -329,7 +329,7 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
   DeviceGuard guard(c->device);
   if (!guard.ok) return FZ_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int st = ensure_cap(c, sh.n_tiles);             // one look-back word per tile
+  int st = ensure_cap(c, sh.n_tiles);             // at least one look-back word per unit
   if (st) return st;
   if ((st = prepare_set(c, s))) return st;
   prof_reset(c);
@@ -369,7 +369,8 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
     return FZ_ERR_CUDA;
   }
   prof_end(c, 1, s);
-  retire_set(c, sh.n_tiles, sh.n_tiles);
+  const uint64_t words = fz::compress_status_words(sh.n_tiles);
+  retire_set(c, words, words);
   if ((st = read_set(c, A, s))) {
     mark_all_dirty(c);
     return st;

@@ -116,26 +116,58 @@ __global__ void __launch_bounds__(256) range_kernel(const float *__restrict__ x,
 }
 
 // ====================================================================
-// compression: persistent warps, one 2048-code tile per ticket
+// compression: persistent blocks, one 2048-code tile per warp and round
 // ====================================================================
 //
-// Every warp is independent (no block-level barrier).  A warp takes the
-// next tile from a ticket counter in stream order and does the whole tile:
-// pre-quantisation, Lorenzo, codes, bitshuffle, flags, the decoupled
-// look-back on the tile index and the compacted stores.  Its input comes
-// either from a per-warp TMA box (the tile plus the previous plane/row the
-// first Lorenzo difference needs, loaded asynchronously one tile ahead) or,
-// for fields whose rows are not 16-byte aligned and for 1-D fields, straight
-// from global memory.
+// One block per SM: kCompWarps compute warps and one scan warp.  Each round
+// the scan warp takes a ticket for a unit of kCompWarps consecutive tiles
+// (stream order); compute warp j does tile j of the unit: pre-quantisation,
+// Lorenzo, codes, bitshuffle, flags, and posts the tile's aggregate (blocks,
+// outliers) in shared memory.  The scan warp sums the unit, runs the
+// decoupled look-back on the unit index and hands every warp its tile's
+// exclusive prefix, which the warp uses one round later to store the
+// compacted blocks.  The look-back therefore walks one status word per
+// unit, and its latency is hidden behind the compute warps' next tile.
+// A compute warp's input comes either from a per-warp TMA box (its tile,
+// loaded one round ahead) or, for fields whose rows are not 16-byte aligned
+// and for 1-D fields, straight from global memory.
 
-constexpr int kCompWarps = 4;                   // warps per block
-// per warp: [TMA box 8 KB][plane buffer 0, 4 KB][plane buffer 1, 4 KB]
+constexpr int kCompWarps = 11;                  // compute warps per block
+constexpr int kCompThreads = 32 * (kCompWarps + 1);   // + the scan warp
+constexpr int kRing = 4;                        // rounds in flight per block
+// per compute warp: [TMA box 8 KB][plane buffer 0, 4 KB][plane buffer 1, 4 KB]
 constexpr int kBoxStride = 16384;
 constexpr int kPlaneOff = 8192;
-constexpr int kCompSmemTma = kCompWarps * kBoxStride + 64 + 1024;
-constexpr int kCompSmemLdg = kCompWarps * 8192 + 64 + 1024;
 constexpr int kHalf2D = 4096;                   // second x half of a 2-D box
 constexpr uint32_t kTileBoxBytes = 32 * 32 * 2 * 4;  // one tile (3-D: 2 planes; 2-D: 2 halves)
+
+// the rounds a block has in flight, in shared memory behind the warps' areas
+struct RoundSlot {
+  uint64_t unit;                 // tiles [unit * kCompWarps, unit * kCompWarps + kCompWarps)
+  uint64_t agg[kCompWarps];      // tile aggregates, (blocks << 32) | outliers
+  uint64_t excl[kCompWarps];     // their exclusive prefixes in the stream
+};
+struct CompShared {
+  uint64_t box_bar[kCompWarps];  // per compute warp: its TMA box landed
+  uint64_t ticket_bar[kRing];    // 1 arrival: the scan warp posted the unit
+  uint64_t agg_bar[kRing];       // kCompWarps arrivals: every aggregate posted
+  uint64_t excl_bar[kRing];      // kCompWarps arrivals: every prefix posted
+  RoundSlot slot[kRing];
+};
+constexpr int kCompSmemTma = kCompWarps * kBoxStride + (int)sizeof(CompShared) + 1024;
+constexpr int kCompSmemLdg = kCompWarps * 8192 + (int)sizeof(CompShared) + 1024;
+static_assert(kCompSmemTma <= 227 * 1024, "shared memory per block");
+
+// number of look-back status words a compression of n_tiles tiles uses
+uint64_t compress_status_words(uint64_t n_tiles) {
+  return (n_tiles + kCompWarps - 1) / kCompWarps;
+}
+
+// bounded wait on an mbarrier phase by a whole warp; the result is uniform
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  const bool ok = mbar_wait_bounded(bar, parity, limit_ns);
+  return __all_sync(0xffffffffu, ok);
+}
 
 // 8 consecutive floats from p.  V = 8: one 32-byte load (p 32-byte
 // aligned); V = 4: two 16-byte loads; V = 1: scalar loads.
@@ -466,24 +498,30 @@ __device__ __forceinline__ void issue_box(const CompressArgs &a, const ChunkGrid
   }
 }
 
-// the compacted blocks of a finished tile, resolved one tile later
+// the compacted blocks of a finished tile, stored one round later
 struct Pending {
   uint64_t T;          // tile index (n_tiles: none)
   uint64_t agg;        // (blocks << 32) | outliers
   uint32_t F, P;       // lane b: flag byte and exclusive block rank of plane b
   uint32_t *pb;        // its plane buffer
+  uint32_t round;      // the block round it belongs to
 };
 
-// Resolve a finished tile's prefix (look-back) and store its compacted blocks
-// (Listing 2's copy: block (b, i) -> payload[PreSum]).
+// Take a finished tile's exclusive prefix from the scan warp and store its
+// compacted blocks (Listing 2's copy: block (b, i) -> payload[PreSum]).
 template <int NDIM>
-__device__ __forceinline__ void finish_tile(const CompressArgs &a, const Pending &d,
-                                            const EbParams &p, float fmin, float fmax,
-                                            uint64_t n_tiles, uint64_t pay, int g) {
+__device__ __forceinline__ void finish_tile(const CompressArgs &a, CompShared *sh,
+                                            const Pending &d, const EbParams &p, float fmin,
+                                            float fmax, uint64_t n_tiles, uint64_t pay, int g,
+                                            int wid) {
   SetScratch *cur = a.set_cur;
-  const uint64_t excl = resolve_prefix(a.status_cur, d.T, d.agg,
-                                       (d.T >> 2) != a.skip_publish_chunk, &cur->err,
-                                       a.wait_limit_ns);
+  const int s = (int)(d.round % kRing);
+  uint64_t excl = 0;
+  if (warp_wait(&sh->excl_bar[s], (d.round / kRing) & 1u, a.wait_limit_ns)) {
+    excl = sh->slot[s].excl[wid];
+  } else if (g == 0) {
+    atomicOr(&cur->err, kErrTimeout);
+  }
   if (g == 0) {
     a.tile_out_prefix[d.T] = (uint32_t)excl;
     a.tile_out_count[d.T] = (uint32_t)d.agg;
@@ -523,22 +561,73 @@ __device__ __forceinline__ void finish_tile(const CompressArgs &a, const Pending
   __syncwarp();                                      // plane buffer free again
 }
 
+// The scan warp's ticket for block round r: a unit index from the global
+// counter, posted in the ring (lane 0 only).  The unit's look-back word in
+// the next call's status array is cleared here.
+__device__ __forceinline__ void post_ticket(const CompressArgs &a, CompShared *sh, uint32_t r,
+                                            uint64_t n_units) {
+  const uint64_t u = atomicAdd(&a.set_cur->ticket, 1u);
+  if (u < n_units) a.status_next[u * kStatusStride] = 0;
+  sh->slot[r % kRing].unit = u;
+  mbar_arrive(&sh->ticket_bar[r % kRing]);
+}
+
+// The scan warp: tickets two rounds ahead, then per round the unit's
+// aggregate, its decoupled look-back and the tiles' exclusive prefixes.
+__device__ __forceinline__ void scan_warp(const CompressArgs &a, CompShared *sh,
+                                          uint64_t n_units, int g) {
+  const unsigned full = 0xffffffffu;
+  SetScratch *cur = a.set_cur;
+  const uint64_t skip_unit = a.skip_publish_chunk < a.n_chunks
+                                 ? a.skip_publish_chunk * kTilesPerChunk / kCompWarps
+                                 : ~0ull;
+  if (g == 0) {
+    post_ticket(a, sh, 0, n_units);
+    post_ticket(a, sh, 1, n_units);
+  }
+  for (uint32_t r = 0;; ++r) {
+    const int s = (int)(r % kRing);
+    __syncwarp();                                    // lane 0's ticket write
+    const uint64_t u = sh->slot[s].unit;
+    if (u >= n_units) break;
+    if (g == 0) post_ticket(a, sh, r + 2, n_units);
+    if (!warp_wait(&sh->agg_bar[s], (r / kRing) & 1u, a.wait_limit_ns)) {
+      if (g == 0) atomicOr(&cur->err, kErrTimeout);
+      break;
+    }
+    const uint64_t t_agg = g < kCompWarps ? sh->slot[s].agg[g] : 0;
+    uint64_t inc = t_agg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(full, inc, o);
+      if (g >= o) inc += y;
+    }
+    const uint64_t total = __shfl_sync(full, inc, 31);
+    const bool publish = u != skip_unit;
+    publish_aggregate(a.status_cur, u, total, publish);
+    const uint64_t excl =
+        resolve_prefix(a.status_cur, u, total, publish, &cur->err, a.wait_limit_ns);
+    if (g < kCompWarps) {
+      sh->slot[s].excl[g] = excl + inc - t_agg;
+      mbar_arrive(&sh->excl_bar[s]);
+    }
+  }
+}
+
 template <int NDIM, int V, bool CHECK, bool TMA>
-__global__ void __launch_bounds__(kCompWarps * 32, 3)
+__global__ void __launch_bounds__(kCompThreads, 1)
     compress_kernel(const CompressArgs a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const unsigned full = 0xffffffffu;
   const int g = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // per warp: [TMA box 8 KB] (TMA only) [plane buffer 0][plane buffer 1]
+  // per compute warp: [TMA box 8 KB] (TMA only) [plane buffer 0][plane buffer 1]
   constexpr int stride = TMA ? kBoxStride : 8192;
-  uint8_t *box = smem + wid * stride;
-  uint32_t *pbs[2] = {reinterpret_cast<uint32_t *>(box + (TMA ? kPlaneOff : 0)),
-                      reinterpret_cast<uint32_t *>(box + (TMA ? kPlaneOff : 0) + 4096)};
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kCompWarps * stride) + wid;
+  CompShared *sh = reinterpret_cast<CompShared *>(smem + kCompWarps * stride);
   SetScratch *cur = a.set_cur;
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
+  const uint64_t n_units = (n_tiles + kCompWarps - 1) / kCompWarps;
   const uint64_t pay = 64 + 32 * n_tiles;
 
   float fmin = 0.f, fmax = 0.f;
@@ -564,110 +653,141 @@ __global__ void __launch_bounds__(kCompWarps * 32, 3)
     nx->ticket = 0; nx->err = 0; nx->nnz = 0; nx->nout = 0;
     nx->n_chunks = 0; nx->hdr_nout = 0;
   }
-  if (!ok) return;                                   // the same in every warp
+  if (!ok) return;                                   // the same in every thread
 
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kCompWarps; ++i) mbar_init(&sh->box_bar[i], 1);
+    for (int i = 0; i < kRing; ++i) {
+      mbar_init(&sh->ticket_bar[i], 1);
+      mbar_init(&sh->agg_bar[i], kCompWarps);
+      mbar_init(&sh->excl_bar[i], kCompWarps);
+    }
+  }
+  __syncthreads();
+  if (wid == kCompWarps) {
+    scan_warp(a, sh, n_units, g);
+    return;
+  }
+
+  // ---- compute warp
+  uint8_t *box = smem + wid * stride;
+  uint32_t *const pb0 = reinterpret_cast<uint32_t *>(box + (TMA ? kPlaneOff : 0));
+  uint64_t *bar = &sh->box_bar[wid];
   const ChunkGrid cg(a);
-  uint64_t T = 0;
-  if (g == 0) T = atomicAdd(&cur->ticket, 1u);
-  T = __shfl_sync(full, T, 0);
+  uint64_t u = n_units;
+  if (warp_wait(&sh->ticket_bar[0], 0, a.wait_limit_ns)) u = sh->slot[0].unit;
+  else if (g == 0) atomicOr(&cur->err, kErrTimeout);
   uint32_t phase = 0;
   if constexpr (TMA) {
-    if (g == 0) {
-      mbar_init(bar, 1);
-      if (T < n_tiles) issue_box<NDIM>(a, cg, &tmap, box, bar, T);
-    }
+    const uint64_t T0 = u * kCompWarps + wid;
+    if (g == 0 && u < n_units && T0 < n_tiles) issue_box<NDIM>(a, cg, &tmap, box, bar, T0);
     __syncwarp();
   }
-  Pending prev{n_tiles, 0, 0, 0, pbs[1]};
-  int buf = 0;
-  while (T < n_tiles) {
-    // the next ticket is requested now; its round trip overlaps this tile
-    uint64_t T_next = 0;
-    if (g == 0) {
-      T_next = atomicAdd(&cur->ticket, 1u);
-      a.status_next[T * kStatusStride] = 0;          // for the next call
-    }
-    const TileGeo q = tile_geo<NDIM>(a, cg, T, g);
-    float hf[32];
-    load_halo<NDIM, V>(a, q, hf);
-    int32_t v[64];
-    uint32_t qmax = 0;
-    if constexpr (TMA) {
-      if (!mbar_wait_bounded(bar, phase, a.wait_limit_ns) && g == 0)
+  Pending prev{n_tiles, 0, 0, 0, pb0, 0};
+  uint32_t buf = 0;                                  // plane buffer of this round
+  for (uint32_t r = 0; u < n_units; ++r) {
+    const int s = (int)(r % kRing);
+    const uint64_t T = u * kCompWarps + wid;
+    // the next round's unit (the scan warp posts tickets two rounds ahead)
+    uint64_t u_next = n_units;
+    auto next_unit = [&] {
+      const int s1 = (int)((r + 1) % kRing);
+      if (warp_wait(&sh->ticket_bar[s1], ((r + 1) / kRing) & 1u, a.wait_limit_ns))
+        u_next = sh->slot[s1].unit;
+      else if (g == 0)
         atomicOr(&cur->err, kErrTimeout);
-      phase ^= 1u;
-      residuals_first<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, g, p.ebx2_r, hf, v, qmax);
-      // the box is consumed: fetch the next tile into it while this one is
-      // finished (generic-proxy reads of the box precede the async write)
-      __syncwarp();
-      T_next = __shfl_sync(full, T_next, 0);
-      if (g == 0 && T_next < n_tiles) {
-        fence_proxy_async_smem();
-        issue_box<NDIM>(a, cg, &tmap, box, bar, T_next);
+    };
+    uint64_t agg = 0;
+    uint32_t F = 0, P = 0;
+    uint32_t *pb = pb0 + 1024 * buf;
+    if (T < n_tiles) {
+      const TileGeo q = tile_geo<NDIM>(a, cg, T, g);
+      float hf[32];
+      load_halo<NDIM, V>(a, q, hf);
+      int32_t v[64];
+      uint32_t qmax = 0;
+      if constexpr (TMA) {
+        if (!mbar_wait_bounded(bar, phase, a.wait_limit_ns) && g == 0)
+          atomicOr(&cur->err, kErrTimeout);
+        phase ^= 1u;
+        residuals_first<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, g, p.ebx2_r, hf, v, qmax);
+        // the box is consumed: fetch the next round's tile into it while this
+        // one is finished (generic-proxy reads of the box precede the async write)
+        __syncwarp();
+        next_unit();
+        const uint64_t T_next = u_next * kCompWarps + wid;
+        if (g == 0 && u_next < n_units && T_next < n_tiles) {
+          fence_proxy_async_smem();
+          issue_box<NDIM>(a, cg, &tmap, box, bar, T_next);
+        }
+      } else {
+        residuals_first<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, g, p.ebx2_r, hf, v, qmax);
+        next_unit();
       }
-    } else {
-      residuals_first<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, g, p.ebx2_r, hf, v, qmax);
-      T_next = __shfl_sync(full, T_next, 0);
-    }
-    residuals_rest<NDIM>(a, q, g, p.ebx2_r, v);
-    if (CHECK && __any_sync(full, qmax > kBiasedMax) && g == 0) atomicOr(&cur->err, kErrRange);
+      residuals_rest<NDIM>(a, q, g, p.ebx2_r, v);
+      if (CHECK && __any_sync(full, qmax > kBiasedMax) && g == 0) atomicOr(&cur->err, kErrRange);
 
-    uint32_t w[32];
-    const uint32_t orabs = pack_codes(v, w);         // v is dead from here on
-    uint32_t nout_lane = 0;
-    uint32_t *pb = pbs[buf];
-    if (__any_sync(full, (orabs >> 15) != 0)) {
-      // rare: some |residual| needs more than 15 bits; recompute and repack
-      // with escapes out of line (through the plane buffer)
-      nout_lane = escape_repack<NDIM, V>(a, T, g, p.ebx2_r, pb);
+      uint32_t w[32];
+      const uint32_t orabs = pack_codes(v, w);       // v is dead from here on
+      uint32_t nout_lane = 0;
+      if (__any_sync(full, (orabs >> 15) != 0)) {
+        // rare: some |residual| needs more than 15 bits; recompute and repack
+        // with escapes out of line (through the plane buffer)
+        nout_lane = escape_repack<NDIM, V>(a, T, g, p.ebx2_r, pb);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
+        for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
+        __syncwarp();
+      }
+      transpose32(w);                                // lane g: out[32b + g]
+
+      // plane buffer: lane b collects plane b's 32 words (8 blocks)
+#pragma unroll
+      for (int b = 0; b < 32; ++b) pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)] = w[b];
       __syncwarp();
-    }
-    transpose32(w);                                  // lane g: out[32b + g]
-
-    // plane buffer: lane b collects plane b's 32 words (8 blocks)
 #pragma unroll
-    for (int b = 0; b < 32; ++b) pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)] = w[b];
-    __syncwarp();
-    uint32_t F = 0;                                  // lane b: flag byte of plane b
+      for (int i = 0; i < 8; ++i) {                  // lane b: flag byte of plane b
+        const uint4 blk = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
+        F |= ((blk.x | blk.y | blk.z | blk.w) != 0u ? 1u : 0u) << i;
+      }
+      const uint32_t pc = __popc(F);
+      P = pc;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const uint4 blk = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
-      F |= ((blk.x | blk.y | blk.z | blk.w) != 0u ? 1u : 0u) << i;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(full, P, o);
+        if (g >= o) P += y;
+      }
+      const uint32_t tile_nnz = __shfl_sync(full, P, 31);
+      P -= pc;
+      const uint32_t tile_nout = __reduce_add_sync(full, nout_lane);
+      a.out[64 + T * 32 + g] = (uint8_t)F;           // Listing 1's flags
+      agg = ((uint64_t)tile_nnz << 32) | tile_nout;
+    } else {
+      next_unit();                                   // past the last tile
     }
-    const uint32_t pc = __popc(F);
-    uint32_t P = pc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(full, P, o);
-      if (g >= o) P += y;
+    if (g == 0) {
+      sh->slot[s].agg[wid] = agg;
+      mbar_arrive(&sh->agg_bar[s]);
     }
-    const uint32_t tile_nnz = __shfl_sync(full, P, 31);
-    P -= pc;
-    const uint32_t tile_nout = __reduce_add_sync(full, nout_lane);
-    a.out[64 + T * 32 + g] = (uint8_t)F;             // Listing 1's flags
-    const uint64_t agg = ((uint64_t)tile_nnz << 32) | tile_nout;
-    publish_aggregate(a.status_cur, T, agg, (T >> 2) != a.skip_publish_chunk);
-
-    // the previous tile's prefix has had a whole tile's time to settle
-    if (prev.T < n_tiles) finish_tile<NDIM>(a, prev, p, fmin, fmax, n_tiles, pay, g);
-    prev = Pending{T, agg, F, P, pb};
+    // the previous round's prefix has had a whole tile's time to settle
+    if (prev.T < n_tiles) finish_tile<NDIM>(a, sh, prev, p, fmin, fmax, n_tiles, pay, g, wid);
+    prev = Pending{T, agg, F, P, pb, r};
     buf ^= 1;
-    T = T_next;
+    u = u_next;
   }
-  if (prev.T < n_tiles) finish_tile<NDIM>(a, prev, p, fmin, fmax, n_tiles, pay, g);
+  if (prev.T < n_tiles) finish_tile<NDIM>(a, sh, prev, p, fmin, fmax, n_tiles, pay, g, wid);
 }
 
 // ====================================================================
 // outlier pass (only tiles that escaped some residual)
 // ====================================================================
+constexpr int kOutWarps = 4;                    // outlier pass: warps per block, one tile each
+
 template <int NDIM, int V>
-__global__ void __launch_bounds__(kCompWarps * 32)
+__global__ void __launch_bounds__(kOutWarps * 32)
     outlier_kernel(const CompressArgs a, uint64_t out_section) {
   const int g = threadIdx.x & 31;
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
-  const uint64_t T = (uint64_t)blockIdx.x * kCompWarps + (threadIdx.x >> 5);
+  const uint64_t T = (uint64_t)blockIdx.x * kOutWarps + (threadIdx.x >> 5);
   if (T >= n_tiles || a.tile_out_count[T] == 0) return;
   float fmin = 0.f, fmax = 0.f;
   if (a.mode == 1) { fmin = a.range->fmin; fmax = a.range->fmax; }
@@ -726,11 +846,11 @@ static cudaError_t launch_c3(const CompressArgs &a, const CUtensorMap &tm, int s
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kCompWarps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kCompThreads, smem);
     if (e != cudaSuccess) return e;
     per_sm = n > 0 ? n : 1;
   }
-  k<<<sms * per_sm, kCompWarps * 32, smem, s>>>(a, tm);
+  k<<<sms * per_sm, kCompThreads, smem, s>>>(a, tm);
   return cudaGetLastError();
 }
 
@@ -809,11 +929,11 @@ cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *
 template <int NDIM>
 static cudaError_t launch_o(const CompressArgs &a, uint64_t out_section, cudaStream_t s) {
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
-  const unsigned blocks = (unsigned)((n_tiles + kCompWarps - 1) / kCompWarps);
+  const unsigned blocks = (unsigned)((n_tiles + kOutWarps - 1) / kOutWarps);
   switch (vec_width(a)) {
-    case 8: outlier_kernel<NDIM, 8><<<blocks, kCompWarps * 32, 0, s>>>(a, out_section); break;
-    case 4: outlier_kernel<NDIM, 4><<<blocks, kCompWarps * 32, 0, s>>>(a, out_section); break;
-    default: outlier_kernel<NDIM, 1><<<blocks, kCompWarps * 32, 0, s>>>(a, out_section); break;
+    case 8: outlier_kernel<NDIM, 8><<<blocks, kOutWarps * 32, 0, s>>>(a, out_section); break;
+    case 4: outlier_kernel<NDIM, 4><<<blocks, kOutWarps * 32, 0, s>>>(a, out_section); break;
+    default: outlier_kernel<NDIM, 1><<<blocks, kOutWarps * 32, 0, s>>>(a, out_section); break;
   }
   return cudaGetLastError();
 }

@@ -48,6 +48,9 @@ void launch_range(const float *x, uint64_t n, float2 *partial, int nblocks,
 // passes a tensor map from encode_field_tmap.
 bool compress_uses_tma(int ndim, const CompressArgs &a);
 bool encode_field_tmap(int ndim, const uint64_t dims[3], const float *x, CUtensorMap *tm);
+// look-back status words (one per unit of consecutive tiles) a compression
+// of n_tiles tiles uses and clears in the other set
+uint64_t compress_status_words(uint64_t n_tiles);
 cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *tm, int sms,
                             cudaStream_t s);
 cudaError_t launch_outliers(int ndim, const CompressArgs &a, uint64_t out_section,
