@@ -153,6 +153,67 @@ int fz_set_profiling(fz_ctx *ctx, int on);
 int fz_get_kernel_times(fz_ctx *ctx, double ms[4]);
 
 /* ---------------------------------------------------------------------
+ * One field split across ranks.  Chunks are independent (Sec. 2.3: the
+ * Lorenzo residual never reaches across a chunk), so a field can be cut
+ * into slabs of whole chunk rows along its slowest axis, each slab
+ * compressed on its own rank, and the slabs' streams concatenated into the
+ * stream of the whole field, byte for byte the stream fz_compress makes of
+ * it.  The relative bound needs one exchange first: the field's value range
+ * (Sec. 4.1), the min and max over every slab.
+ *
+ * fz_range: value range of a device field of n floats (the relative mode's
+ * range pass).  Writes *h_min, *h_max (+0 for zeros of either sign) and
+ * *h_nonfinite (1 if some element is NaN or Inf; min/max then unspecified).
+ * Synchronises `stream`.  FZ_OK, FZ_ERR_ARG (n == 0, NULL pointer, d_in
+ * not 4-byte aligned) or FZ_ERR_CUDA. */
+int fz_range(fz_ctx *ctx, const float *d_in, uint64_t n, float *h_min,
+             float *h_max, int *h_nonfinite, void *stream);
+
+/* fz_compress in relative mode (Sec. 4.1) against a value range supplied by
+ * the caller, [range_min, range_max], instead of d_in's own: the bound is
+ * eb * (range_max - range_min), as fz_compress would derive it from a field
+ * with that range, and the header records that range.  No range pass runs;
+ * every element is still checked (FZ_ERR_NONFINITE, FZ_ERR_EB_RANGE).  A
+ * non-finite or inverted range is FZ_ERR_ARG.  Other arguments and errors
+ * as fz_compress. */
+int fz_compress_ranged(fz_ctx *ctx, const float *d_in, const uint64_t dims[3],
+                       int ndim, double eb, float range_min, float range_max,
+                       void *d_out, uint64_t out_capacity, uint64_t *out_size,
+                       void *stream);
+
+/* Slab `shard` of `n_shards` of a field: the range [*begin, *end) of its
+ * slowest axis (z for 3-D, y for 2-D, x for 1-D), whole chunk rows, the rows
+ * dealt out as evenly as possible in order.  A shard may be empty
+ * (*begin == *end) when there are fewer rows than shards.  Host only.
+ * FZ_OK or FZ_ERR_ARG. */
+int fz_shard_extent(const uint64_t dims[3], int ndim, int n_shards, int shard,
+                    uint64_t *begin, uint64_t *end);
+
+/* Concatenate the streams of consecutive slabs of one field, in slab order,
+ * into the stream of the whole field (header totals summed, flags, payloads
+ * and outlier lists appended, outlier code indices moved by the codes before
+ * each slab).  Every part must come from fz_compress (ABS) or
+ * fz_compress_ranged (REL, same range) with the same ndim, mode, eb and
+ * non-slowest dims; every part but the last must span whole chunk rows.
+ *   d_parts[i]   device pointer to part i, 8-byte aligned, part_sizes[i] bytes
+ *   d_out        device pointer, 16-byte aligned, out_capacity bytes
+ *   out_size     host pointer; receives the stream size (also on
+ *                FZ_ERR_CAPACITY: the size needed)
+ * Synchronises `stream`.  FZ_OK, FZ_ERR_ARG, FZ_ERR_CORRUPT (a part's
+ * header or size is inconsistent, or the parts do not fit together),
+ * FZ_ERR_CAPACITY or FZ_ERR_CUDA. */
+int fz_concat_streams(fz_ctx *ctx, const void *const *d_parts,
+                      const uint64_t *part_sizes, int n_parts, void *d_out,
+                      uint64_t out_capacity, uint64_t *out_size, void *stream);
+
+/* The same concatenation of host copies of the parts into host memory (no
+ * GPU involved; usable on a rank without one).  h_out may be NULL with
+ * out_capacity 0: a size query (FZ_ERR_CAPACITY, *out_size = the size). */
+int fz_concat_streams_host(const void *const *h_parts,
+                           const uint64_t *part_sizes, int n_parts, void *h_out,
+                           uint64_t out_capacity, uint64_t *out_size);
+
+/* ---------------------------------------------------------------------
  * Compression without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * GPU memory while they run, e.g. an application whose memory pool has

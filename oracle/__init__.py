@@ -92,6 +92,10 @@ def lib() -> ctypes.CDLL:
             L.fzo_compress.argtypes = [_f32p, _u32p, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, _u8p, ctypes.c_uint64,
                                        ctypes.POINTER(ctypes.c_uint64)]
+            L.fzo_compress_ranged.argtypes = [_f32p, _u32p, ctypes.c_int,
+                                              ctypes.c_double, ctypes.c_float,
+                                              ctypes.c_float, _u8p, ctypes.c_uint64,
+                                              ctypes.POINTER(ctypes.c_uint64)]
             L.fzo_decompress.argtypes = [_u8p, ctypes.c_uint64, _f32p,
                                          ctypes.c_uint64]
             L.fzo_reconstruct_closed_form.argtypes = [_f32p, ctypes.c_uint64,
@@ -213,6 +217,29 @@ def compress(x: np.ndarray, ndim: int, mode: int, eb: float):
         st = lib().fzo_compress(_ptr(x, _f32p), _ptr(dims, _u32p), ndim, mode,
                                 eb, _ptr(out, _u8p), size.value,
                                 ctypes.byref(size))
+    if st != OK:
+        return st, b""
+    return st, out[: size.value].tobytes()
+
+
+def compress_ranged(x: np.ndarray, ndim: int, eb: float, range_min: float,
+                    range_max: float):
+    """Relative bound against a supplied value range (x one slab of a field
+    whose range that is).  Returns (status, bytes)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    dims = _dims3(x.shape[::-1][:ndim])
+    cap = compress_bound(ndim, dims)
+    cap = min(cap, 64 + 32 * num_tiles(ndim, dims) * 129 + 8 * x.size)
+    out = np.empty(cap, np.uint8)
+    size = ctypes.c_uint64()
+    args = (ctypes.c_float(range_min), ctypes.c_float(range_max))
+    st = lib().fzo_compress_ranged(_ptr(x, _f32p), _ptr(dims, _u32p), ndim, eb,
+                                   *args, _ptr(out, _u8p), cap, ctypes.byref(size))
+    if st == ERR_CAPACITY:
+        out = np.empty(size.value, np.uint8)
+        st = lib().fzo_compress_ranged(_ptr(x, _f32p), _ptr(dims, _u32p), ndim,
+                                       eb, *args, _ptr(out, _u8p), size.value,
+                                       ctypes.byref(size))
     if st != OK:
         return st, b""
     return st, out[: size.value].tobytes()

@@ -321,8 +321,34 @@ static int check_dims(int ndim, const uint32_t dims[3]) {
   return 1;
 }
 
+/* Shared by fzo_compress and fzo_compress_ranged: rng == NULL takes the
+ * relative bound's value range from x itself. */
+static int compress_common(const float *x, const uint32_t dims[3], int ndim,
+                           int mode, double eb, const float *rng,
+                           uint8_t *out, uint64_t cap, uint64_t *out_size);
+
 int fzo_compress(const float *x, const uint32_t dims[3], int ndim, int mode,
                  double eb, uint8_t *out, uint64_t cap, uint64_t *out_size) {
+  return compress_common(x, dims, ndim, mode, eb, NULL, out, cap, out_size);
+}
+
+/* Sec. 4.1's value-range-relative bound with the range supplied by the
+ * caller: the range of the whole field when x is one slab of it, so that
+ * every slab quantises with the field's bound. */
+int fzo_compress_ranged(const float *x, const uint32_t dims[3], int ndim,
+                        double eb, float range_min, float range_max,
+                        uint8_t *out, uint64_t cap, uint64_t *out_size) {
+  float rng[2] = {range_min, range_max};
+  if (!isfinite(range_min) || !isfinite(range_max) || range_min > range_max) {
+    *out_size = 0;
+    return FZO_ERR_ARG;
+  }
+  return compress_common(x, dims, ndim, FZO_EB_REL, eb, rng, out, cap, out_size);
+}
+
+static int compress_common(const float *x, const uint32_t dims[3], int ndim,
+                           int mode, double eb, const float *rng,
+                           uint8_t *out, uint64_t cap, uint64_t *out_size) {
   *out_size = 0;
   if (!x || !out || !check_dims(ndim, dims)) return FZO_ERR_ARG;
   if (mode != FZO_EB_ABS && mode != FZO_EB_REL) return FZO_ERR_ARG;
@@ -339,7 +365,10 @@ int fzo_compress(const float *x, const uint32_t dims[3], int ndim, int mode,
 
   /* value range (relative mode), +0 for zeros */
   float fmin = 0.0f, fmax = 0.0f;
-  if (mode == FZO_EB_REL) {
+  if (mode == FZO_EB_REL && rng) {
+    fmin = rng[0] + 0.0f;
+    fmax = rng[1] + 0.0f;
+  } else if (mode == FZO_EB_REL) {
     fmin = x[0]; fmax = x[0];
     for (uint64_t i = 1; i < n; i++) {
       if (x[i] < fmin) fmin = x[i];

@@ -98,6 +98,14 @@ uint64_t fzo_compress_bound(int ndim, const uint32_t dims[3]);
 int fzo_compress(const float *x, const uint32_t dims[3], int ndim, int mode,
                  double eb, uint8_t *out, uint64_t cap, uint64_t *out_size);
 
+/* The relative bound (Sec. 4.1) against a caller-supplied value range
+ * [range_min, range_max] instead of x's own (x a slab of a larger field whose
+ * range this is).  Header mode REL, header range = the supplied one.
+ * FZO_ERR_ARG for a non-finite or inverted range. */
+int fzo_compress_ranged(const float *x, const uint32_t dims[3], int ndim,
+                        double eb, float range_min, float range_max,
+                        uint8_t *out, uint64_t cap, uint64_t *out_size);
+
 /* Decompress a stream into x (capacity in elements). */
 int fzo_decompress(const uint8_t *in, uint64_t in_size, float *x,
                    uint64_t cap_elems);

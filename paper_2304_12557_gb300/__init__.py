@@ -16,7 +16,8 @@ import threading
 __all__ = ["Codec", "FZError", "load_library", "library_path", "EB_ABS",
            "EB_REL", "OK", "ERR_ARG", "ERR_CAPACITY", "ERR_NONFINITE",
            "ERR_EB_RANGE", "ERR_CORRUPT", "ERR_TIMEOUT", "ERR_CUDA",
-           "compress_bound", "stream_min_bytes", "inspect", "C_API"]
+           "compress_bound", "stream_min_bytes", "inspect", "shard_extent",
+           "concat_streams_host", "C_API"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libfz_gb300.so")
@@ -37,7 +38,9 @@ C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
          "fz_compress", "fz_decompress", "fz_compress_host",
          "fz_decompress_host", "fz_inspect", "fz_strerror",
          "fz_set_wait_limit_ns", "fz_debug_skip_publish",
-         "fz_set_profiling", "fz_get_kernel_times", "fz_compress_noalloc"]
+         "fz_set_profiling", "fz_get_kernel_times", "fz_range",
+         "fz_compress_ranged", "fz_shard_extent", "fz_concat_streams",
+         "fz_concat_streams_host", "fz_compress_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -102,6 +105,22 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_compress_noalloc.argtypes = [_vp, dims_t, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, _vp, _u64,
                                           ctypes.POINTER(_u64), _vp]
+        L.fz_range.argtypes = [_vp, _vp, _u64, ctypes.POINTER(ctypes.c_float),
+                               ctypes.POINTER(ctypes.c_float),
+                               ctypes.POINTER(ctypes.c_int), _vp]
+        L.fz_compress_ranged.argtypes = [_vp, _vp, dims_t, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_float,
+                                         ctypes.c_float, _vp, _u64,
+                                         ctypes.POINTER(_u64), _vp]
+        L.fz_shard_extent.argtypes = [dims_t, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.POINTER(_u64),
+                                      ctypes.POINTER(_u64)]
+        L.fz_concat_streams.argtypes = [_vp, ctypes.POINTER(_vp), dims_t,
+                                        ctypes.c_int, _vp, _u64,
+                                        ctypes.POINTER(_u64), _vp]
+        L.fz_concat_streams_host.argtypes = [ctypes.POINTER(_vp), dims_t,
+                                             ctypes.c_int, _vp, _u64,
+                                             ctypes.POINTER(_u64)]
         _lib = L
         return L
 
@@ -134,6 +153,36 @@ def inspect(header: bytes) -> dict:
             "range_min": info.range_min, "range_max": info.range_max,
             "n_tiles": info.n_tiles, "nnz_blocks": info.nnz_blocks,
             "n_outliers": info.n_outliers, "stream_bytes": info.stream_bytes}
+
+
+def shard_extent(dims, ndim: int, n_shards: int, shard: int):
+    """Slab `shard` of `n_shards` of a field: (begin, end) along its slowest
+    axis (z for 3-D, y for 2-D, x for 1-D), whole chunk rows."""
+    b, e = _u64(0), _u64(0)
+    st = load_library().fz_shard_extent(_dims(dims), ndim, n_shards, shard,
+                                        ctypes.byref(b), ctypes.byref(e))
+    if st != OK:
+        raise FZError(st, "fz_shard_extent")
+    return int(b.value), int(e.value)
+
+
+def concat_streams_host(parts) -> bytes:
+    """Stream of a whole field from the streams (bytes) of its consecutive
+    slabs, on the host."""
+    bufs = [ctypes.create_string_buffer(bytes(p), len(p)) for p in parts]
+    ptrs = (_vp * len(bufs))(*[ctypes.cast(b, _vp) for b in bufs])
+    sizes = (_u64 * len(bufs))(*[len(p) for p in parts])
+    total = _u64(0)
+    L = load_library()
+    st = L.fz_concat_streams_host(ptrs, sizes, len(bufs), None, 0,
+                                  ctypes.byref(total))
+    if st == ERR_CAPACITY:
+        out = ctypes.create_string_buffer(int(total.value))
+        st = L.fz_concat_streams_host(ptrs, sizes, len(bufs), out,
+                                      total.value, ctypes.byref(total))
+    if st != OK:
+        raise FZError(st, "fz_concat_streams_host")
+    return out.raw[: int(total.value)]
 
 
 def _mode(mode) -> int:
@@ -240,6 +289,46 @@ class Codec:
         if st != OK:
             raise FZError(st, "fz_compress")
         return out[:size]
+
+    def value_range(self, x, stream=None):
+        """(min, max, nonfinite) of a float32 CUDA tensor (the range pass)."""
+        lo, hi, bad = ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
+        st = self._L.fz_range(self._ctx, _vp(x.data_ptr()), x.numel(),
+                              ctypes.byref(lo), ctypes.byref(hi),
+                              ctypes.byref(bad), self._stream(stream))
+        if st != OK:
+            raise FZError(st, "fz_range")
+        return lo.value, hi.value, bool(bad.value)
+
+    def compress_ranged_into(self, x, out, eb, range_min, range_max, ndim=None,
+                             stream=None, raise_on_error=True):
+        """Relative bound eb against the supplied value range (x a slab of a
+        field with that range).  Returns (status, size)."""
+        ndim = ndim or x.dim()
+        dims = list(x.shape[::-1])[:ndim]
+        assert x.is_cuda and x.is_contiguous(), "x must be a contiguous CUDA tensor"
+        size = _u64(0)
+        st = self._L.fz_compress_ranged(self._ctx, _vp(x.data_ptr()), _dims(dims),
+                                        ndim, float(eb), float(range_min),
+                                        float(range_max), _vp(out.data_ptr()),
+                                        out.numel() * out.element_size(),
+                                        ctypes.byref(size), self._stream(stream))
+        if st != OK and raise_on_error:
+            raise FZError(st, "fz_compress_ranged")
+        return st, int(size.value)
+
+    def concat_into(self, parts, out, stream=None, raise_on_error=True):
+        """Concatenate slab streams (uint8 CUDA tensors, in slab order) into
+        the whole field's stream in `out`.  Returns (status, size)."""
+        ptrs = (_vp * len(parts))(*[p.data_ptr() for p in parts])
+        sizes = (_u64 * len(parts))(*[p.numel() for p in parts])
+        size = _u64(0)
+        st = self._L.fz_concat_streams(self._ctx, ptrs, sizes, len(parts),
+                                       _vp(out.data_ptr()), out.numel(),
+                                       ctypes.byref(size), self._stream(stream))
+        if st != OK and raise_on_error:
+            raise FZError(st, "fz_concat_streams")
+        return st, int(size.value)
 
     def decompress_into(self, stream_t, out, nbytes=None, stream=None,
                         raise_on_error=True):

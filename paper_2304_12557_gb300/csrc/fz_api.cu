@@ -312,8 +312,11 @@ int fz_debug_skip_publish(fz_ctx *c, uint64_t chunk) {
   return FZ_OK;
 }
 
-int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, int mode,
-                double eb, void *d_out, uint64_t cap, uint64_t *out_size, void *stream) {
+// fz_compress and fz_compress_ranged: rng = NULL takes a relative bound's
+// range from a range pass over d_in, else rng[0..1] is the range
+static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim,
+                         int mode, double eb, const float *rng, void *d_out, uint64_t cap,
+                         uint64_t *out_size, void *stream) {
   if (out_size) *out_size = 0;
   Shape sh;
   if (!c || !d_in || !d_out || !out_size || !make_shape(dims, ndim, &sh)) return FZ_ERR_ARG;
@@ -333,7 +336,7 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
   if (st) return st;
   if ((st = prepare_set(c, s))) return st;
   prof_reset(c);
-  if (mode == FZ_EB_REL) {
+  if (mode == FZ_EB_REL && !rng) {
     prof_begin(c, 0, s);
     if ((st = range_pass(c, d_in, sh.n_elems, s))) return st;
     prof_end(c, 0, s);
@@ -349,6 +352,9 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
   a.mode = mode;
   a.eb_req = eb;
   a.range = c->range;
+  a.range_given = rng != nullptr;
+  a.range_lo = rng ? rng[0] : 0.f;
+  a.range_hi = rng ? rng[1] : 0.f;
   a.set_cur = c->sets + A;
   a.set_next = c->sets + (1 - A);
   a.status_cur = c->status + A * c->cap * fz::kStatusStride;
@@ -383,7 +389,8 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
   }
   if (r.err & fz::kErrNonFinite) return FZ_ERR_NONFINITE;
   if (r.err & (fz::kErrEbParam | fz::kErrRange)) {
-    if (mode == FZ_EB_ABS) return classify_range_error(c, d_in, sh.n_elems, s);
+    // elements checked one by one: NaN/Inf fail the same check
+    if (mode == FZ_EB_ABS || rng) return classify_range_error(c, d_in, sh.n_elems, s);
     return FZ_ERR_EB_RANGE;
   }
   if (r.err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
@@ -413,6 +420,92 @@ int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, 
   }
   *out_size = total;
   return FZ_OK;
+}
+
+int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, int mode,
+                double eb, void *d_out, uint64_t cap, uint64_t *out_size, void *stream) {
+  return compress_impl(c, d_in, dims, ndim, mode, eb, nullptr, d_out, cap, out_size, stream);
+}
+
+int fz_compress_ranged(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim,
+                       double eb, float range_min, float range_max, void *d_out, uint64_t cap,
+                       uint64_t *out_size, void *stream) {
+  if (out_size) *out_size = 0;
+  if (!std::isfinite(range_min) || !std::isfinite(range_max) || range_min > range_max)
+    return FZ_ERR_ARG;
+  const float rng[2] = {range_min + 0.0f, range_max + 0.0f};   // +0 for a zero of either sign
+  return compress_impl(c, d_in, dims, ndim, FZ_EB_REL, eb, rng, d_out, cap, out_size, stream);
+}
+
+int fz_range(fz_ctx *c, const float *d_in, uint64_t n, float *h_min, float *h_max,
+             int *h_nonfinite, void *stream) {
+  if (!c || !d_in || !h_min || !h_max || !h_nonfinite || n == 0 ||
+      (reinterpret_cast<uintptr_t>(d_in) & 3u))
+    return FZ_ERR_ARG;
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (range_pass(c, d_in, n, s) != FZ_OK ||
+      cudaMemcpyAsync(c->h_range, c->range, sizeof(RangeResult), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  *h_min = c->h_range->fmin;
+  *h_max = c->h_range->fmax;
+  *h_nonfinite = c->h_range->nonfinite ? 1 : 0;
+  return FZ_OK;
+}
+
+int fz_concat_streams(fz_ctx *c, const void *const *d_parts, const uint64_t *part_sizes,
+                      int n_parts, void *d_out, uint64_t cap, uint64_t *out_size, void *stream) {
+  if (out_size) *out_size = 0;
+  if (!c || !d_parts || !part_sizes || !d_out || !out_size || n_parts < 1) return FZ_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(d_out) & 15u) return FZ_ERR_ARG;
+  for (int i = 0; i < n_parts; ++i)
+    if (!d_parts[i] || (reinterpret_cast<uintptr_t>(d_parts[i]) & 7u)) return FZ_ERR_ARG;
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t(*hdrs)[64] = new (std::nothrow) uint8_t[n_parts][64];
+  fz::ConcatPart *parts = new (std::nothrow) fz::ConcatPart[n_parts];
+  int st = (hdrs && parts) ? FZ_OK : FZ_ERR_CUDA;
+  // the parts' headers, after whatever wrote them on the stream
+  for (int i = 0; st == FZ_OK && i < n_parts; ++i) {
+    std::memset(hdrs[i], 0, 64);
+    const uint64_t nb = part_sizes[i] < 64 ? part_sizes[i] : 64;
+    if (nb && cudaMemcpyAsync(hdrs[i], d_parts[i], nb, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      st = FZ_ERR_CUDA;
+  }
+  if (st == FZ_OK && cudaStreamSynchronize(s) != cudaSuccess) st = FZ_ERR_CUDA;
+  fz::ConcatPlan plan;
+  if (st == FZ_OK) st = fz::concat_plan(hdrs, part_sizes, n_parts, parts, &plan);
+  if (st == FZ_OK && plan.total > cap) {
+    *out_size = plan.total;
+    st = FZ_ERR_CAPACITY;
+  }
+  if (st == FZ_OK) {
+    uint8_t *o = static_cast<uint8_t *>(d_out);
+    const uint64_t pay = 64 + 32 * plan.n_tiles, outs = pay + 16 * plan.nnz;
+    bool ok = cudaMemcpyAsync(o, plan.hdr, 64, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    for (int i = 0; ok && i < n_parts; ++i) {
+      const uint8_t *p = static_cast<const uint8_t *>(d_parts[i]);
+      const fz::ConcatPart &q = parts[i];
+      const uint8_t *src_out = p + 64 + 32 * q.tiles + 16 * q.nnz;
+      ok = cudaMemcpyAsync(o + 64 + 32 * q.tile_off, p + 64, 32 * q.tiles,
+                           cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+           (q.nnz == 0 || cudaMemcpyAsync(o + pay + 16 * q.nnz_off, p + 64 + 32 * q.tiles,
+                                          16 * q.nnz, cudaMemcpyDeviceToDevice,
+                                          s) == cudaSuccess) &&
+           fz::launch_rebase_outliers(src_out, o + outs + 8 * q.out_off, q.nout,
+                                      (uint32_t)(q.tile_off * fz::kTileCodes), s) == cudaSuccess;
+    }
+    // the header copy reads plan.hdr (host memory) until the stream reaches it
+    if (!ok || cudaStreamSynchronize(s) != cudaSuccess) st = FZ_ERR_CUDA;
+    else *out_size = plan.total;
+  }
+  delete[] hdrs;
+  delete[] parts;
+  return st;
 }
 
 int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,

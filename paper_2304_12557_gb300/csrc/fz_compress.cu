@@ -189,6 +189,20 @@ __device__ __forceinline__ void load8(const float *p, float (&f)[8]) {
   }
 }
 
+// The value range a relative bound is taken against (Sec. 4.1): the range
+// pass's result, or the caller's range (a slab of a field split across
+// ranks uses the whole field's).  Absolute bounds have none.
+__device__ __forceinline__ void field_range(const CompressArgs &a, float &fmin, float &fmax,
+                                            bool &nonfinite) {
+  if (a.mode != 1) return;
+  if (a.range_given) {
+    fmin = a.range_lo; fmax = a.range_hi;
+  } else {
+    fmin = a.range->fmin; fmax = a.range->fmax;
+    nonfinite = a.range->nonfinite != 0;
+  }
+}
+
 // fl(v + 1.5*2^23) of v = fl(x * r): the integer rint(v) sits in the low
 // mantissa bits; returned as raw bits (biased by kMagicBits).
 __device__ __forceinline__ int32_t quant_bits(float x, float r) {
@@ -632,13 +646,10 @@ __global__ void __launch_bounds__(kCompThreads, 1)
 
   float fmin = 0.f, fmax = 0.f;
   bool nonfinite = false;
-  if (a.mode == 1) {
-    fmin = a.range->fmin; fmax = a.range->fmax;
-    nonfinite = a.range->nonfinite != 0;
-  }
+  field_range(a, fmin, fmax, nonfinite);
   const EbParams p = derive_eb(a.mode, a.eb_req, fmin, fmax);
   bool ok = p.ok && !nonfinite;
-  if (ok && a.mode == 1) {
+  if (ok && a.mode == 1 && !a.range_given) {
     // relative bound: the element of largest magnitude is in the field, so
     // checking it checks every element (fp multiply and rounding are monotone)
     const float m = fmaxf(fabsf(fmin), fabsf(fmax));
@@ -790,7 +801,8 @@ __global__ void __launch_bounds__(kOutWarps * 32)
   const uint64_t T = (uint64_t)blockIdx.x * kOutWarps + (threadIdx.x >> 5);
   if (T >= n_tiles || a.tile_out_count[T] == 0) return;
   float fmin = 0.f, fmax = 0.f;
-  if (a.mode == 1) { fmin = a.range->fmin; fmax = a.range->fmax; }
+  bool nonfinite = false;
+  field_range(a, fmin, fmax, nonfinite);
   const EbParams p = derive_eb(a.mode, a.eb_req, fmin, fmax);
   int32_t v[64];
   residuals_global<NDIM, V>(a, T, g, p.ebx2_r, v);
@@ -868,8 +880,9 @@ static cudaError_t launch_c2(const CompressArgs &a, const CUtensorMap *tm, int s
 template <int NDIM, int V>
 static cudaError_t launch_c1(const CompressArgs &a, const CUtensorMap *tm, int sms,
                              cudaStream_t s) {
-  return a.mode == 0 ? launch_c2<NDIM, V, true>(a, tm, sms, s)
-                     : launch_c2<NDIM, V, false>(a, tm, sms, s);
+  // every element is range-checked unless a range pass has bounded them all
+  return (a.mode == 0 || a.range_given) ? launch_c2<NDIM, V, true>(a, tm, sms, s)
+                                        : launch_c2<NDIM, V, false>(a, tm, sms, s);
 }
 
 template <int NDIM>

@@ -18,7 +18,9 @@ struct CompressArgs {
   uint64_t n_chunks;
   int mode;                    // 0 abs, 1 rel
   double eb_req;
-  const RangeResult *range;    // relative mode: min/max/non-finite
+  const RangeResult *range;    // relative mode: min/max/non-finite of a range pass
+  int range_given;             // relative mode: use [range_lo, range_hi] instead
+  float range_lo, range_hi;
   SetScratch *set_cur, *set_next;
   uint64_t *status_cur, *status_next;
   uint32_t *tile_out_prefix;   // per tile: exclusive outlier prefix
@@ -56,6 +58,22 @@ cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *
 cudaError_t launch_outliers(int ndim, const CompressArgs &a, uint64_t out_section,
                             cudaStream_t s);
 cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s);
+
+// concatenation of slab streams (fz_shard.cu)
+struct ConcatPart {
+  uint64_t tiles, nnz, nout;              // the part's own counts
+  uint64_t tile_off, nnz_off, out_off;    // counts of the parts before it
+};
+struct ConcatPlan {
+  uint8_t hdr[64];                        // the whole field's header
+  uint64_t n_tiles, nnz, nout, total;
+};
+// Validate the parts' headers (host copies) and sizes; FZ_OK or an FZ_ERR_*.
+int concat_plan(const uint8_t (*hdrs)[64], const uint64_t *sizes, int n, ConcatPart *parts,
+                ConcatPlan *plan);
+// dst[i] = src[i] with the code index moved by `add` (n 8-byte records)
+cudaError_t launch_rebase_outliers(const void *src, void *dst, uint64_t n, uint32_t add,
+                                   cudaStream_t s);
 int decompress_blocks_per_sm();
 
 }  // namespace fz
