@@ -243,8 +243,10 @@ def run_ours(args, rank, world, local_rank, dist):
     k_comp = [kc[1] for _, _, _, kc, _, _ in recs]
     k_out = [kc[2] for _, _, _, kc, _, _ in recs]
     k_dec = [kd[3] for _, _, _, _, kd, _ in recs]
+    k_doff = [kd[4] for _, _, _, _, kd, _ in recs]
     size = recs[-1][5]
-    launches = sum(2 + (1 if kc[2] > 0 else 0) + 1 for _, _, _, kc, _, _ in recs)
+    # per step: range, compress, (outliers), offsets pass, decompress
+    launches = sum(4 + (1 if kc[2] > 0 else 0) for _, _, _, kc, _, _ in recs)
 
     # roofline of the dominant kernel (algorithmic bytes per launch)
     mean = lambda v: sum(v) / len(v)
@@ -296,7 +298,8 @@ def run_ours(args, rank, world, local_rank, dist):
             "compress_ms": {"p50": percentile(comp_ms, 0.5), "p99": percentile(comp_ms, 0.99)},
             "decompress_ms": {"p50": percentile(dec_ms, 0.5), "p99": percentile(dec_ms, 0.99)},
             "kernel_ms": {"range": mean(k_range), "compress": mean(k_comp),
-                          "outliers": mean(k_out), "decompress": mean(k_dec)},
+                          "outliers": mean(k_out), "decompress_offsets": mean(k_doff),
+                          "decompress": mean(k_dec)},
             "ratio": field_bytes / size, "stream_bytes": size,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,

@@ -138,19 +138,22 @@ const char *fz_strerror(int status);
  * prefix-sum look-back and the tile-load barrier).  Default 2e9. */
 int fz_set_wait_limit_ns(fz_ctx *ctx, uint64_t ns);
 
-/* Fault injection for tests of the bounded waits: the chunk with this
- * index skips publishing its look-back aggregate, so its successors' waits
- * run out and the call returns FZ_ERR_TIMEOUT.  UINT64_MAX disables. */
+/* Fault injection for tests of the bounded waits: the look-back unit that
+ * holds this chunk (the compressor's unit of 11 consecutive tiles, the
+ * decompressor's unit of 512 consecutive chunks) skips publishing its
+ * aggregate, so later units' waits run out and the call returns
+ * FZ_ERR_TIMEOUT.  UINT64_MAX disables. */
 int fz_debug_skip_publish(fz_ctx *ctx, uint64_t chunk);
 
 /* Kernel timing for profiling (off by default).  When on, each call
  * records CUDA events around every kernel it launches, on the call's
- * stream, and fz_get_kernel_times fills ms[0..3] with the last call's
+ * stream, and fz_get_kernel_times fills ms[0..4] with the last call's
  * durations in milliseconds: [0] range pass, [1] compression kernel,
- * [2] outlier pass, [3] decompression kernel (0 for kernels not run).
+ * [2] outlier pass, [3] decompression kernel, [4] the decompressor's
+ * offsets pass (0 for kernels not run).
  * Returns FZ_OK, FZ_ERR_ARG or FZ_ERR_CUDA. */
 int fz_set_profiling(fz_ctx *ctx, int on);
-int fz_get_kernel_times(fz_ctx *ctx, double ms[4]);
+int fz_get_kernel_times(fz_ctx *ctx, double ms[5]);
 
 /* ---------------------------------------------------------------------
  * One field split across ranks.  Chunks are independent (Sec. 2.3: the

@@ -244,8 +244,9 @@ class Codec:
             raise FZError(st, "fz_set_profiling")
 
     def kernel_times_ms(self):
-        """[range, compress, outliers, decompress] of the last call (ms)."""
-        ms = (ctypes.c_double * 4)()
+        """[range, compress, outliers, decompress, decompression offsets] of
+        the last call (ms)."""
+        ms = (ctypes.c_double * 5)()
         st = self._L.fz_get_kernel_times(self._ctx, ms)
         if st != OK:
             raise FZError(st, "fz_get_kernel_times")

@@ -42,8 +42,8 @@ struct fz_ctx {
   uint64_t stage_out_cap = 0;
   // profiling: events around each kernel of the last call
   bool profiling = false;
-  cudaEvent_t ev[8] = {};
-  bool ev_used[4] = {false, false, false, false};
+  cudaEvent_t ev[2 * fz::kProfSlots] = {};
+  bool ev_used[fz::kProfSlots] = {};
 };
 
 namespace {
@@ -181,13 +181,13 @@ int classify_range_error(fz_ctx *c, const float *x, uint64_t n, cudaStream_t s) 
   return c->h_range->nonfinite ? FZ_ERR_NONFINITE : FZ_ERR_EB_RANGE;
 }
 
-// events k (start) / k+4 (end) bracket kernel k when profiling is on
+// events k (start) / k+kProfSlots (end) bracket kernel k when profiling is on
 void prof_begin(fz_ctx *c, int k, cudaStream_t s) {
   if (c->profiling) cudaEventRecord(c->ev[k], s);
 }
 void prof_end(fz_ctx *c, int k, cudaStream_t s) {
   if (c->profiling) {
-    cudaEventRecord(c->ev[k + 4], s);
+    cudaEventRecord(c->ev[k + fz::kProfSlots], s);
     c->ev_used[k] = true;
   }
 }
@@ -291,15 +291,15 @@ int fz_set_profiling(fz_ctx *c, int on) {
   return FZ_OK;
 }
 
-int fz_get_kernel_times(fz_ctx *c, double ms[4]) {
+int fz_get_kernel_times(fz_ctx *c, double ms[5]) {
   if (!c || !ms) return FZ_ERR_ARG;
   DeviceGuard guard(c->device);
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < fz::kProfSlots; ++k) {
     ms[k] = 0.0;
     if (!c->ev_used[k]) continue;
     float t = 0.f;
-    if (cudaEventSynchronize(c->ev[k + 4]) != cudaSuccess ||
-        cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 4]) != cudaSuccess)
+    if (cudaEventSynchronize(c->ev[k + fz::kProfSlots]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, c->ev[k], c->ev[k + fz::kProfSlots]) != cudaSuccess)
       return FZ_ERR_CUDA;
     ms[k] = t;
   }
@@ -535,10 +535,18 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   a.status_cur = c->status + A * c->cap * fz::kStatusStride;
   a.status_next = c->status + (1 - A) * c->cap * fz::kStatusStride;
   a.status_cap = c->cap;
+  a.chunk_off = c->out_prefix;
+  a.chunk_olo = c->out_count;
   a.wait_limit_ns = c->wait_limit_ns;
   a.skip_publish_chunk = c->skip_publish;
   const int grid = c->num_sms * c->dec_blocks_per_sm;
   prof_reset(c);
+  prof_begin(c, 4, s);
+  if (fz::launch_dec_offsets(a, bound, s) != cudaSuccess) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  prof_end(c, 4, s);
   prof_begin(c, 3, s);
   if (fz::launch_decompress(a, grid, s) != cudaSuccess) {
     mark_all_dirty(c);
@@ -550,7 +558,8 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
     return st;
   }
   const SetScratch r = *c->h_res;
-  retire_set(c, r.n_chunks ? r.n_chunks : c->cap, r.n_chunks);
+  const uint64_t words = fz::decompress_status_words(r.n_chunks);
+  retire_set(c, r.n_chunks ? words : c->cap, words);
   if (r.err & fz::kErrTimeout) mark_all_dirty(c);
   // a timed-out wait leaves later offsets unreliable, so it takes precedence
   if (r.err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;

@@ -125,9 +125,9 @@ __global__ void __launch_bounds__(256) range_kernel(const float *__restrict__ x,
 // Lorenzo, codes, bitshuffle, flags, and posts the tile's aggregate (blocks,
 // outliers) in shared memory.  The scan warp sums the unit, runs the
 // decoupled look-back on the unit index and hands every warp its tile's
-// exclusive prefix, which the warp uses one round later to store the
+// exclusive prefix, which the warp uses two rounds later to store the
 // compacted blocks.  The look-back therefore walks one status word per
-// unit, and its latency is hidden behind the compute warps' next tile.
+// unit, and its latency is hidden behind the compute warps' next tiles.
 // A compute warp's input comes either from a per-warp TMA box (its tile,
 // loaded one round ahead) or, for fields whose rows are not 16-byte aligned
 // and for 1-D fields, straight from global memory.
@@ -135,8 +135,12 @@ __global__ void __launch_bounds__(256) range_kernel(const float *__restrict__ x,
 constexpr int kCompWarps = 11;                  // compute warps per block
 constexpr int kCompThreads = 32 * (kCompWarps + 1);   // + the scan warp
 constexpr int kRing = 4;                        // rounds in flight per block
-// per compute warp: [TMA box 8 KB][plane buffer 0, 4 KB][plane buffer 1, 4 KB]
-constexpr int kBoxStride = 16384;
+// Each warp stores a tile's compacted blocks two rounds after computing it,
+// so that the scan warp has two tiles' time to resolve the tile's prefix:
+// three plane buffers per warp.
+constexpr int kPlaneBufs = 3;
+// per compute warp: [TMA box 8 KB][plane buffers 0..2, 4 KB each]
+constexpr int kBoxStride = 8192 + kPlaneBufs * 4096;
 constexpr int kPlaneOff = 8192;
 constexpr int kHalf2D = 4096;                   // second x half of a 2-D box
 constexpr uint32_t kTileBoxBytes = 32 * 32 * 2 * 4;  // one tile (3-D: 2 planes; 2-D: 2 halves)
@@ -155,7 +159,7 @@ struct CompShared {
   RoundSlot slot[kRing];
 };
 constexpr int kCompSmemTma = kCompWarps * kBoxStride + (int)sizeof(CompShared) + 1024;
-constexpr int kCompSmemLdg = kCompWarps * 8192 + (int)sizeof(CompShared) + 1024;
+constexpr int kCompSmemLdg = kCompWarps * kPlaneBufs * 4096 + (int)sizeof(CompShared) + 1024;
 static_assert(kCompSmemTma <= 227 * 1024, "shared memory per block");
 
 // number of look-back status words a compression of n_tiles tiles uses
@@ -512,7 +516,7 @@ __device__ __forceinline__ void issue_box(const CompressArgs &a, const ChunkGrid
   }
 }
 
-// the compacted blocks of a finished tile, stored one round later
+// the compacted blocks of a finished tile, stored two rounds later
 struct Pending {
   uint64_t T;          // tile index (n_tiles: none)
   uint64_t agg;        // (blocks << 32) | outliers
@@ -619,8 +623,9 @@ __device__ __forceinline__ void scan_warp(const CompressArgs &a, CompShared *sh,
     const uint64_t total = __shfl_sync(full, inc, 31);
     const bool publish = u != skip_unit;
     publish_aggregate(a.status_cur, u, total, publish);
+    // 4 words per lane: a window of 128 units per round trip
     const uint64_t excl =
-        resolve_prefix(a.status_cur, u, total, publish, &cur->err, a.wait_limit_ns);
+        resolve_prefix<4>(a.status_cur, u, total, publish, &cur->err, a.wait_limit_ns);
     if (g < kCompWarps) {
       sh->slot[s].excl[g] = excl + inc - t_agg;
       mbar_arrive(&sh->excl_bar[s]);
@@ -636,8 +641,8 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const unsigned full = 0xffffffffu;
   const int g = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // per compute warp: [TMA box 8 KB] (TMA only) [plane buffer 0][plane buffer 1]
-  constexpr int stride = TMA ? kBoxStride : 8192;
+  // per compute warp: [TMA box 8 KB] (TMA only) [plane buffers 0..2]
+  constexpr int stride = TMA ? kBoxStride : kPlaneBufs * 4096;
   CompShared *sh = reinterpret_cast<CompShared *>(smem + kCompWarps * stride);
   SetScratch *cur = a.set_cur;
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
@@ -694,7 +699,8 @@ __global__ void __launch_bounds__(kCompThreads, 1)
     if (g == 0 && u < n_units && T0 < n_tiles) issue_box<NDIM>(a, cg, &tmap, box, bar, T0);
     __syncwarp();
   }
-  Pending prev{n_tiles, 0, 0, 0, pb0, 0};
+  Pending prev1{n_tiles, 0, 0, 0, pb0, 0};          // last round's tile
+  Pending prev2{n_tiles, 0, 0, 0, pb0, 0};          // the round before's
   uint32_t buf = 0;                                  // plane buffer of this round
   for (uint32_t r = 0; u < n_units; ++r) {
     const int s = (int)(r % kRing);
@@ -779,13 +785,15 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       sh->slot[s].agg[wid] = agg;
       mbar_arrive(&sh->agg_bar[s]);
     }
-    // the previous round's prefix has had a whole tile's time to settle
-    if (prev.T < n_tiles) finish_tile<NDIM>(a, sh, prev, p, fmin, fmax, n_tiles, pay, g, wid);
-    prev = Pending{T, agg, F, P, pb, r};
-    buf ^= 1;
+    // the prefix of the tile two rounds back has had two tiles' time to settle
+    if (prev2.T < n_tiles) finish_tile<NDIM>(a, sh, prev2, p, fmin, fmax, n_tiles, pay, g, wid);
+    prev2 = prev1;
+    prev1 = Pending{T, agg, F, P, pb, r};
+    buf = buf == kPlaneBufs - 1 ? 0 : buf + 1;
     u = u_next;
   }
-  if (prev.T < n_tiles) finish_tile<NDIM>(a, sh, prev, p, fmin, fmax, n_tiles, pay, g, wid);
+  if (prev2.T < n_tiles) finish_tile<NDIM>(a, sh, prev2, p, fmin, fmax, n_tiles, pay, g, wid);
+  if (prev1.T < n_tiles) finish_tile<NDIM>(a, sh, prev1, p, fmin, fmax, n_tiles, pay, g, wid);
 }
 
 // ====================================================================

@@ -19,7 +19,8 @@
 
 namespace fz {
 
-constexpr int kDecWarps = 4;
+constexpr int kDecWarps = 4;                    // decompression: warps per block
+constexpr int kOffChunks = 512;                 // offsets pass: chunks (threads) per block
 constexpr int kDecSmemBytes = kDecWarps * kTilesPerChunk * 4096;
 
 struct Hdr {
@@ -80,7 +81,7 @@ __device__ __forceinline__ uint64_t lower_bound_rec(const uint2 *rec, uint64_t n
 
 // residual of the escaped code with stream index `key`, searched among the
 // chunk's records [lo, hi); false when absent or not a real outlier
-__device__ __noinline__ bool find_outlier(const uint2 *rec, uint64_t lo, uint64_t hi,
+__device__ __forceinline__ bool find_outlier(const uint2 *rec, uint64_t lo, uint64_t hi,
                                           uint32_t key, int32_t *val) {
   uint64_t k = lo + lower_bound_rec(rec + lo, hi - lo, key);
   if (k >= hi) return false;
@@ -125,23 +126,6 @@ __device__ __forceinline__ void decode_codes(const uint32_t (&w)[32], int32_t (&
     const uint32_t s1 = prmt_sign(w[i], 0xBBBB);   // sign of the high code
     v[2 * i] = (int32_t)(((w[i] & 0x7FFFu) ^ s0) - s0);
     v[2 * i + 1] = (int32_t)((((w[i] >> 16) & 0x7FFFu) ^ s1) - s1);
-  }
-}
-
-// position of brick element e of lane g in tile t of chunk (cx,cy,cz)
-template <int NDIM>
-__device__ __forceinline__ void elem_coord(uint64_t cx, uint64_t cy, uint64_t cz, int t,
-                                           int g, int e, uint64_t &x, uint64_t &y,
-                                           uint64_t &z) {
-  using G = Geo<NDIM>;
-  const int bx = g % G::NBX, by = g / G::NBX;
-  const int ix = e % G::BX, iy = (e / G::BX) % G::BY, iz = e / (G::BX * G::BY);
-  if constexpr (NDIM == 3) {
-    x = cx * 32 + 8 * bx + ix; y = cy * 32 + 4 * by + iy; z = cz * 8 + 2 * t + iz;
-  } else if constexpr (NDIM == 2) {
-    x = cx * 64 + 8 * bx + ix; y = cy * 128 + 32 * t + 8 * by + iy; z = 0;
-  } else {
-    x = cx * 8192 + 2048 * t + 64 * g + e; y = 0; z = 0;
   }
 }
 
@@ -245,40 +229,102 @@ __device__ __forceinline__ void inverse_lorenzo(int32_t (&v)[64], int32_t (&carr
   }
 }
 
-// q (biased by the float bits of 1.5*2^23, which the chunk origin carries)
-// -> fl(float(q) * 2eb), stored row by row (8 floats per row)
+// elements of [o, o + n) below the field's extent L
+__device__ __forceinline__ uint32_t extent_in(uint64_t o, uint64_t L, uint32_t n) {
+  return o >= L ? 0u : (L - o < n ? (uint32_t)(L - o) : n);
+}
+
+// lowest n bits set, n in [0, 32]
+__device__ __forceinline__ uint32_t low_bits(uint32_t n) {
+  return n >= 32 ? 0xFFFFFFFFu : (1u << n) - 1u;
+}
+
+// Which of a lane's 64 brick elements lie inside the field, as two masks
+// over its 32 code words: bit t of `ev` for element 2t (the low code of word
+// t), of `od` for element 2t+1.  l[0..2]: elements of the brick's first row
+// / rows / planes that are inside (clamped to the brick).
 template <int NDIM>
-__device__ __forceinline__ void store_brick(const DecompressArgs &a, const Hdr &h,
-                                            const int32_t (&q)[64], uint64_t cx, uint64_t cy,
-                                            uint64_t cz, int t, int g, bool edge, int vw) {
-  const float e2 = h.ebx2;
-  const uint64_t X = h.dims[0], Y = h.dims[1];
+__device__ __forceinline__ void inside_masks(uint32_t lx, uint32_t ly, uint32_t lz,
+                                             uint32_t &ev, uint32_t &od) {
+  if constexpr (NDIM == 1) {
+    ev = low_bits((lx + 1) / 2);
+    od = low_bits(lx / 2);
+  } else {
+    // rows of 8 elements = 4 words; row r is (iy, iz) = (r % BY, r / BY)
+    using G = Geo<NDIM>;
+    const uint32_t re = low_bits((lx + 1) / 2), ro = low_bits(lx / 2);
+    ev = 0; od = 0;
 #pragma unroll
-  for (int row = 0; row < 8; ++row) {
-    float f[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      f[k] = __fmul_rn(__fsub_rn(__int_as_float(q[8 * row + k]), kRoundMagic), e2);
-    uint64_t x0, y, z;
-    elem_coord<NDIM>(cx, cy, cz, t, g, 8 * row, x0, y, z);
-    float *dst = a.out + x0 + X * (y + Y * z);
-    const bool full_row = !edge || (x0 + 8 <= X && y < Y && z < h.dims[2]);
-    if (full_row && vw == 8) {
-      asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst),
-                   "f"(f[0]), "f"(f[1]), "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]),
-                   "f"(f[6]), "f"(f[7])
-                   : "memory");
-    } else if (full_row && vw == 4) {
-      __stcs(reinterpret_cast<float4 *>(dst), make_float4(f[0], f[1], f[2], f[3]));
-      __stcs(reinterpret_cast<float4 *>(dst) + 1, make_float4(f[4], f[5], f[6], f[7]));
-    } else if (full_row) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) __stcs(dst + k, f[k]);
-    } else if (y < Y && z < h.dims[2]) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (x0 + k < X) __stcs(dst + k, f[k]);
+    for (int r = 0; r < 8; ++r) {
+      const uint32_t iy = r % G::BY, iz = r / G::BY;
+      if (iy < ly && iz < lz) { ev |= re << (4 * r); od |= ro << (4 * r); }
     }
+  }
+}
+
+// the 8 flag bytes of tile t for lane b (plane b), from the chunk's flag
+// words held one per lane
+__device__ __forceinline__ uint32_t plane_flags(uint32_t fw, int t, int g) {
+  return (__shfl_sync(0xffffffffu, fw, 8 * t + (g >> 2)) >> (8 * (g & 3))) & 0xFFu;
+}
+
+// Copy tile t's present blocks into its plane buffer (Listing 2 backwards:
+// block k comes from payload[PreSum[k]]), as one commit group; lane b
+// copies plane b's blocks, `rank` its first block's payload index.  Absent
+// blocks are zero-filled; a rank past the payload marks the stream corrupt.
+__device__ __forceinline__ bool gather_tile(const uint8_t *payload, uint64_t nnz, uint32_t *dst,
+                                            uint32_t F, uint64_t rank, int g) {
+  bool oob = false;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const bool present = (F >> i) & 1u;
+    const bool valid = present && rank < nnz;
+    oob |= present && !valid;
+    cp_async16(dst + 32 * g + 4 * (i ^ (g & 7)), payload + 16 * (valid ? rank : 0),
+               valid ? 16u : 0u);
+    rank += present;
+  }
+  cp_async_commit();
+  return oob;
+}
+
+// A chunk's per-lane gather state: its flag word (lane l: word l of the
+// chunk's 32) and, per tile, the payload index of lane b's first block.
+struct ChunkPlan {
+  uint32_t fw;
+  uint64_t base;              // the chunk's first payload block
+  uint32_t p01, p23;          // per-lane exclusive ranks, tiles 0/1 and 2/3 (16-bit halves)
+  uint32_t c01, c23;          // tile block counts, same packing
+};
+
+__device__ __forceinline__ ChunkPlan plan_chunk(uint32_t fw, uint64_t base, int g) {
+  const unsigned full = 0xffffffffu;
+  ChunkPlan p;
+  p.fw = fw;
+  p.base = base;
+  uint32_t a = __popc(plane_flags(fw, 0, g)) | (__popc(plane_flags(fw, 1, g)) << 16);
+  uint32_t b = __popc(plane_flags(fw, 2, g)) | (__popc(plane_flags(fw, 3, g)) << 16);
+  uint32_t ia = a, ib = b;                    // two tiles per scan: sums <= 256
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t ya = __shfl_up_sync(full, ia, o), yb = __shfl_up_sync(full, ib, o);
+    if (g >= o) { ia += ya; ib += yb; }
+  }
+  p.c01 = __shfl_sync(full, ia, 31);
+  p.c23 = __shfl_sync(full, ib, 31);
+  p.p01 = ia - a;
+  p.p23 = ib - b;
+  return p;
+}
+
+// payload index of lane g's first block of tile t
+__device__ __forceinline__ uint64_t tile_rank(const ChunkPlan &p, int t) {
+  const uint32_t lo01 = p.c01 & 0xFFFFu, hi01 = p.c01 >> 16, lo23 = p.c23 & 0xFFFFu;
+  switch (t) {
+    case 0: return p.base + (p.p01 & 0xFFFFu);
+    case 1: return p.base + lo01 + (p.p01 >> 16);
+    case 2: return p.base + lo01 + hi01 + (p.p23 & 0xFFFFu);
+    default: return p.base + lo01 + hi01 + lo23 + (p.p23 >> 16);
   }
 }
 
@@ -295,135 +341,177 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
   const int vw = (h.dims[0] % 8 == 0 && op % 32 == 0) ? 8
                  : (h.dims[0] % 4 == 0 && op % 16 == 0) ? 4 : 1;
   const FastDiv dx((uint32_t)h.ncx), dy((uint32_t)h.ncy);
-  while (true) {
-    uint64_t c = 0;
-    if (g == 0) c = atomicAdd(&cur->ticket, 1u);
-    c = __shfl_sync(full, c, 0);
-    if (c >= h.n_chunks) break;
-    if (g == 0) a.status_next[c * kStatusStride] = 0;
-    const uint32_t cr = dx.div((uint32_t)c);
-    const uint64_t cx = (uint32_t)c - cr * dx.d, cz = dy.div(cr), cy = cr - (uint32_t)cz * dy.d;
-    // flags of the chunk's 4 tiles: lane l holds word l
-    const uint32_t fw = __ldg(reinterpret_cast<const uint32_t *>(flags + 128 * c) + g);
-    const uint32_t chunk_cnt = __reduce_add_sync(full, (uint32_t)__popc(fw));
-    const bool publish = c != a.skip_publish_chunk;
-    const uint64_t excl = lookback(a.status_cur, c, (uint64_t)chunk_cnt << 32, publish,
-                                   &cur->err, a.wait_limit_ns) >> 32;
-    if (c == h.n_chunks - 1 && g == 0 && excl + chunk_cnt != h.nnz)
-      atomicOr(&cur->err, kErrCorrupt);
+  const uint64_t X = h.dims[0], Y = h.dims[1];
+  const float e2 = h.ebx2;
+  // chunks are dealt out statically: their payload offsets come from the
+  // offsets pass, so no chunk waits for another
+  const uint64_t n_warps = (uint64_t)gridDim.x * kDecWarps;
+  uint64_t c = (uint64_t)blockIdx.x * kDecWarps + (threadIdx.x >> 5);
+  bool oob = false;
+  uint32_t matched = 0, bad = 0;
 
-    // gather all four tiles: lane b copies plane b's present blocks (Listing
-    // 2 backwards: block k of the tile comes from payload[PreSum[k]])
-    uint64_t base = excl;
-    bool oob = false;
-#pragma unroll
-    for (int t = 0; t < kTilesPerChunk; ++t) {
-      const uint32_t F = (__shfl_sync(full, fw, 8 * t + (g >> 2)) >> (8 * (g & 3))) & 0xFFu;
-      const uint32_t pc = __popc(F);
-      uint32_t P = pc;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(full, P, o);
-        if (g >= o) P += y;
-      }
-      const uint32_t tile_cnt = __shfl_sync(full, P, 31);
-      uint64_t rank = base + P - pc;
-      uint32_t *dst = pbuf + 1024 * t + 32 * g;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const bool present = (F >> i) & 1u;
-        const bool valid = present && rank < h.nnz;
-        oob |= present && !valid;
-        cp_async16(dst + 4 * (i ^ (g & 7)), payload + 16 * (valid ? rank : 0), valid ? 16u : 0u);
-        rank += present;
-      }
-      cp_async_commit();
-      base += tile_cnt;
+  auto load_plan = [&](uint64_t cc) {
+    uint32_t fw = 0;
+    uint64_t base = 0;
+    if (cc < h.n_chunks) {
+      fw = __ldg(reinterpret_cast<const uint32_t *>(flags + 128 * cc) + g);
+      base = __ldg(a.chunk_off + cc);
     }
-    if (oob) atomicOr(&cur->err, kErrCorrupt);
-
-    // outliers of this chunk (rare path)
+    return plan_chunk(fw, base, g);
+  };
+  // the first chunk's four tiles are requested up front
+  ChunkPlan cp = load_plan(c);
+#pragma unroll
+  for (int t = 0; t < kTilesPerChunk; ++t) {
+    if (c < h.n_chunks) oob |= gather_tile(payload, h.nnz, pbuf + 1024 * t, plane_flags(cp.fw, t, g),
+                                           tile_rank(cp, t), g);
+    else cp_async_commit();
+  }
+  while (c < h.n_chunks) {
+    const uint64_t cn = c + n_warps;
+    // next chunk's flags and offset: in flight while tile 0 is decoded
+    uint32_t fw_n = 0;
+    uint64_t base_n = 0;
+    if (cn < h.n_chunks) {
+      fw_n = __ldg(reinterpret_cast<const uint32_t *>(flags + 128 * cn) + g);
+      base_n = __ldg(a.chunk_off + cn);
+    }
     uint64_t o_lo = 0, o_hi = 0;
     if (h.nout) {
-      if (g == 0) {
-        o_lo = lower_bound_rec(recs, h.nout, (uint32_t)(c * kChunkCodes));
-        o_hi = lower_bound_rec(recs, h.nout, (uint32_t)((c + 1) * kChunkCodes));
-      }
-      o_lo = __shfl_sync(full, o_lo, 0);
-      o_hi = __shfl_sync(full, o_hi, 0);
+      o_lo = __ldg(a.chunk_olo + c);
+      o_hi = c + 1 < h.n_chunks ? __ldg(a.chunk_olo + c + 1) : h.nout;
     }
-    uint32_t matched = 0;
+    const uint32_t cr = dx.div((uint32_t)c);
+    const uint64_t cx = (uint32_t)c - cr * dx.d, cz = dy.div(cr), cy = cr - (uint32_t)cz * dy.d;
     const bool edge = (cx + 1) * G::CX > h.dims[0] || (cy + 1) * G::CY > h.dims[1] ||
                       (cz + 1) * G::CZ > h.dims[2];
+    // origin of lane g's brick in tile 0, and per-tile / per-row strides
+    const int bx = g % G::NBX, by = g / G::NBX;
+    uint64_t x0, y0, z0;
+    if constexpr (NDIM == 3) {
+      x0 = cx * 32 + 8 * bx; y0 = cy * 32 + 4 * by; z0 = cz * 8;
+    } else if constexpr (NDIM == 2) {
+      x0 = cx * 64 + 8 * bx; y0 = cy * 128 + 8 * by; z0 = 0;
+    } else {
+      x0 = cx * 8192 + 64 * g; y0 = 0; z0 = 0;
+    }
+    ChunkPlan np{};
     int32_t carry[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) carry[e] = 0;
 #pragma unroll 1
     for (int t = 0; t < kTilesPerChunk; ++t) {
-      switch (t) {
-        case 0: cp_async_wait<3>(); break;
-        case 1: cp_async_wait<2>(); break;
-        case 2: cp_async_wait<1>(); break;
-        default: cp_async_wait<0>(); break;
-      }
+      cp_async_wait<3>();                // this tile's group (3 newer ones may pend)
       __syncwarp();
-      const uint32_t *pb = pbuf + 1024 * t;
+      uint32_t *pb = pbuf + 1024 * t;
       uint32_t w[32];
 #pragma unroll
       for (int b = 0; b < 32; ++b) w[b] = pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)];
-      // an escape (0x8000) has its sign plane set and every magnitude plane
-      // clear: find them on the planes, before the transpose
+      __syncwarp();                      // the buffer is free: refill it for the next chunk
+      if (t == 0) np = plan_chunk(fw_n, base_n, g);
+      if (cn < h.n_chunks)
+        oob |= gather_tile(payload, h.nnz, pb, plane_flags(np.fw, t, g), tile_rank(np, t), g);
+      else
+        cp_async_commit();
+      // codes on the bit planes (before the transpose): bit t of a mask is
+      // word t of this lane's brick, low code (even element) or high code
       uint32_t lo_or = 0, hi_or = 0;
 #pragma unroll
       for (int b = 0; b < 15; ++b) { lo_or |= w[b]; hi_or |= w[b + 16]; }
-      const uint32_t esc_even = w[15] & ~lo_or, esc_odd = w[31] & ~hi_or;
+      uint32_t esc_ev = w[15] & ~lo_or, esc_od = w[31] & ~hi_or;   // 0x8000: an escape
+      // this tile's brick origin
+      uint64_t bxo = x0, byo = y0, bzo = z0;
+      if constexpr (NDIM == 3) bzo += 2 * t;
+      else if constexpr (NDIM == 2) byo += 32 * t;
+      else bxo += 2048 * t;
+      if (edge) {
+        // padding codes must be 0; escapes count only inside the field
+        const uint32_t lx = extent_in(bxo, X, G::BX);
+        const uint32_t ly = extent_in(byo, Y, G::BY);
+        const uint32_t lz = extent_in(bzo, h.dims[2], G::BZ);
+        uint32_t in_ev, in_od;
+        inside_masks<NDIM>(lx, ly, lz, in_ev, in_od);
+        bad |= ((lo_or | w[15]) & ~in_ev) | ((hi_or | w[31]) & ~in_od);
+        esc_ev &= in_ev;
+        esc_od &= in_od;
+      }
       transpose32(w);                    // lane g: the 32 code words of brick g
       int32_t v[64];
-      decode_codes(w, v);
-      if (__any_sync(full, (esc_even | esc_odd) != 0 || edge)) {
-        // rare path: patch escapes from the outlier list; padding must be 0.
-        // Fully unrolled so that v and w stay in registers.
-        const uint64_t tile = c * kTilesPerChunk + t;
-        uint32_t bad = 0;
+      decode_codes(w, v);                // an escape decodes to 0
+      if (__any_sync(full, (esc_ev | esc_od) != 0)) {
+        // rare: patch each escape with its recorded residual
+        const uint32_t tile_code0 = (uint32_t)((c * kTilesPerChunk + t) * kTileCodes) + 64 * g;
+        while (esc_ev | esc_od) {
+          int e;
+          if (esc_ev) { e = 2 * (__ffs(esc_ev) - 1); esc_ev &= esc_ev - 1; }
+          else { e = 2 * (__ffs(esc_od) - 1) + 1; esc_od &= esc_od - 1; }
+          int32_t val;
+          if (find_outlier(recs, o_lo, o_hi, tile_code0 + e, &val)) {
+            ++matched;
 #pragma unroll
-        for (int e = 0; e < 64; ++e) {
-          const uint32_t code = (w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
-          uint64_t x, y, z;
-          elem_coord<NDIM>(cx, cy, cz, t, g, e, x, y, z);
-          const bool inside = x < h.dims[0] && y < h.dims[1] && z < h.dims[2];
-          bad |= (!inside && code != 0);
-          if (inside && code == 0x8000u) {
-            int32_t val;
-            if (find_outlier(recs, o_lo, o_hi, (uint32_t)(tile * kTileCodes + 64 * g + e), &val)) {
-              v[e] = val;
-              ++matched;
-            } else {
-              bad = 1;
-            }
+            for (int k = 0; k < 64; ++k) v[k] = k == e ? val : v[k];
+          } else {
+            bad = 1;
           }
         }
-        if (bad) atomicOr(&cur->err, kErrCorrupt);
       }
       // the chunk origin carries the float bias of 1.5*2^23 into every q
       if (t == 0 && g == 0) v[0] += (int32_t)kMagicBits;
       inverse_lorenzo<NDIM>(v, carry, g);
-      store_brick<NDIM>(a, h, v, cx, cy, cz, t, g, edge, vw);
-    }
-    __syncwarp();                        // plane buffers free for the next chunk
-    if (h.nout) {
-      const uint32_t m = __reduce_add_sync(full, matched);
-      if (g == 0) {
-        if (m != o_hi - o_lo) atomicOr(&cur->err, kErrCorrupt);
-        atomicAdd(reinterpret_cast<unsigned long long *>(&cur->nout), (unsigned long long)m);
+      // q -> fl(float(q) * 2eb), 8-float rows
+      float *base = a.out + bxo + X * (byo + Y * bzo);
+#pragma unroll
+      for (int row = 0; row < 8; ++row) {
+        float f[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          f[k] = __fmul_rn(__fsub_rn(__int_as_float(v[8 * row + k]), kRoundMagic), e2);
+        int iy, iz, ix;
+        if constexpr (NDIM == 3) { ix = 0; iy = row % 4; iz = row / 4; }
+        else if constexpr (NDIM == 2) { ix = 0; iy = row; iz = 0; }
+        else { ix = 8 * row; iy = 0; iz = 0; }
+        float *dst = base + ix + X * (iy + Y * iz);
+        const bool row_in = !edge || (byo + iy < Y && bzo + iz < h.dims[2]);
+        const bool full_row = !edge || (row_in && bxo + ix + 8 <= X);
+        if (full_row && vw == 8) {
+          asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst),
+                       "f"(f[0]), "f"(f[1]), "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]),
+                       "f"(f[6]), "f"(f[7])
+                       : "memory");
+        } else if (full_row && vw == 4) {
+          __stcs(reinterpret_cast<float4 *>(dst), make_float4(f[0], f[1], f[2], f[3]));
+          __stcs(reinterpret_cast<float4 *>(dst) + 1, make_float4(f[4], f[5], f[6], f[7]));
+        } else if (row_in) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (bxo + ix + k < X) __stcs(dst + k, f[k]);
+        }
       }
     }
+    if (h.nout) {
+      const uint32_t m = __reduce_add_sync(full, matched);
+      if (g == 0 && m != o_hi - o_lo) atomicOr(&cur->err, kErrCorrupt);
+      if (g == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&cur->nout), (unsigned long long)m);
+      matched = 0;
+    }
+    c = cn;
   }
+  cp_async_wait<0>();
+  if (__any_sync(full, oob || bad != 0) && g == 0) atomicOr(&cur->err, kErrCorrupt);
 }
 
-__global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const DecompressArgs a) {
-  extern __shared__ __align__(16) uint32_t dsmem[];
+// Offsets pass: each block owns a unit of kOffChunks consecutive chunks
+// (ticketed in order), one chunk per thread: it counts the chunk's non-zero
+// blocks from its 128 flag bytes, scans the counts over the block and takes
+// the unit's offset by decoupled look-back, then writes every chunk's first
+// payload block and, with outliers, its first outlier record.  It also
+// validates the header and prepares the next call's scratch.
+__global__ void __launch_bounds__(kOffChunks) dec_offsets_kernel(const DecompressArgs a) {
+  const unsigned full = 0xffffffffu;
+  __shared__ uint32_t warp_tot[kOffChunks / 32];
+  __shared__ uint64_t s_unit, s_excl;
   SetScratch *cur = a.set_cur;
-  const int w = threadIdx.x >> 5;
+  const int g = threadIdx.x & 31, w = threadIdx.x >> 5;
   const Hdr h = read_header(a);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     SetScratch *nx = a.set_next;
@@ -436,16 +524,82 @@ __global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const Dec
     cur->hdr_nout = h.ok ? (uint32_t)h.nout : 0;
   }
   if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
+  const uint64_t n_units = cdiv(h.n_chunks, kOffChunks);
+  if (threadIdx.x == 0) s_unit = atomicAdd(&cur->ticket, 1u);
+  __syncthreads();
+  const uint64_t u = s_unit;
+  if (u >= n_units) return;                          // the same in the whole block
+  const uint64_t c = u * kOffChunks + threadIdx.x;
+  uint32_t cnt = 0;
+  if (c < h.n_chunks) {
+    const uint4 *f = reinterpret_cast<const uint4 *>(a.in + 64 + 128 * c);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint4 v = __ldg(f + i);
+      cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    }
+  }
+  uint32_t inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(full, inc, o);
+    if (g >= o) inc += y;
+  }
+  if (g == 31) warp_tot[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    // the unit's total, its look-back, and the warps' exclusive offsets
+    const uint32_t t = g < kOffChunks / 32 ? warp_tot[g] : 0u;
+    uint32_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(full, ti, o);
+      if (g >= o) ti += y;
+    }
+    const uint32_t total = __shfl_sync(full, ti, 31);
+    const bool publish = a.skip_publish_chunk >= h.n_chunks ||
+                         u != a.skip_publish_chunk / kOffChunks;
+    const uint64_t excl = lookback(a.status_cur, u, total, publish, &cur->err, a.wait_limit_ns);
+    if (g < kOffChunks / 32) warp_tot[g] = ti - t;
+    if (g == 0) {
+      s_excl = excl;
+      a.status_next[u * kStatusStride] = 0;            // for the next call
+      if (u == n_units - 1 && excl + total != h.nnz) atomicOr(&cur->err, kErrCorrupt);
+    }
+  }
+  __syncthreads();
+  if (c < h.n_chunks) {
+    const uint64_t off = s_excl + warp_tot[w] + inc - cnt;
+    if (off + cnt > h.nnz) atomicOr(&cur->err, kErrCorrupt);
+    a.chunk_off[c] = (uint32_t)off;
+    if (h.nout) {
+      const uint2 *recs = reinterpret_cast<const uint2 *>(a.in + 64 + 32 * h.n_tiles + 16 * h.nnz);
+      a.chunk_olo[c] = (uint32_t)lower_bound_rec(recs, h.nout, (uint32_t)(c * kChunkCodes));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const DecompressArgs a) {
+  extern __shared__ __align__(16) uint32_t dsmem[];
+  SetScratch *cur = a.set_cur;
+  const int w = threadIdx.x >> 5;
+  const Hdr h = read_header(a);
+  if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
   uint32_t *pbuf = dsmem + w * kTilesPerChunk * 1024;
   if (h.ndim == 3) decompress_chunks<3>(a, h, pbuf, cur);
   else if (h.ndim == 2) decompress_chunks<2>(a, h, pbuf, cur);
   else decompress_chunks<1>(a, h, pbuf, cur);
 }
 
+cudaError_t launch_dec_offsets(const DecompressArgs &a, uint64_t max_chunks, cudaStream_t s) {
+  const uint64_t blocks = (max_chunks + kOffChunks - 1) / kOffChunks;
+  dec_offsets_kernel<<<(unsigned)(blocks ? blocks : 1), kOffChunks, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(decompress_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kDecSmemBytes);
+  const cudaError_t e = cudaFuncSetAttribute(
+      decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmemBytes);
   if (e != cudaSuccess) return e;
   decompress_kernel<<<grid, kDecWarps * 32, kDecSmemBytes, s>>>(a);
   return cudaGetLastError();
@@ -459,6 +613,10 @@ int decompress_blocks_per_sm() {
                                                     kDecSmemBytes) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
+}
+
+uint64_t decompress_status_words(uint64_t n_chunks) {
+  return (n_chunks + kOffChunks - 1) / kOffChunks;
 }
 
 }  // namespace fz

@@ -7,6 +7,10 @@
 
 namespace fz {
 
+// kernels timed by fz_get_kernel_times: range, compress, outliers,
+// decompress, decompression offsets
+constexpr int kProfSlots = 5;
+
 struct SetScratch;
 struct RangeResult;
 struct FastDiv;
@@ -38,7 +42,9 @@ struct DecompressArgs {
   uint64_t out_cap_elems;
   SetScratch *set_cur, *set_next;
   uint64_t *status_cur, *status_next;
-  uint64_t status_cap;         // entries available in the status arrays
+  uint64_t status_cap;         // entries available in the status and chunk arrays
+  uint32_t *chunk_off;         // per chunk: first payload block (offsets pass)
+  uint32_t *chunk_olo;         // per chunk: first outlier record (offsets pass)
   uint64_t wait_limit_ns;
   uint64_t skip_publish_chunk;
 };
@@ -57,7 +63,12 @@ cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *
                             cudaStream_t s);
 cudaError_t launch_outliers(int ndim, const CompressArgs &a, uint64_t out_section,
                             cudaStream_t s);
+// offsets pass (header check, per-chunk payload and outlier offsets) over
+// at most max_chunks chunks, then the decompression proper
+cudaError_t launch_dec_offsets(const DecompressArgs &a, uint64_t max_chunks, cudaStream_t s);
 cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s);
+// look-back status words the offsets pass uses and clears in the other set
+uint64_t decompress_status_words(uint64_t n_chunks);
 
 // concatenation of slab streams (fz_shard.cu)
 struct ConcatPart {

@@ -226,20 +226,24 @@ def test_corrupt_streams(codec, torch):
 
 
 def test_bounded_wait_times_out_and_recovers(codec, torch):
-    """A chunk that never publishes its look-back aggregate: the successors'
+    """A unit that never publishes its look-back aggregate: the successors'
     bounded waits give up and the call reports FZ_ERR_TIMEOUT; the context
-    and the GPU stay usable."""
+    and the GPU stay usable.  The compressor's units are 11 tiles, the
+    decompressor's offsets pass takes 512 chunks per unit, so the second
+    field spans two of those."""
     x = fields.grf((32, 128, 128), -3.0, 6).astype(np.float32)
+    y = fields.grf((72, 256, 256), -3.0, 7).astype(np.float32)     # 576 chunks
+    _, s = oracle.compress(y, 3, fz.EB_REL, 1e-3)
     codec.set_wait_limit_ns(20_000_000)
     codec.debug_skip_publish(5)
     try:
         assert _status(codec, torch, x, 3, fz.EB_REL, 1e-3)[0] == fz.ERR_TIMEOUT
-        _, s = oracle.compress(x, 3, fz.EB_REL, 1e-3)
-        assert _dec_status(codec, torch, s) == fz.ERR_TIMEOUT
+        assert _dec_status(codec, torch, s, cap=y.size) == fz.ERR_TIMEOUT
     finally:
         codec.debug_skip_publish(None)
         codec.set_wait_limit_ns(2_000_000_000)
     check_parity(codec, torch, x, 3, fz.EB_REL, 1e-3)
+    check_parity(codec, torch, y, 3, fz.EB_REL, 1e-3)
 
 
 # ------------------------------------------------------------ host API
