@@ -42,6 +42,36 @@ WORKLOAD_DESC = ("512x512x512 float32 lognormal density exp(0.5 g), g a unit-std
                  "value-range-relative error bound 1e-3")
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# each kernel on the 512^3 workload, from one ncu capture of this benchmark
+# (summarised in profiles/launches_cosmo3d_512.md).  A figure stands only while
+# the kernel's sources are the ones that were captured (SHA-256 over them).
+TRAFFIC = {
+    "compress_kernel": (("fz_compress.cu", "fz_device.cuh", "fz_kernels.h"),
+                        "7848fa3be9332971cd7adf5c3acfb507362f658e856f28641d94bd81efee1463",
+                        537911552 + 75093504),
+    "decompress_kernel": (("fz_decompress.cu", "fz_device.cuh", "fz_kernels.h"),
+                          "a2b4d2184226bfdbc91457a554e229f0e0184ada3926d18b2c5e6100ad6be55c",
+                          96762624 + 471520512),
+    "range_kernel": (("fz_compress.cu", "fz_device.cuh", "fz_kernels.h"),
+                     "7848fa3be9332971cd7adf5c3acfb507362f658e856f28641d94bd81efee1463",
+                     536888832 + 2733312),
+}
+
+
+def traffic_bytes(kernel: str, size: int):
+    """Captured DRAM bytes per launch, or None (other size, changed sources)."""
+    import hashlib
+    if size != 512 or kernel not in TRAFFIC:
+        return None
+    files, digest, nbytes = TRAFFIC[kernel]
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2304_12557_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return nbytes if h.hexdigest() == digest else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -259,11 +289,14 @@ def run_ours(args, rank, world, local_rank, dist):
     peak, peak_kind = peaks()
     achieved = kern[dom][1] / (kern[dom][0] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_bytes(dom, args.size),
             "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes_per_launch": kern[dom][1],
+            "traffic_unit": "bytes per launch (ncu DRAM read + write)",
             "kernels": {k: {"ms": v[0], "GB/s": v[1] / (v[0] / 1e3) / 1e9,
-                            "frac": v[1] / (v[0] / 1e3) / 1e9 / peak}
+                            "frac": v[1] / (v[0] / 1e3) / 1e9 / peak,
+                            "traffic": traffic_bytes(k, args.size)}
                         for k, v in kern.items()}}
 
     # end to end through the host-buffer calls (pinned host memory)
