@@ -217,6 +217,59 @@ int fz_concat_streams_host(const void *const *h_parts,
                            uint64_t out_capacity, uint64_t *out_size);
 
 /* ---------------------------------------------------------------------
+ * Many fields in one persistent launch.  A batch is planned once for a fixed
+ * list of fields (their device buffers, dims and bounds); every run
+ * compresses the fields' current contents.  A run is one range pass over the
+ * relative-bound fields, one small per-field preparation, one persistent
+ * compression launch per dimensionality present (every field with its own
+ * look-back domain, so each field's stream is byte for byte what
+ * fz_compress makes of it alone), one escape pass per dimensionality and one
+ * copy of the per-field results to the host: a fixed sequence, captured in a
+ * CUDA graph and replayed on later runs (fz_batch_set_graph).  The paper
+ * has no counterpart; its future-work section asks for fusing the kernels. */
+
+typedef struct fz_field {
+  const float *d_in;      /* device, 4-byte aligned; dims as fz_compress     */
+  uint64_t dims[3];
+  int32_t ndim;
+  int32_t mode;           /* FZ_EB_ABS or FZ_EB_REL                          */
+  double eb;
+  void *d_out;            /* device, 16-byte aligned                         */
+  uint64_t out_capacity;  /* bytes                                           */
+} fz_field;
+
+typedef struct fz_batch fz_batch;
+
+#define FZ_BATCH_MAX_FIELDS 65536
+
+/* Plan a batch of n fields on ctx's device: validates every field (FZ_ERR_ARG;
+ * FZ_ERR_CAPACITY when an output cannot hold the header and flags) and
+ * allocates the batch's descriptors and scratch (FZ_ERR_CUDA).  The batch
+ * keeps ctx for later calls; destroy the batch before the context. */
+int fz_batch_create(fz_ctx *ctx, const fz_field *fields, int n, fz_batch **batch);
+
+/* Release a batch.  NULL is allowed. */
+void fz_batch_destroy(fz_batch *batch);
+
+/* Run the batch on `stream` and wait for it.  out_sizes[i] and statuses[i]
+ * (host arrays of n) receive each field's stream size and status, as
+ * fz_compress would report them.  Returns FZ_OK when every field succeeded,
+ * else the first failing field's status (FZ_ERR_CUDA for the run itself). */
+int fz_batch_compress(fz_batch *batch, uint64_t *out_sizes, int *statuses, void *stream);
+
+/* Capture runs in a CUDA graph (default on) or launch them directly. */
+int fz_batch_set_graph(fz_batch *batch, int on);
+
+/* Autotune the batch's load path: time `reps` runs with TMA tile loads for
+ * the fields whose rows allow them (2-D/3-D, rows 16-byte aligned) and
+ * `reps` runs with direct loads for every field, and keep the faster.  The
+ * outputs are overwritten by the trial runs.  fz_batch_tuning reports the
+ * choice (1: TMA) and the median run times in ms ([0] direct, [1] TMA; 0
+ * before tuning). */
+int fz_batch_autotune(fz_batch *batch, int reps, void *stream);
+int fz_batch_tuning(const fz_batch *batch, int *tma_on, double ms[2]);
+
+/* ---------------------------------------------------------------------
  * Compression without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * GPU memory while they run, e.g. an application whose memory pool has

@@ -17,7 +17,7 @@ __all__ = ["Codec", "FZError", "load_library", "library_path", "EB_ABS",
            "EB_REL", "OK", "ERR_ARG", "ERR_CAPACITY", "ERR_NONFINITE",
            "ERR_EB_RANGE", "ERR_CORRUPT", "ERR_TIMEOUT", "ERR_CUDA",
            "compress_bound", "stream_min_bytes", "inspect", "shard_extent",
-           "concat_streams_host", "C_API"]
+           "concat_streams_host", "Batch", "C_API"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libfz_gb300.so")
@@ -40,7 +40,9 @@ C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
          "fz_set_wait_limit_ns", "fz_debug_skip_publish",
          "fz_set_profiling", "fz_get_kernel_times", "fz_range",
          "fz_compress_ranged", "fz_shard_extent", "fz_concat_streams",
-         "fz_concat_streams_host", "fz_compress_noalloc"]
+         "fz_concat_streams_host", "fz_batch_create", "fz_batch_destroy",
+         "fz_batch_compress", "fz_batch_set_graph", "fz_batch_autotune",
+         "fz_batch_tuning", "fz_compress_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -63,6 +65,12 @@ class _Info(ctypes.Structure):
                 ("range_max", ctypes.c_float), ("n_tiles", _u64),
                 ("nnz_blocks", _u64), ("n_outliers", _u64),
                 ("stream_bytes", _u64)]
+
+
+class _Field(ctypes.Structure):
+    _fields_ = [("d_in", _vp), ("dims", _u64 * 3), ("ndim", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("eb", ctypes.c_double),
+                ("d_out", _vp), ("out_capacity", _u64)]
 
 
 def library_path() -> str:
@@ -121,6 +129,16 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_concat_streams_host.argtypes = [ctypes.POINTER(_vp), dims_t,
                                              ctypes.c_int, _vp, _u64,
                                              ctypes.POINTER(_u64)]
+        L.fz_batch_create.argtypes = [_vp, ctypes.POINTER(_Field), ctypes.c_int,
+                                      ctypes.POINTER(_vp)]
+        L.fz_batch_destroy.argtypes = [_vp]
+        L.fz_batch_destroy.restype = None
+        L.fz_batch_compress.argtypes = [_vp, ctypes.POINTER(_u64),
+                                        ctypes.POINTER(ctypes.c_int), _vp]
+        L.fz_batch_set_graph.argtypes = [_vp, ctypes.c_int]
+        L.fz_batch_autotune.argtypes = [_vp, ctypes.c_int, _vp]
+        L.fz_batch_tuning.argtypes = [_vp, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_double)]
         _lib = L
         return L
 
@@ -183,6 +201,78 @@ def concat_streams_host(parts) -> bytes:
     if st != OK:
         raise FZError(st, "fz_concat_streams_host")
     return out.raw[: int(total.value)]
+
+
+class Batch:
+    """A planned batch: many fields compressed by one persistent launch per
+    dimensionality (see fz_batch_create).  `fields` is a list of
+    (x, out, mode, eb[, ndim]) with x a contiguous float32 CUDA tensor
+    indexed [z, y, x] and out a uint8 CUDA tensor for its stream.  The tensors
+    must stay alive (and in place) while the batch is used."""
+
+    def __init__(self, codec, fields):
+        self._L = load_library()
+        self._codec = codec
+        self._keep = []
+        arr = (_Field * len(fields))()
+        for i, spec in enumerate(fields):
+            x, out, mode, eb = spec[:4]
+            ndim = spec[4] if len(spec) > 4 else x.dim()
+            assert x.is_cuda and x.is_contiguous() and out.is_cuda
+            dims = list(x.shape[::-1])[:ndim] + [1] * (3 - ndim)
+            arr[i].d_in = x.data_ptr()
+            arr[i].dims = (_u64 * 3)(*[int(d) for d in dims])
+            arr[i].ndim = ndim
+            arr[i].mode = _mode(mode)
+            arr[i].eb = float(eb)
+            arr[i].d_out = out.data_ptr()
+            arr[i].out_capacity = out.numel() * out.element_size()
+            self._keep.append((x, out))
+        self.n = len(fields)
+        self._h = _vp()
+        st = self._L.fz_batch_create(codec._ctx, arr, self.n, ctypes.byref(self._h))
+        if st != OK:
+            raise FZError(st, "fz_batch_create")
+        self._sizes = (_u64 * self.n)()
+        self._st = (ctypes.c_int * self.n)()
+
+    def compress(self, stream=None):
+        """Run the batch; returns (sizes, statuses) lists."""
+        st = self._L.fz_batch_compress(self._h, self._sizes, self._st,
+                                       Codec._stream(stream))
+        if st == ERR_CUDA:
+            raise FZError(st, "fz_batch_compress")
+        return list(self._sizes), list(self._st)
+
+    def set_graph(self, on: bool):
+        st = self._L.fz_batch_set_graph(self._h, int(bool(on)))
+        if st != OK:
+            raise FZError(st, "fz_batch_set_graph")
+
+    def autotune(self, reps: int = 3, stream=None):
+        st = self._L.fz_batch_autotune(self._h, int(reps), Codec._stream(stream))
+        if st != OK:
+            raise FZError(st, "fz_batch_autotune")
+        return self.tuning()
+
+    def tuning(self):
+        on = ctypes.c_int()
+        ms = (ctypes.c_double * 2)()
+        st = self._L.fz_batch_tuning(self._h, ctypes.byref(on), ms)
+        if st != OK:
+            raise FZError(st, "fz_batch_tuning")
+        return {"tma": bool(on.value), "ms_direct": ms[0], "ms_tma": ms[1]}
+
+    def close(self):
+        if self._h:
+            self._L.fz_batch_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _mode(mode) -> int:

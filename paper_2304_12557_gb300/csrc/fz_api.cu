@@ -46,6 +46,10 @@ struct fz_ctx {
   bool ev_used[fz::kProfSlots] = {};
 };
 
+namespace fz {
+int context_device(const fz_ctx *c) { return c ? c->device : -1; }
+}  // namespace fz
+
 namespace {
 
 struct DeviceGuard {

@@ -1,0 +1,855 @@
+// fz_compress_impl.cuh -- the compression kernels' device code, shared by the
+// single-field launch (fz_compress.cu) and the batched launch (fz_batch.cu).
+//
+//  compress_kernel  persistent blocks of kCompWarps compute warps and one
+//                   scan warp; one 2048-code tile per compute warp and round:
+//                   32-byte row loads or a TMA box -> pre-quantisation
+//                   (Sec. 2.3) -> chunk-local Lorenzo residual (Sec. 2.3,
+//                   3.1) -> sign-magnitude codes (Sec. 3.2) -> 32x32
+//                   bitshuffle (Sec. 3.3) -> zero-block flags (Sec. 3.4,
+//                   Listing 1) -> decoupled look-back on units of tiles ->
+//                   compacted 16-byte block stores (Listing 2).
+//  outlier_kernel   rare path: writes the escaped residuals of the tiles that
+//                   had any, at offsets found by compress_kernel.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "fz_device.cuh"
+#include "fz_kernels.h"
+
+namespace fz {
+
+// ====================================================================
+// compression: persistent blocks, one 2048-code tile per warp and round
+// ====================================================================
+//
+// One block per SM: kCompWarps compute warps and one scan warp.  Each round
+// the scan warp takes a ticket for a unit of kCompWarps consecutive tiles
+// (stream order); compute warp j does tile j of the unit: pre-quantisation,
+// Lorenzo, codes, bitshuffle, flags, and posts the tile's aggregate (blocks,
+// outliers) in shared memory.  The scan warp sums the unit, runs the
+// decoupled look-back on the unit index and hands every warp its tile's
+// exclusive prefix, which the warp uses two rounds later to store the
+// compacted blocks.  The look-back therefore walks one status word per
+// unit, and its latency is hidden behind the compute warps' next tiles.
+// A compute warp's input comes either from a per-warp TMA box (its tile,
+// loaded one round ahead) or, for fields whose rows are not 16-byte aligned
+// and for 1-D fields, straight from global memory.
+
+constexpr int kCompWarps = 11;                  // compute warps per block
+constexpr int kCompThreads = 32 * (kCompWarps + 1);   // + the scan warp
+constexpr int kRing = 4;                        // rounds in flight per block
+// Each warp stores a tile's compacted blocks two rounds after computing it,
+// so that the scan warp has two tiles' time to resolve the tile's prefix:
+// three plane buffers per warp.
+constexpr int kPlaneBufs = 3;
+// per compute warp: [TMA box 8 KB][plane buffers 0..2, 4 KB each]
+constexpr int kBoxStride = 8192 + kPlaneBufs * 4096;
+constexpr int kPlaneOff = 8192;
+constexpr int kHalf2D = 4096;                   // second x half of a 2-D box
+constexpr uint32_t kTileBoxBytes = 32 * 32 * 2 * 4;  // one tile (3-D: 2 planes; 2-D: 2 halves)
+
+// the rounds a block has in flight, in shared memory behind the warps' areas
+struct RoundSlot {
+  uint64_t unit;                 // ticket: the launch's unit index
+  uint32_t field, local;         // its field, and its index among the field's units:
+                                 // tiles [local * kCompWarps, local * kCompWarps + kCompWarps)
+  uint64_t agg[kCompWarps];      // tile aggregates, (blocks << 32) | outliers
+  uint64_t excl[kCompWarps];     // their exclusive prefixes in the stream
+};
+struct CompShared {
+  uint64_t box_bar[kCompWarps];  // per compute warp: its TMA box landed
+  uint64_t ticket_bar[kRing];    // 1 arrival: the scan warp posted the unit
+  uint64_t agg_bar[kRing];       // kCompWarps arrivals: every aggregate posted
+  uint64_t excl_bar[kRing];      // kCompWarps arrivals: every prefix posted
+  RoundSlot slot[kRing];
+};
+// What the kernel derives once per field: the bound (Sec. 4.1), the range it
+// came from, whether the quantiser takes the field, and the chunk grid's
+// divisors.
+struct FieldRt {
+  EbParams p;
+  float fmin, fmax;
+  uint32_t ok;
+  FastDiv dx, dy;
+};
+
+// A batch: several fields in one launch.  Units of kCompWarps consecutive
+// tiles never straddle a field, so every field keeps its own look-back
+// domain, result block and stream.
+struct BatchArgs {
+  const CompressArgs *fields;    // per field (device)
+  const FieldRt *rt;             // per field, written by the batch's prepare pass
+  const CUtensorMap *tmaps;      // per field (TMA launches), 64-byte aligned
+  const uint2 *unit_map;         // per unit of the launch: (field, unit within the field)
+  uint64_t n_units;
+  uint32_t *ticket;              // the launch's unit counter, zero at launch
+};
+
+constexpr int kCompSmemTma = kCompWarps * kBoxStride + (int)sizeof(CompShared) + 1024;
+constexpr int kCompSmemLdg = kCompWarps * kPlaneBufs * 4096 + (int)sizeof(CompShared) + 1024;
+static_assert(kCompSmemTma <= 227 * 1024, "shared memory per block");
+
+// bounded wait on an mbarrier phase by a whole warp; the result is uniform
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+  const bool ok = mbar_wait_bounded(bar, parity, limit_ns);
+  return __all_sync(0xffffffffu, ok);
+}
+
+// 8 consecutive floats from p.  V = 8: one 32-byte load (p 32-byte
+// aligned); V = 4: two 16-byte loads; V = 1: scalar loads.
+template <int V>
+__device__ __forceinline__ void load8(const float *p, float (&f)[8]) {
+  if constexpr (V == 8) {
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(f[0]), "=f"(f[1]), "=f"(f[2]), "=f"(f[3]), "=f"(f[4]), "=f"(f[5]),
+          "=f"(f[6]), "=f"(f[7])
+        : "l"(p));
+  } else if constexpr (V == 4) {
+    const float4 a = __ldcs(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldcs(reinterpret_cast<const float4 *>(p) + 1);
+    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+    f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = __ldcs(p + k);
+  }
+}
+
+// The value range a relative bound is taken against (Sec. 4.1): the range
+// pass's result, or the caller's range (a slab of a field split across
+// ranks uses the whole field's).  Absolute bounds have none.
+__device__ __forceinline__ void field_range(const CompressArgs &a, float &fmin, float &fmax,
+                                            bool &nonfinite) {
+  if (a.mode != 1) return;
+  if (a.range_given) {
+    fmin = a.range_lo; fmax = a.range_hi;
+  } else {
+    fmin = a.range->fmin; fmax = a.range->fmax;
+    nonfinite = a.range->nonfinite != 0;
+  }
+}
+
+// fl(v + 1.5*2^23) of v = fl(x * r): the integer rint(v) sits in the low
+// mantissa bits; returned as raw bits (biased by kMagicBits).
+__device__ __forceinline__ int32_t quant_bits(float x, float r) {
+  return (int32_t)__float_as_uint(__fadd_rn(__fmul_rn(x, r), kRoundMagic));
+}
+
+// The per-field derivation: bound from the request and the range, the
+// quantiser's range check for relative bounds (the element of largest
+// magnitude is in the field, and fp multiply and rounding are monotone, so
+// checking it checks every element), and the error bits that stop the field.
+__device__ __forceinline__ FieldRt derive_field(const CompressArgs &a, uint32_t &err) {
+  FieldRt rt;
+  float fmin = 0.f, fmax = 0.f;
+  bool nonfinite = false;
+  field_range(a, fmin, fmax, nonfinite);
+  rt.p = derive_eb(a.mode, a.eb_req, fmin, fmax);
+  rt.fmin = fmin;
+  rt.fmax = fmax;
+  bool ok = rt.p.ok && !nonfinite;
+  err = 0;
+  if (ok && a.mode == 1 && !a.range_given) {
+    const float m = fmaxf(fabsf(fmin), fabsf(fmax));
+    const uint32_t b = (uint32_t)quant_bits(m, rt.p.ebx2_r) - kBiasBits;
+    ok = b <= kBiasedMax;
+    if (!ok) err |= kErrRange;
+  }
+  if (!rt.p.ok) err |= kErrEbParam;
+  if (nonfinite) err |= kErrNonFinite;
+  rt.ok = ok;
+  rt.dx = FastDiv(a.ncx);
+  rt.dy = FastDiv(a.ncy);
+  return rt;
+}
+
+struct TileGeo {
+  uint64_t x0, y0, z0;       // origin of this lane's brick
+  uint64_t cx, cy, cz;       // chunk coordinates
+  int t, bx, by;
+  bool edge;                 // the chunk reaches past the field
+};
+
+// chunk grid divisors, built once per warp
+struct ChunkGrid {
+  FastDiv x, y;
+  __device__ explicit ChunkGrid(const CompressArgs &a) : x(a.ncx), y(a.ncy) {}
+  __device__ ChunkGrid(const FastDiv &dx, const FastDiv &dy) : x(dx), y(dy) {}
+};
+
+template <int NDIM>
+__device__ __forceinline__ TileGeo tile_geo(const CompressArgs &a, const ChunkGrid &cg,
+                                            uint64_t T, int g) {
+  using G = Geo<NDIM>;
+  TileGeo q;
+  const uint32_t c = (uint32_t)(T >> 2);             // < 2^19
+  q.t = (int)(T & 3);
+  const uint32_t r = cg.x.div(c);
+  q.cx = c - r * cg.x.d;
+  q.cz = cg.y.div(r);
+  q.cy = r - (uint32_t)q.cz * cg.y.d;
+  q.bx = g % G::NBX;
+  q.by = g / G::NBX;
+  if constexpr (NDIM == 3) {
+    q.x0 = q.cx * 32 + 8 * q.bx; q.y0 = q.cy * 32 + 4 * q.by; q.z0 = q.cz * 8 + 2 * q.t;
+  } else if constexpr (NDIM == 2) {
+    q.x0 = q.cx * 64 + 8 * q.bx; q.y0 = q.cy * 128 + 32 * q.t + 8 * q.by; q.z0 = 0;
+  } else {
+    q.x0 = q.cx * 8192 + 2048 * q.t + 64 * g; q.y0 = 0; q.z0 = 0;
+  }
+  q.edge = (q.cx + 1) * G::CX > a.dims[0] || (q.cy + 1) * G::CY > a.dims[1] ||
+           (q.cz + 1) * G::CZ > a.dims[2];
+  return q;
+}
+
+// Rows of 8 floats of a lane's brick, read from global memory.  Row
+// selectors: 3-D (p, iy) with p = -1 the previous plane, 0/1 the brick's
+// planes; 2-D (0, iy) with iy = -1 the previous row; 1-D (0, 0, xo).
+// Elements outside the field read as 0.
+template <int NDIM, int V>
+struct GlobalRows {
+  const CompressArgs &a;
+  const TileGeo &q;
+  __device__ __forceinline__ void row(int p, int iy, int xo, float (&f)[8]) const {
+    const uint64_t x = q.x0 + xo, y = q.y0 + iy, z = q.z0 + p;
+    const float *ptr = a.x + x + a.dims[0] * (y + a.dims[1] * z);
+    if (!q.edge) {
+      load8<V>(ptr, f);
+    } else {
+      const bool in = y < a.dims[1] && z < a.dims[2];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) f[k] = (in && x + k < a.dims[0]) ? __ldcs(ptr + k) : 0.0f;
+    }
+  }
+};
+
+// The same rows from the warp's TMA box (128-byte swizzled rows of 32
+// floats; the TMA unit has zero-filled everything outside the field).
+// Only the brick's own rows come from the box (p = 0, 1 / iy >= 0).
+template <int NDIM>
+struct BoxRows {
+  const uint8_t *box;
+  int bx, by;
+  __device__ __forceinline__ void row(int p, int iy, int, float (&f)[8]) const {
+    uint32_t base, r, c0;
+    if constexpr (NDIM == 3) {
+      base = 0; r = (uint32_t)(4 * by + iy + 32 * p); c0 = 2 * bx;
+    } else {
+      base = (bx >> 2) * kHalf2D; r = (uint32_t)(8 * by + iy); c0 = 2 * (bx & 3);
+    }
+    const float4 u = *reinterpret_cast<const float4 *>(box + base + swz(r, c0));
+    const float4 w = *reinterpret_cast<const float4 *>(box + base + swz(r, c0 + 1));
+    f[0] = u.x; f[1] = u.y; f[2] = u.z; f[3] = u.w;
+    f[4] = w.x; f[5] = w.y; f[6] = w.z; f[7] = w.w;
+  }
+};
+
+// The neighbours the first Lorenzo difference needs from the previous tile
+// of the chunk (3-D: the previous plane under the brick, 2-D: the row
+// before the brick for by == 0 lanes), read from global memory before the
+// tile's own data is waited for.  A chunk's first tile has none.
+template <int NDIM, int V>
+__device__ __forceinline__ void load_halo(const CompressArgs &a, const TileGeo &q,
+                                          float (&hf)[32]) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) hf[k] = 0.0f;
+  const GlobalRows<NDIM, V> src{a, q};
+  if constexpr (NDIM == 3) {
+    if (q.t > 0) {
+#pragma unroll
+      for (int iy = 0; iy < 4; ++iy) {
+        float h8[8];
+        src.row(-1, iy, 0, h8);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) hf[8 * iy + k] = h8[k];
+      }
+    }
+  } else if constexpr (NDIM == 2) {
+    if (q.t > 0 && q.by == 0) {
+      float h8[8];
+      src.row(0, -1, 0, h8);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) hf[k] = h8[k];
+    }
+  }
+}
+
+// Part 1 of a brick's residuals: read the brick, pre-quantise (Sec. 2.3) and
+// take the first difference against the preloaded neighbours hf (a chunk's
+// first tile has none: q = 0 there).  CHECK folds the unsigned maximum of
+// (bits - kBiasBits) into qmax, checking the value range per element
+// (absolute bounds; with a relative bound the range pass has shown that every
+// element passes).
+template <int NDIM, bool CHECK, class Src>
+__device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q, int g,
+                                                float r, const float (&hf)[32],
+                                                int32_t (&v)[64], uint32_t &qmax) {
+  const unsigned full = 0xffffffffu;
+  if constexpr (NDIM == 3) {
+#pragma unroll
+    for (int iy = 0; iy < 4; ++iy) {                 // D_z, one row at a time
+      float p0[8], p1[8];
+      src.row(0, iy, 0, p0);
+      src.row(1, iy, 0, p1);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int32_t q0 = quant_bits(p0[k], r), q1 = quant_bits(p1[k], r);
+        const int32_t qh = quant_bits(hf[8 * iy + k], r);   // hf = 0 when t == 0: q = 0
+        if (CHECK) qmax = max(qmax, max((uint32_t)q0 - kBiasBits, (uint32_t)q1 - kBiasBits));
+        v[8 * iy + k] = q0 - qh;
+        v[32 + 8 * iy + k] = q1 - q0;
+      }
+    }
+  } else if constexpr (NDIM == 2) {
+#pragma unroll
+    for (int row = 0; row < 8; ++row) {
+      float f8[8];
+      src.row(0, row, 0, f8);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        v[8 * row + k] = quant_bits(f8[k], r);
+        if (CHECK) qmax = max(qmax, (uint32_t)v[8 * row + k] - kBiasBits);
+      }
+    }
+#pragma unroll
+    for (int ix = 0; ix < 8; ++ix) {                 // D_y
+      int32_t up = __shfl_up_sync(full, v[ix + 56], 8);
+      if (q.by == 0) up = quant_bits(hf[ix], r);        // hf = 0 when t == 0: q = 0
+#pragma unroll
+      for (int iy = 7; iy >= 1; --iy) v[ix + 8 * iy] -= v[ix + 8 * (iy - 1)];
+      v[ix] -= up;
+    }
+  } else {
+#pragma unroll
+    for (int row = 0; row < 8; ++row) {
+      float f8[8];
+      src.row(0, 0, 8 * row, f8);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        v[8 * row + k] = quant_bits(f8[k], r);
+        if (CHECK) qmax = max(qmax, (uint32_t)v[8 * row + k] - kBiasBits);
+      }
+    }
+  }
+}
+
+// Part 2: the remaining differences (no more input reads) and code 0 for
+// padding positions.
+template <int NDIM>
+__device__ __forceinline__ void residuals_rest(const CompressArgs &a, const TileGeo &q, int g,
+                                               float r, int32_t (&v)[64]) {
+  using G = Geo<NDIM>;
+  const unsigned full = 0xffffffffu;
+  if constexpr (NDIM == 3) {
+#pragma unroll
+    for (int iz = 0; iz < 2; ++iz) {                 // D_y
+#pragma unroll
+      for (int ix = 0; ix < 8; ++ix) {
+        int32_t up = __shfl_up_sync(full, v[ix + 24 + 32 * iz], 4);
+        if (q.by == 0) up = 0;
+#pragma unroll
+        for (int iy = 3; iy >= 1; --iy) v[ix + 8 * iy + 32 * iz] -= v[ix + 8 * (iy - 1) + 32 * iz];
+        v[ix + 32 * iz] -= up;
+      }
+    }
+  }
+  if constexpr (NDIM >= 2) {
+#pragma unroll
+    for (int row = 0; row < 8; ++row) {              // D_x
+      int32_t left = __shfl_up_sync(full, v[7 + 8 * row], 1);
+      if (q.bx == 0) left = 0;
+#pragma unroll
+      for (int ix = 7; ix >= 1; --ix) v[ix + 8 * row] -= v[ix - 1 + 8 * row];
+      v[8 * row] -= left;
+    }
+  } else {
+    int32_t hq = (int32_t)kMagicBits;
+    if (q.t > 0 && g == 0)
+      hq = quant_bits((q.x0 - 1 < a.dims[0]) ? __ldcs(a.x + q.x0 - 1) : 0.0f, r);
+    int32_t left = __shfl_up_sync(full, v[63], 1);
+    if (g == 0) left = hq;
+#pragma unroll
+    for (int e = 63; e >= 1; --e) v[e] -= v[e - 1];
+    v[0] -= left;
+  }
+  if (q.edge) {
+    const uint64_t X = a.dims[0];
+    const uint64_t lx = q.x0 < X ? X - q.x0 : 0;
+    const uint64_t ly = q.y0 < a.dims[1] ? a.dims[1] - q.y0 : 0;
+    const uint64_t lz = q.z0 < a.dims[2] ? a.dims[2] - q.z0 : 0;
+#pragma unroll
+    for (int e = 0; e < 64; ++e) {
+      const int ix = e % G::BX, iy = (e / G::BX) % G::BY, iz = e / (G::BX * G::BY);
+      if (!((uint64_t)ix < lx && (uint64_t)iy < ly && (uint64_t)iz < lz)) v[e] = 0;
+    }
+  }
+}
+
+// all residuals from global memory (the rare escape repack and the outlier
+// pass, when the TMA box no longer holds the tile)
+template <int NDIM, int V>
+__device__ __forceinline__ void residuals_global(const CompressArgs &a, uint64_t T, int g,
+                                                 float r, int32_t (&v)[64]) {
+  const TileGeo q = tile_geo<NDIM>(a, ChunkGrid(a), T, g);
+  uint32_t unused = 0;
+  float hf[32];
+  load_halo<NDIM, V>(a, q, hf);
+  residuals_first<NDIM, false>(GlobalRows<NDIM, V>{a, q}, q, g, r, hf, v, unused);
+  residuals_rest<NDIM>(a, q, g, r, v);
+}
+
+// residuals -> pairs of 16-bit sign-magnitude codes (Sec. 3.2), even code in
+// the low half.  Returns the OR of |residual| (bit 15 or above set: escapes).
+__device__ __forceinline__ uint32_t pack_codes(const int32_t (&v)[64], uint32_t (&w)[32]) {
+  uint32_t orabs = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int32_t d0 = v[2 * i], d1 = v[2 * i + 1];
+    const uint32_t a0 = (uint32_t)abs(d0), a1 = (uint32_t)abs(d1);
+    orabs |= a0 | a1;
+    const uint32_t mag = byte_perm(a0, a1, 0x5410);             // |d0| | |d1|<<16
+    const uint32_t sgn = byte_perm((uint32_t)d0, (uint32_t)d1, 0x7030);
+    w[i] = mag | (sgn & 0x80008000u);
+  }
+  return orabs;
+}
+
+// escape: a residual whose magnitude needs more than 15 bits gets 0x8000
+__device__ __forceinline__ uint32_t pack_codes_escaped(const int32_t (&v)[64], uint32_t (&w)[32]) {
+  uint32_t n = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int32_t d0 = v[2 * i], d1 = v[2 * i + 1];
+    const uint32_t a0 = (uint32_t)abs(d0), a1 = (uint32_t)abs(d1);
+    uint32_t c0 = a0 | ((uint32_t)(d0 >> 16) & 0x8000u);
+    uint32_t c1 = a1 | ((uint32_t)(d1 >> 16) & 0x8000u);
+    n += (a0 > 32767u) + (a1 > 32767u);
+    c0 = a0 > 32767u ? 0x8000u : c0;
+    c1 = a1 > 32767u ? 0x8000u : c1;
+    w[i] = byte_perm(c0, c1, 0x5410);
+  }
+  return n;
+}
+
+// The rare escape path, kept out of the hot loop: recompute the lane's
+// residuals from global memory, pack them with escapes into pb[32g..32g+31]
+// and return the lane's escape count.
+template <int NDIM, int V>
+__device__ __forceinline__ uint32_t escape_repack(const CompressArgs &a, uint64_t T, int g, float r,
+                                               uint32_t *pb) {
+  int32_t v[64];
+  residuals_global<NDIM, V>(a, T, g, r, v);
+  uint32_t w[32];
+  const uint32_t n = pack_codes_escaped(v, w);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) pb[32 * g + i] = w[i];
+  __syncwarp();
+  return n;
+}
+
+// TMA box of tile T for this warp: 3-D {32,32,2} (the tile's two planes),
+// 2-D two {32,32} x halves of the tile's 32 rows
+template <int NDIM>
+__device__ __forceinline__ void issue_box(const CompressArgs &a, const ChunkGrid &cg,
+                                          const CUtensorMap *tm, uint8_t *box, uint64_t *bar,
+                                          uint64_t T) {
+  const uint32_t c = (uint32_t)(T >> 2);
+  const int t = (int)(T & 3);
+  const uint32_t r = cg.x.div(c);
+  const uint32_t cx = c - r * cg.x.d, cz = cg.y.div(r), cy = r - cz * cg.y.d;
+  mbar_expect_tx(bar, kTileBoxBytes);
+  if constexpr (NDIM == 3) {
+    tma_load_3d(box, tm, bar, (int)(cx * 32), (int)(cy * 32), (int)(cz * 8 + 2 * t));
+  } else {
+    const int y = (int)(cy * 128 + 32 * t);
+    tma_load_2d(box, tm, bar, (int)(cx * 64), y);
+    tma_load_2d(box + kHalf2D, tm, bar, (int)(cx * 64 + 32), y);
+  }
+}
+
+// the compacted blocks of a finished tile, stored two rounds later
+struct Pending {
+  uint64_t T;          // tile index in its field (~0: none)
+  uint32_t field;      // its field (batches)
+  uint64_t agg;        // (blocks << 32) | outliers
+  uint32_t F, P;       // lane b: flag byte and exclusive block rank of plane b
+  uint32_t *pb;        // its plane buffer
+  uint32_t round;      // the block round it belongs to
+};
+
+// Take a finished tile's exclusive prefix from the scan warp and store its
+// compacted blocks (Listing 2's copy: block (b, i) -> payload[PreSum]).
+template <int NDIM>
+__device__ __forceinline__ void finish_tile(const CompressArgs &a, CompShared *sh,
+                                            const Pending &d, const FieldRt &rt, int g,
+                                            int wid) {
+  SetScratch *cur = a.set_cur;
+  const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
+  const uint64_t pay = 64 + 32 * n_tiles;
+  const EbParams &p = rt.p;
+  const float fmin = rt.fmin, fmax = rt.fmax;
+  const int s = (int)(d.round % kRing);
+  uint64_t excl = 0;
+  if (warp_wait(&sh->excl_bar[s], (d.round / kRing) & 1u, a.wait_limit_ns)) {
+    excl = sh->slot[s].excl[wid];
+  } else if (g == 0) {
+    atomicOr(&cur->err, kErrTimeout);
+  }
+  if (g == 0) {
+    a.tile_out_prefix[d.T] = (uint32_t)excl;
+    a.tile_out_count[d.T] = (uint32_t)d.agg;
+    if (d.T == n_tiles - 1) {
+      const uint64_t inc = excl + d.agg;
+      StreamHeader *h = reinterpret_cast<StreamHeader *>(a.out);
+      h->magic[0] = 'F'; h->magic[1] = 'Z'; h->magic[2] = 'G'; h->magic[3] = '1';
+      h->version = 1; h->ndim = (uint8_t)NDIM; h->mode = (uint8_t)a.mode;
+      h->reserved0 = 0;
+      h->dims[0] = (uint32_t)a.dims[0]; h->dims[1] = (uint32_t)a.dims[1];
+      h->dims[2] = (uint32_t)a.dims[2];
+      h->n_tiles = (uint32_t)n_tiles;
+      h->eb_requested = a.eb_req;
+      h->eb = p.eb; h->ebx2 = p.ebx2; h->ebx2_r = p.ebx2_r;
+      h->nnz_blocks = (uint32_t)(inc >> 32);
+      h->n_outliers = (uint32_t)inc;
+      h->range_min = fmin; h->range_max = fmax;
+      h->reserved1 = 0;
+      cur->nnz = inc >> 32;
+      cur->nout = inc & 0xffffffffull;
+    }
+  }
+  const uint32_t tile_nnz = (uint32_t)(d.agg >> 32);
+  uint64_t dst = pay + 16 * ((excl >> 32) + d.P);
+  if (pay + 16 * ((excl >> 32) + tile_nnz) <= a.out_capacity) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if ((d.F >> i) & 1u) {
+        const uint4 blk = *reinterpret_cast<const uint4 *>(d.pb + 32 * g + 4 * (i ^ (g & 7)));
+        __stcs(reinterpret_cast<uint4 *>(a.out + dst), blk);
+        dst += 16;
+      }
+    }
+  } else if (g == 0) {
+    atomicOr(&cur->err, kErrCapacity);
+  }
+  __syncwarp();                                      // plane buffer free again
+}
+
+// The scan warp's ticket for block round r: a unit index from the launch's
+// counter and the unit's field, posted in the ring (lane 0 only).  A single
+// field's launch clears the unit's look-back word in the next call's status
+// array here (a batch's status words are cleared before its launch).
+template <bool BATCH>
+__device__ __forceinline__ void post_ticket(const CompressArgs &a0, const BatchArgs &b,
+                                            CompShared *sh, uint32_t r, uint64_t n_units) {
+  RoundSlot &slot = sh->slot[r % kRing];
+  if constexpr (BATCH) {
+    const uint64_t u = atomicAdd(b.ticket, 1u);
+    const uint2 m = u < n_units ? b.unit_map[u] : make_uint2(0u, 0u);
+    slot.unit = u;
+    slot.field = m.x;
+    slot.local = m.y;
+  } else {
+    const uint64_t u = atomicAdd(&a0.set_cur->ticket, 1u);
+    if (u < n_units) a0.status_next[u * kStatusStride] = 0;
+    slot.unit = u;
+    slot.field = 0;
+    slot.local = (uint32_t)u;
+  }
+  mbar_arrive(&sh->ticket_bar[r % kRing]);
+}
+
+// The scan warp: tickets two rounds ahead, then per round the unit's
+// aggregate, its decoupled look-back (in its field's domain) and the tiles'
+// exclusive prefixes.
+template <bool BATCH>
+__device__ __forceinline__ void scan_warp(const CompressArgs &a0, const BatchArgs &b,
+                                          CompShared *sh, uint64_t n_units, int g) {
+  const unsigned full = 0xffffffffu;
+  const uint64_t skip_unit = !BATCH && a0.skip_publish_chunk < a0.n_chunks
+                                 ? a0.skip_publish_chunk * kTilesPerChunk / kCompWarps
+                                 : ~0ull;
+  if (g == 0) {
+    post_ticket<BATCH>(a0, b, sh, 0, n_units);
+    post_ticket<BATCH>(a0, b, sh, 1, n_units);
+  }
+  for (uint32_t r = 0;; ++r) {
+    const int s = (int)(r % kRing);
+    __syncwarp();                                    // lane 0's ticket write
+    const uint64_t u = sh->slot[s].unit;
+    const uint32_t f = sh->slot[s].field, ul = sh->slot[s].local;
+    if (u >= n_units) break;
+    const CompressArgs &a = BATCH ? b.fields[f] : a0;
+    SetScratch *cur = a.set_cur;
+    if (g == 0) post_ticket<BATCH>(a0, b, sh, r + 2, n_units);
+    if (!warp_wait(&sh->agg_bar[s], (r / kRing) & 1u, a.wait_limit_ns)) {
+      if (g == 0) atomicOr(&cur->err, kErrTimeout);
+      break;
+    }
+    const uint64_t t_agg = g < kCompWarps ? sh->slot[s].agg[g] : 0;
+    uint64_t inc = t_agg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(full, inc, o);
+      if (g >= o) inc += y;
+    }
+    const uint64_t total = __shfl_sync(full, inc, 31);
+    const bool publish = ul != skip_unit;
+    publish_aggregate(a.status_cur, ul, total, publish);
+    // 4 words per lane: a window of 128 units per round trip
+    const uint64_t excl =
+        resolve_prefix<4>(a.status_cur, ul, total, publish, &cur->err, a.wait_limit_ns);
+    if (g < kCompWarps) {
+      sh->slot[s].excl[g] = excl + inc - t_agg;
+      mbar_arrive(&sh->excl_bar[s]);
+    }
+  }
+}
+
+// One block per SM.  A single field's launch (BATCH = false) reads its field
+// from the kernel parameters; a batched launch reads each unit's field from
+// the batch's descriptors.
+template <int NDIM, int V, bool CHECK, bool TMA, bool BATCH>
+__global__ void __launch_bounds__(kCompThreads, 1)
+    compress_kernel(const __grid_constant__ CompressArgs a0,
+                    const __grid_constant__ CUtensorMap tmap0,
+                    const __grid_constant__ BatchArgs b) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const unsigned full = 0xffffffffu;
+  const int g = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // per compute warp: [TMA box 8 KB] (TMA only) [plane buffers 0..2]
+  constexpr int stride = TMA ? kBoxStride : kPlaneBufs * 4096;
+  CompShared *sh = reinterpret_cast<CompShared *>(smem + kCompWarps * stride);
+
+  uint64_t n_units;
+  FieldRt rt0{};
+  if constexpr (BATCH) {
+    n_units = b.n_units;
+  } else {
+    n_units = (a0.n_chunks * kTilesPerChunk + kCompWarps - 1) / kCompWarps;
+    uint32_t err = 0;
+    rt0 = derive_field(a0, err);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (err) atomicOr(&a0.set_cur->err, err);
+      SetScratch *nx = a0.set_next;                  // the next call's block
+      nx->ticket = 0; nx->err = 0; nx->nnz = 0; nx->nout = 0;
+      nx->n_chunks = 0; nx->hdr_nout = 0;
+    }
+    if (!rt0.ok) return;                             // the same in every thread
+  }
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kCompWarps; ++i) mbar_init(&sh->box_bar[i], 1);
+    for (int i = 0; i < kRing; ++i) {
+      mbar_init(&sh->ticket_bar[i], 1);
+      mbar_init(&sh->agg_bar[i], kCompWarps);
+      mbar_init(&sh->excl_bar[i], kCompWarps);
+    }
+  }
+  __syncthreads();
+  if (wid == kCompWarps) {
+    scan_warp<BATCH>(a0, b, sh, n_units, g);
+    return;
+  }
+
+  // ---- compute warp
+  uint8_t *box = smem + wid * stride;
+  uint32_t *const pb0 = reinterpret_cast<uint32_t *>(box + (TMA ? kPlaneOff : 0));
+  uint64_t *bar = &sh->box_bar[wid];
+  const uint64_t limit = a0.wait_limit_ns;
+  // a unit's tile for this warp, and whether this warp computes it (the
+  // unit exists, the tile lies in the field and the field can be quantised)
+  struct Work {
+    uint64_t u, T;
+    uint32_t field;
+    bool run;
+  };
+  auto work_of = [&](int s) {
+    Work w;
+    w.u = sh->slot[s].unit;
+    w.field = sh->slot[s].field;
+    w.T = (uint64_t)sh->slot[s].local * kCompWarps + wid;
+    w.run = false;
+    if (w.u < n_units) {
+      if constexpr (BATCH) {
+        w.run = w.T < b.fields[w.field].n_chunks * kTilesPerChunk && b.rt[w.field].ok;
+      } else {
+        w.run = w.T < a0.n_chunks * kTilesPerChunk;
+      }
+    }
+    return w;
+  };
+  auto rt_of = [&](uint32_t f) -> FieldRt { return BATCH ? b.rt[f] : rt0; };
+  // whether a unit's tile comes by TMA (a batch decides per field: rows
+  // 16-byte aligned; the others read global memory directly)
+  auto tma_of = [&](const Work &w) -> bool {
+    if constexpr (!TMA) return false;
+    else if constexpr (BATCH) return w.run && b.fields[w.field].use_tma != 0;
+    else return w.run;
+  };
+  auto issue = [&](const Work &w) {
+    if constexpr (TMA) {
+      const FieldRt rt = rt_of(w.field);
+      fence_proxy_async_smem();          // earlier generic reads of the box first
+      issue_box<NDIM>(BATCH ? b.fields[w.field] : a0, ChunkGrid(rt.dx, rt.dy),
+                      BATCH ? &b.tmaps[w.field] : &tmap0, box, bar, w.T);
+    }
+  };
+
+  Work cw{n_units, 0, 0, false};
+  if (warp_wait(&sh->ticket_bar[0], 0, limit)) cw = work_of(0);
+  else if (g == 0) atomicOr(&a0.set_cur->err, kErrTimeout);
+  uint32_t phase = 0;
+  if constexpr (TMA) {
+    if (g == 0 && tma_of(cw)) issue(cw);
+    __syncwarp();
+  }
+  Pending prev1{~0ull, 0, 0, 0, 0, pb0, 0};         // last round's tile
+  Pending prev2{~0ull, 0, 0, 0, 0, pb0, 0};         // the round before's
+  uint32_t buf = 0;                                  // plane buffer of this round
+  for (uint32_t r = 0; cw.u < n_units; ++r) {
+    const int s = (int)(r % kRing);
+    const uint64_t T = cw.T;
+    // the next round's unit (the scan warp posts tickets two rounds ahead)
+    Work nw{n_units, 0, 0, false};
+    auto next_unit = [&] {
+      const int s1 = (int)((r + 1) % kRing);
+      if (warp_wait(&sh->ticket_bar[s1], ((r + 1) / kRing) & 1u, limit))
+        nw = work_of(s1);
+      else if (g == 0)
+        atomicOr(&a0.set_cur->err, kErrTimeout);
+    };
+    uint64_t agg = 0;
+    uint32_t F = 0, P = 0;
+    uint32_t *pb = pb0 + 1024 * buf;
+    if (cw.run) {
+      const CompressArgs &a = BATCH ? b.fields[cw.field] : a0;
+      const FieldRt rt = rt_of(cw.field);
+      const ChunkGrid cg(rt.dx, rt.dy);
+      SetScratch *cur = a.set_cur;
+      const TileGeo q = tile_geo<NDIM>(a, cg, T, g);
+      float hf[32];
+      load_halo<NDIM, V>(a, q, hf);
+      int32_t v[64];
+      uint32_t qmax = 0;
+      if (tma_of(cw)) {
+        if (!mbar_wait_bounded(bar, phase, limit) && g == 0) atomicOr(&cur->err, kErrTimeout);
+        phase ^= 1u;
+        residuals_first<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, g, rt.p.ebx2_r, hf, v,
+                                     qmax);
+        __syncwarp();                    // every lane is done with the box
+      } else {
+        residuals_first<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, g, rt.p.ebx2_r, hf, v, qmax);
+      }
+      // the box is free: fetch the next round's tile into it while this one
+      // is finished
+      next_unit();
+      if (g == 0 && tma_of(nw)) issue(nw);
+      residuals_rest<NDIM>(a, q, g, rt.p.ebx2_r, v);
+      if (CHECK && __any_sync(full, qmax > kBiasedMax) && g == 0) atomicOr(&cur->err, kErrRange);
+
+      uint32_t w[32];
+      const uint32_t orabs = pack_codes(v, w);       // v is dead from here on
+      uint32_t nout_lane = 0;
+      if (__any_sync(full, (orabs >> 15) != 0)) {
+        // rare: some |residual| needs more than 15 bits; recompute and repack
+        // with escapes out of line (through the plane buffer)
+        nout_lane = escape_repack<NDIM, V>(a, T, g, rt.p.ebx2_r, pb);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
+        __syncwarp();
+      }
+      transpose32(w);                                // lane g: out[32b + g]
+
+      // plane buffer: lane b collects plane b's 32 words (8 blocks)
+#pragma unroll
+      for (int b2 = 0; b2 < 32; ++b2) pb[32 * b2 + 4 * ((g >> 2) ^ (b2 & 7)) + (g & 3)] = w[b2];
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {                  // lane b: flag byte of plane b
+        const uint4 blk = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
+        F |= ((blk.x | blk.y | blk.z | blk.w) != 0u ? 1u : 0u) << i;
+      }
+      const uint32_t pc = __popc(F);
+      P = pc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(full, P, o);
+        if (g >= o) P += y;
+      }
+      const uint32_t tile_nnz = __shfl_sync(full, P, 31);
+      P -= pc;
+      const uint32_t tile_nout = __reduce_add_sync(full, nout_lane);
+      a.out[64 + T * 32 + g] = (uint8_t)F;           // Listing 1's flags
+      agg = ((uint64_t)tile_nnz << 32) | tile_nout;
+    } else {
+      next_unit();                                   // no tile here this round
+      if (g == 0 && tma_of(nw)) issue(nw);
+    }
+    if (g == 0) {
+      sh->slot[s].agg[wid] = agg;
+      mbar_arrive(&sh->agg_bar[s]);
+    }
+    // the prefix of the tile two rounds back has had two tiles' time to settle
+    if (prev2.T != ~0ull) {
+      const CompressArgs &a = BATCH ? b.fields[prev2.field] : a0;
+      finish_tile<NDIM>(a, sh, prev2, rt_of(prev2.field), g, wid);
+    }
+    prev2 = prev1;
+    prev1 = Pending{cw.run ? T : ~0ull, cw.field, agg, F, P, pb, r};
+    buf = buf == kPlaneBufs - 1 ? 0 : buf + 1;
+    cw = nw;
+  }
+  if (prev2.T != ~0ull)
+    finish_tile<NDIM>(BATCH ? b.fields[prev2.field] : a0, sh, prev2, rt_of(prev2.field), g, wid);
+  if (prev1.T != ~0ull)
+    finish_tile<NDIM>(BATCH ? b.fields[prev1.field] : a0, sh, prev1, rt_of(prev1.field), g, wid);
+}
+
+// ====================================================================
+// outlier pass (only tiles that escaped some residual)
+// ====================================================================
+constexpr int kOutWarps = 4;                    // outlier pass: warps per block, one tile each
+
+template <int NDIM, int V>
+__global__ void __launch_bounds__(kOutWarps * 32)
+    outlier_kernel(const CompressArgs a, uint64_t out_section) {
+  const int g = threadIdx.x & 31;
+  const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
+  const uint64_t T = (uint64_t)blockIdx.x * kOutWarps + (threadIdx.x >> 5);
+  if (T >= n_tiles || a.tile_out_count[T] == 0) return;
+  float fmin = 0.f, fmax = 0.f;
+  bool nonfinite = false;
+  field_range(a, fmin, fmax, nonfinite);
+  const EbParams p = derive_eb(a.mode, a.eb_req, fmin, fmax);
+  int32_t v[64];
+  residuals_global<NDIM, V>(a, T, g, p.ebx2_r, v);
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int e = 0; e < 64; ++e) cnt += (uint32_t)abs(v[e]) > 32767u;
+  uint32_t inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (g >= o) inc += y;
+  }
+  uint64_t pos = (uint64_t)a.tile_out_prefix[T] + inc - cnt;
+#pragma unroll
+  for (int e = 0; e < 64; ++e) {
+    if ((uint32_t)abs(v[e]) > 32767u) {
+      const uint64_t at = out_section + 8 * pos;
+      if (at + 8 <= a.out_capacity) {
+        *reinterpret_cast<uint2 *>(a.out + at) =
+            make_uint2((uint32_t)(T * kTileCodes + 64 * g + e), (uint32_t)v[e]);
+      } else {
+        atomicOr(&a.set_cur->err, kErrCapacity);
+      }
+      ++pos;
+    }
+  }
+}
+
+}  // namespace fz

@@ -5,7 +5,12 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+struct fz_ctx;
+
 namespace fz {
+
+// the CUDA device a context was created on (-1 for NULL)
+int context_device(const fz_ctx *c);
 
 // kernels timed by fz_get_kernel_times: range, compress, outliers,
 // decompress, decompression offsets
@@ -25,6 +30,8 @@ struct CompressArgs {
   const RangeResult *range;    // relative mode: min/max/non-finite of a range pass
   int range_given;             // relative mode: use [range_lo, range_hi] instead
   float range_lo, range_hi;
+  int use_tma;                 // batches: this field's tiles come by TMA
+  int ndim;                    // batches: the field's dimensionality
   SetScratch *set_cur, *set_next;
   uint64_t *status_cur, *status_next;
   uint32_t *tile_out_prefix;   // per tile: exclusive outlier prefix

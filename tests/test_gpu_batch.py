@@ -1,0 +1,168 @@
+"""GPU: many fields through one planned batch (one persistent launch per
+dimensionality, replayed from a CUDA graph).  Every field's stream must be
+byte for byte the stream of the single-field call on the same data (itself
+checked against the oracle here and in test_gpu_parity.py), across graph
+replays, in-place changes of the inputs, graph-off runs, autotuning and
+per-field errors."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2304_12557_gb300 as fz
+from paper_2304_12557_gb300 import fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    return t
+
+
+@pytest.fixture(scope="module")
+def codec(torch):
+    from paper_2304_12557_gb300 import build
+    build.build()
+    c = fz.Codec(0)
+    yield c
+    c.close()
+
+
+def _outliers(shape, n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0, 1, shape).astype(np.float32)
+    flat = x.reshape(-1)
+    idx = rng.choice(flat.size, n, replace=False)
+    flat[idx] = rng.choice([-1, 1], n) * rng.uniform(2e4, 9e4, n)
+    return x
+
+
+def _specs():
+    """(array, ndim, mode, eb): aligned rows (TMA), unaligned rows (direct
+    loads), 1-D, absolute and relative bounds, escapes, degenerate fields,
+    and a run of small uneven fields shaped like the batched workload."""
+    s = [
+        (fields.climate2d(300, 500), 2, "rel", 1e-3),
+        (fields.grf((257, 301), -3.0, 21).astype(np.float32), 2, "rel", 1e-2),
+        (_outliers((40, 64, 96), 60, 22), 3, "abs", 0.5),
+        (fields.grf((33, 70, 41), -3.0, 23).astype(np.float32), 3, "rel", 1e-4),
+        (fields.bumps3d(64), 3, "rel", 1e-3),
+        (fields.grf((30001,), -2.0, 24).astype(np.float32), 1, "rel", 1e-3),
+        (fields.grf((8192,), -2.0, 25).astype(np.float32), 1, "abs", 1e-3),
+        (fields.grf((129, 65), -2.5, 26).astype(np.float32), 2, "abs", 0.01),
+        (np.zeros((16, 32, 32), np.float32), 3, "rel", 1e-3),
+        (np.full((20, 40), 3.5, np.float32), 2, "rel", 1e-3),
+    ]
+    for i, (shape, ndim, beta, eb) in enumerate(fields.batch_shapes(count=60, seed=27)):
+        if np.prod(shape) * 4 > (2 << 20):
+            continue
+        s.append((fields.grf(shape, beta, 100 + i).astype(np.float32), ndim, "rel", eb))
+        if len(s) >= 30:
+            break
+    return s
+
+
+def _single(codec, xt, ndim, mode, eb):
+    return codec.compress(xt, mode=mode, eb=eb, ndim=ndim).cpu().numpy().tobytes()
+
+
+def _make_batch(codec, torch, specs, cap_override=None):
+    xs, outs, spec = [], [], []
+    for i, (x, ndim, mode, eb) in enumerate(specs):
+        xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        dims = list(xt.shape[::-1])[:ndim]
+        cap = fz.compress_bound(dims, ndim)
+        if cap_override and i in cap_override:
+            cap = cap_override[i]
+        out = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+        xs.append(xt)
+        outs.append(out)
+        spec.append((xt, out, mode, eb, ndim))
+    return xs, outs, fz.Batch(codec, spec)
+
+
+def _check(codec, specs, xs, outs, sizes, sts):
+    for i, (x, ndim, mode, eb) in enumerate(specs):
+        assert sts[i] == fz.OK, (i, sts[i])
+        got = outs[i][: sizes[i]].cpu().numpy().tobytes()
+        assert got == _single(codec, xs[i], ndim, mode, eb), i
+
+
+def test_batch_equals_single_field_streams(codec, torch):
+    specs = _specs()
+    assert len(specs) >= 25
+    xs, outs, b = _make_batch(codec, torch, specs)
+    try:
+        sizes, sts = b.compress()
+        _check(codec, specs, xs, outs, sizes, sts)
+        # the oracle on the first field, and the escapes really happened
+        st, o = oracle.compress(specs[0][0], 2, fz.EB_REL, 1e-3)
+        assert outs[0][: sizes[0]].cpu().numpy().tobytes() == o
+        assert fz.inspect(outs[2][:64].cpu().numpy().tobytes())["n_outliers"] >= 60
+        # a replay of the captured graph gives the same streams
+        for o_ in outs:
+            o_.zero_()
+        sizes2, sts2 = b.compress()
+        assert sizes2 == sizes and sts2 == sts
+        _check(codec, specs, xs, outs, sizes2, sts2)
+        # new contents in place: the replay compresses the new data
+        for x in xs:
+            x.mul_(1.7).add_(0.25)
+        sizes3, sts3 = b.compress()
+        _check(codec, specs, xs, outs, sizes3, sts3)
+        # without the graph
+        b.set_graph(False)
+        sizes4, sts4 = b.compress()
+        assert sizes4 == sizes3
+        _check(codec, specs, xs, outs, sizes4, sts4)
+    finally:
+        b.close()
+
+
+def test_batch_autotune_keeps_streams(codec, torch):
+    specs = _specs()[:14]
+    xs, outs, b = _make_batch(codec, torch, specs)
+    try:
+        t = b.autotune(reps=2)
+        assert t["ms_direct"] > 0 and t["ms_tma"] > 0
+        sizes, sts = b.compress()
+        _check(codec, specs, xs, outs, sizes, sts)
+    finally:
+        b.close()
+
+
+def test_batch_per_field_errors(codec, torch):
+    good = fields.bumps3d(64)
+    bad = good.copy()
+    bad[5, 6, 7] = np.nan
+    small = fields.climate2d(300, 500)
+    specs = [(good, 3, "rel", 1e-3), (bad, 3, "rel", 1e-3), (small, 2, "rel", 1e-4),
+             (bad, 3, "abs", 1e-3), (good, 3, "abs", 1e-9)]
+    need = len(_single(codec, torch.from_numpy(small).cuda(), 2, "rel", 1e-4))
+    min_bytes = fz.stream_min_bytes((500, 300), 2)
+    xs, outs, b = _make_batch(codec, torch, specs, cap_override={2: min_bytes + 16})
+    try:
+        sizes, sts = b.compress()
+        assert sts[0] == fz.OK
+        assert sts[1] == fz.ERR_NONFINITE and sizes[1] == 0
+        assert sts[2] == fz.ERR_CAPACITY and sizes[2] == need
+        assert sts[3] == fz.ERR_NONFINITE
+        assert sts[4] == fz.ERR_EB_RANGE
+        assert outs[0][: sizes[0]].cpu().numpy().tobytes() == _single(codec, xs[0], 3, "rel",
+                                                                         1e-3)
+    finally:
+        b.close()
+
+
+def test_batch_rejects_bad_fields(codec, torch):
+    x = torch.zeros((8, 8), device="cuda")
+    out = torch.zeros(16, dtype=torch.uint8, device="cuda")       # below header + flags
+    with pytest.raises(fz.FZError) as e:
+        fz.Batch(codec, [(x, out, "rel", 1e-3)])
+    assert e.value.status == fz.ERR_CAPACITY
+    out = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    with pytest.raises(fz.FZError) as e:
+        fz.Batch(codec, [(x, out, "rel", -1.0)])
+    assert e.value.status == fz.ERR_ARG
