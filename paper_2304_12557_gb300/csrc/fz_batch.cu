@@ -67,11 +67,19 @@ __global__ void __launch_bounds__(256) range_batch_kernel(const RangeSeg *segs, 
     const RangeSeg sg = segs[sgi];
     float lo = INFINITY, hi = -INFINITY;
     uint32_t bad = 0;
-    const bool vec = (reinterpret_cast<uintptr_t>(sg.x) & 15u) == 0;
-    uint64_t done = 0;
-    if (vec) {
-      const uint64_t n4 = sg.n / 4;
-      const float4 *x4 = reinterpret_cast<const float4 *>(sg.x);
+    // elements before the first 16-byte boundary, then 16-byte loads
+    const uint64_t head0 = ((16u - (reinterpret_cast<uintptr_t>(sg.x) & 15u)) & 15u) / 4;
+    const uint64_t head = head0 < sg.n ? head0 : sg.n;
+    if (threadIdx.x < head) {
+      const float a = sg.x[threadIdx.x];
+      bad |= (__float_as_uint(a) & 0x7F800000u) == 0x7F800000u;
+      lo = fminf(lo, a);
+      hi = fmaxf(hi, a);
+    }
+    uint64_t done = head;
+    {
+      const uint64_t n4 = (sg.n - head) / 4;
+      const float4 *x4 = reinterpret_cast<const float4 *>(sg.x + head);
       for (uint64_t i = threadIdx.x; i < n4; i += blockDim.x) {
         const float4 v = __ldcs(&x4[i]);
         const float a[4] = {v.x, v.y, v.z, v.w};
@@ -82,7 +90,7 @@ __global__ void __launch_bounds__(256) range_batch_kernel(const RangeSeg *segs, 
           hi = fmaxf(hi, a[k]);
         }
       }
-      done = n4 * 4;
+      done = head + n4 * 4;
     }
     for (uint64_t i = done + threadIdx.x; i < sg.n; i += blockDim.x) {
       const float a = sg.x[i];
@@ -211,6 +219,7 @@ namespace {
 
 struct Cls {                       // the fields of one dimensionality
   int ndim = 0;
+  bool check = false;              // some field needs the per-element check
   std::vector<uint32_t> fields;    // batch field indices
   uint64_t n_tiles = 0;
   uint64_t n_units = 0;
@@ -274,11 +283,13 @@ struct fz_batch {
 
 namespace {
 
-// a0 carries only the launch-level error block and the wait limit
-template <int NDIM>
+// a0 carries only the launch-level error block and the wait limit.  CHECK:
+// some field of the class needs the per-element quantiser check (absolute
+// bounds, or a relative bound against a supplied range).
+template <int NDIM, bool CHECK>
 cudaError_t launch_batch_compress(const CompressArgs &a0, const BatchArgs &b, int sms,
                                   cudaStream_t s) {
-  auto k = fz::compress_kernel<NDIM, 1, true, NDIM >= 2, true>;
+  auto k = fz::compress_kernel<NDIM, 1, CHECK, NDIM >= 2, true>;
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
   k<<<sms, fz::kCompThreads, fz::kCompSmemTma, s>>>(a0, none, b);
@@ -288,15 +299,19 @@ cudaError_t launch_batch_compress(const CompressArgs &a0, const BatchArgs &b, in
 // the batch kernels' shared-memory limits, set once before any capture
 cudaError_t batch_kernel_attrs() {
   static cudaError_t done = [] {
-    cudaError_t e = cudaFuncSetAttribute(fz::compress_kernel<3, 1, true, true, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         fz::kCompSmemTma);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const int sm = fz::kCompSmemTma;
+    cudaError_t e = cudaFuncSetAttribute(fz::compress_kernel<3, 1, true, true, true>, at, sm);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fz::compress_kernel<2, 1, true, true, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, fz::kCompSmemTma);
+      e = cudaFuncSetAttribute(fz::compress_kernel<2, 1, true, true, true>, at, sm);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fz::compress_kernel<1, 1, true, false, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, fz::kCompSmemTma);
+      e = cudaFuncSetAttribute(fz::compress_kernel<1, 1, true, false, true>, at, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fz::compress_kernel<3, 1, false, true, true>, at, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fz::compress_kernel<2, 1, false, true, true>, at, sm);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fz::compress_kernel<1, 1, false, false, true>, at, sm);
     return e;
   }();
   return done;
@@ -324,9 +339,15 @@ int enqueue_run(fz_batch *B, cudaStream_t s) {
     CompressArgs a0{};
     a0.set_cur = B->d_batch_set;
     a0.wait_limit_ns = B->wait_limit_ns;
-    cudaError_t e = c.ndim == 3   ? launch_batch_compress<3>(a0, b, B->num_sms, s)
-                    : c.ndim == 2 ? launch_batch_compress<2>(a0, b, B->num_sms, s)
-                                  : launch_batch_compress<1>(a0, b, B->num_sms, s);
+    cudaError_t e;
+    if (c.check)
+      e = c.ndim == 3   ? launch_batch_compress<3, true>(a0, b, B->num_sms, s)
+          : c.ndim == 2 ? launch_batch_compress<2, true>(a0, b, B->num_sms, s)
+                        : launch_batch_compress<1, true>(a0, b, B->num_sms, s);
+    else
+      e = c.ndim == 3   ? launch_batch_compress<3, false>(a0, b, B->num_sms, s)
+          : c.ndim == 2 ? launch_batch_compress<2, false>(a0, b, B->num_sms, s)
+                        : launch_batch_compress<1, false>(a0, b, B->num_sms, s);
     if (e != cudaSuccess) return FZ_ERR_CUDA;
   }
   {
@@ -483,6 +504,7 @@ int fz_batch_create(fz_ctx *ctx, const fz_field *fields, int n, fz_batch **out) 
     total_status += units;
     Cls &c = by_ndim[h.ndim];
     c.fields.push_back((uint32_t)f);
+    if (h.mode == FZ_EB_ABS) c.check = true;
     c.n_tiles += tiles;
     c.n_units += units;
     if (h.mode == FZ_EB_REL) {

@@ -33,11 +33,20 @@ __global__ void __launch_bounds__(256) range_kernel(const float *__restrict__ x,
   uint32_t bad = 0;
   const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
-  const bool vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-  uint64_t done = 0;
-  if (vec) {
-    const uint64_t n4 = n / 4;
-    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+  // elements before the first 16-byte boundary (x is 4-byte aligned), then
+  // 16-byte loads, then the tail
+  const uint64_t head0 = ((16u - (reinterpret_cast<uintptr_t>(x) & 15u)) & 15u) / 4;
+  const uint64_t head = head0 < n ? head0 : n;
+  if (tid < head) {
+    const float a = x[tid];
+    bad |= (__float_as_uint(a) & 0x7F800000u) == 0x7F800000u;
+    lo = fminf(lo, a);
+    hi = fmaxf(hi, a);
+  }
+  uint64_t done = head;
+  {
+    const uint64_t n4 = (n - head) / 4;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x + head);
     for (uint64_t i = tid; i < n4; i += nth) {
       float4 v = __ldcs(&x4[i]);
       float a[4] = {v.x, v.y, v.z, v.w};
@@ -48,7 +57,7 @@ __global__ void __launch_bounds__(256) range_kernel(const float *__restrict__ x,
         hi = fmaxf(hi, a[k]);
       }
     }
-    done = n4 * 4;
+    done = head + n4 * 4;
   }
   for (uint64_t i = done + tid; i < n; i += nth) {
     float a = x[i];

@@ -68,7 +68,7 @@ struct CompShared {
 // What the kernel derives once per field: the bound (Sec. 4.1), the range it
 // came from, whether the quantiser takes the field, and the chunk grid's
 // divisors.
-struct FieldRt {
+struct __align__(8) FieldRt {
   EbParams p;
   float fmin, fmax;
   uint32_t ok;
@@ -87,9 +87,21 @@ struct BatchArgs {
   uint32_t *ticket;              // the launch's unit counter, zero at launch
 };
 
-constexpr int kCompSmemTma = kCompWarps * kBoxStride + (int)sizeof(CompShared) + 1024;
-constexpr int kCompSmemLdg = kCompWarps * kPlaneBufs * 4096 + (int)sizeof(CompShared) + 1024;
+// a batch's compute warp keeps its current field's arguments in shared
+// memory (global stores cannot alias them there, so the compiler need not
+// reload them after every store)
+struct __align__(16) WarpField {
+  CompressArgs a;
+  FieldRt rt;
+};
+constexpr int kWarpFieldBytes = (int)((sizeof(WarpField) + 15) / 16 * 16);
+
+constexpr int kCompSmemTma =
+    kCompWarps * kBoxStride + (int)sizeof(CompShared) + kCompWarps * kWarpFieldBytes + 1024;
+constexpr int kCompSmemLdg = kCompWarps * kPlaneBufs * 4096 + (int)sizeof(CompShared) +
+                             kCompWarps * kWarpFieldBytes + 1024;
 static_assert(kCompSmemTma <= 227 * 1024, "shared memory per block");
+static_assert(sizeof(CompressArgs) % 8 == 0 && sizeof(FieldRt) % 8 == 0, "copied as u64 words");
 
 // bounded wait on an mbarrier phase by a whole warp; the result is uniform
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
@@ -520,13 +532,14 @@ __device__ __forceinline__ void finish_tile(const CompressArgs &a, CompShared *s
     }
   }
   const uint32_t tile_nnz = (uint32_t)(d.agg >> 32);
+  uint8_t *const out = a.out;                        // read once: stores follow
   uint64_t dst = pay + 16 * ((excl >> 32) + d.P);
   if (pay + 16 * ((excl >> 32) + tile_nnz) <= a.out_capacity) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       if ((d.F >> i) & 1u) {
         const uint4 blk = *reinterpret_cast<const uint4 *>(d.pb + 32 * g + 4 * (i ^ (g & 7)));
-        __stcs(reinterpret_cast<uint4 *>(a.out + dst), blk);
+        __stcs(reinterpret_cast<uint4 *>(out + dst), blk);
         dst += 16;
       }
     }
@@ -623,6 +636,9 @@ __global__ void __launch_bounds__(kCompThreads, 1)
   // per compute warp: [TMA box 8 KB] (TMA only) [plane buffers 0..2]
   constexpr int stride = TMA ? kBoxStride : kPlaneBufs * 4096;
   CompShared *sh = reinterpret_cast<CompShared *>(smem + kCompWarps * stride);
+  WarpField *wfield = reinterpret_cast<WarpField *>(
+      smem + kCompWarps * stride + ((sizeof(CompShared) + 15) / 16 * 16) +
+      (wid < kCompWarps ? wid : 0) * kWarpFieldBytes);
 
   uint64_t n_units;
   FieldRt rt0{};
@@ -710,6 +726,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
   Pending prev1{~0ull, 0, 0, 0, 0, pb0, 0};         // last round's tile
   Pending prev2{~0ull, 0, 0, 0, 0, pb0, 0};         // the round before's
   uint32_t buf = 0;                                  // plane buffer of this round
+  uint32_t cached = ~0u;                             // the field in wfield (batches)
   for (uint32_t r = 0; cw.u < n_units; ++r) {
     const int s = (int)(r % kRing);
     const uint64_t T = cw.T;
@@ -726,13 +743,30 @@ __global__ void __launch_bounds__(kCompThreads, 1)
     uint32_t F = 0, P = 0;
     uint32_t *pb = pb0 + 1024 * buf;
     if (cw.run) {
-      const CompressArgs &a = BATCH ? b.fields[cw.field] : a0;
-      const FieldRt rt = rt_of(cw.field);
+      if constexpr (BATCH) {
+        if (cw.field != cached) {                    // this warp's field changed
+          constexpr int kWords = (int)(sizeof(WarpField) / 8);
+          const uint64_t *src_a = reinterpret_cast<const uint64_t *>(&b.fields[cw.field]);
+          const uint64_t *src_r = reinterpret_cast<const uint64_t *>(&b.rt[cw.field]);
+          uint64_t *dst = reinterpret_cast<uint64_t *>(wfield);
+          constexpr int kA = (int)(sizeof(CompressArgs) / 8), kR = (int)(sizeof(FieldRt) / 8);
+          for (int i = g; i < kA; i += 32) dst[i] = src_a[i];
+          for (int i = g; i < kR; i += 32)
+            reinterpret_cast<uint64_t *>(&wfield->rt)[i] = src_r[i];
+          (void)kWords;
+          __syncwarp();
+          cached = cw.field;
+        }
+      }
+      const CompressArgs &a = BATCH ? wfield->a : a0;
+      const FieldRt rt = BATCH ? wfield->rt : rt0;
       const ChunkGrid cg(rt.dx, rt.dy);
       SetScratch *cur = a.set_cur;
       const TileGeo q = tile_geo<NDIM>(a, cg, T, g);
       float hf[32];
-      load_halo<NDIM, V>(a, q, hf);
+      // a batch's TMA fields have 16-byte aligned rows: vector halo loads
+      if (BATCH && V < 4 && tma_of(cw)) load_halo<NDIM, 4>(a, q, hf);
+      else load_halo<NDIM, V>(a, q, hf);
       int32_t v[64];
       uint32_t qmax = 0;
       if (tma_of(cw)) {

@@ -121,6 +121,19 @@ def test_batch_equals_single_field_streams(codec, torch):
         b.close()
 
 
+def test_batch_relative_only(codec, torch):
+    """A batch of relative bounds only: its kernels skip the per-element
+    quantiser check (the range pass has bounded every element)."""
+    specs = [s for s in _specs() if s[2] == "rel"]
+    assert len(specs) >= 20
+    xs, outs, b = _make_batch(codec, torch, specs)
+    try:
+        sizes, sts = b.compress()
+        _check(codec, specs, xs, outs, sizes, sts)
+    finally:
+        b.close()
+
+
 def test_batch_autotune_keeps_streams(codec, torch):
     specs = _specs()[:14]
     xs, outs, b = _make_batch(codec, torch, specs)
