@@ -270,6 +270,73 @@ int fz_batch_autotune(fz_batch *batch, int reps, void *stream);
 int fz_batch_tuning(const fz_batch *batch, int *tma_on, double ms[2]);
 
 /* ---------------------------------------------------------------------
+ * A request server with continuous batching.  Clients submit compress and
+ * decompress requests at any time, from any thread; a worker thread admits
+ * them in arrival order while a device-resident pool of pool_bytes has room
+ * for the request's input, output and scratch (a later request may pass
+ * one that does not fit yet), copies their inputs in, and runs them:
+ * every admitted compress request joins the next batched launch (as in
+ * fz_batch_*; the next batch is formed and queued while one runs), and
+ * decompressions run on a second stream beside the batches.  Results stay
+ * in the pool until fetched.  Each result equals what fz_compress /
+ * fz_decompress return for that input alone.  The paper has no counterpart. */
+
+#define FZ_PENDING 1            /* poll/fetch: the request is not done yet */
+#define FZ_OP_COMPRESS 0
+#define FZ_OP_DECOMPRESS 1
+
+typedef struct fz_request {
+  int32_t op;             /* FZ_OP_COMPRESS or FZ_OP_DECOMPRESS               */
+  int32_t ndim;           /* compress: the field (as fz_compress)              */
+  uint64_t dims[3];
+  int32_t mode;
+  int32_t reserved;
+  double eb;
+  const void *h_in;       /* host: the field (compress) or the stream; must
+                             stay valid until the request is done; pinned
+                             memory copies without blocking the worker         */
+  uint64_t in_bytes;      /* 4 * elements, or the stream's size               */
+} fz_request;
+
+typedef struct fz_server_stats {
+  uint64_t completed;     /* requests done (since the last reset)             */
+  uint64_t failed;        /* of which with an error status                     */
+  uint64_t queued;        /* waiting for pool room                             */
+  uint64_t in_flight;     /* admitted, not yet done                            */
+  uint64_t pool_used, pool_bytes;
+  double p50_ms, p99_ms;  /* submit-to-done latency of the completed requests  */
+  double seconds;         /* since the last reset                              */
+} fz_server_stats;
+
+typedef struct fz_server fz_server;
+
+/* Start a server on `device` with a pool of pool_bytes (>= 1 MiB) and at most
+ * max_batch fields per batched launch.  FZ_OK, FZ_ERR_ARG or FZ_ERR_CUDA. */
+int fz_server_create(int device, uint64_t pool_bytes, int max_batch, fz_server **server);
+
+/* Stop the worker (requests not done are dropped) and free everything. */
+void fz_server_destroy(fz_server *server);
+
+/* Queue a request; *id names it.  FZ_ERR_ARG (bad request), FZ_ERR_CORRUPT
+ * (a decompress input whose header or size is inconsistent) or
+ * FZ_ERR_CAPACITY (the request needs more than the whole pool). */
+int fz_server_submit(fz_server *server, const fz_request *request, uint64_t *id);
+
+/* FZ_PENDING while the request runs; FZ_OK when done, with *status its
+ * result (as the single call would return it) and *size its output bytes
+ * (the stream, or 4 * elements). */
+int fz_server_poll(fz_server *server, uint64_t id, int *status, uint64_t *size);
+
+/* Copy a done request's output to h_out (capacity bytes; NULL discards it)
+ * and release the request.  FZ_PENDING while it runs, FZ_ERR_CAPACITY when
+ * h_out is too small (the request stays), FZ_ERR_ARG for an unknown id or a
+ * request that failed (which is released). */
+int fz_server_fetch(fz_server *server, uint64_t id, void *h_out, uint64_t capacity);
+
+/* Counters and latency percentiles; reset != 0 starts a new window. */
+int fz_server_get_stats(fz_server *server, fz_server_stats *stats, int reset);
+
+/* ---------------------------------------------------------------------
  * Compression without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * GPU memory while they run, e.g. an application whose memory pool has

@@ -17,7 +17,7 @@ __all__ = ["Codec", "FZError", "load_library", "library_path", "EB_ABS",
            "EB_REL", "OK", "ERR_ARG", "ERR_CAPACITY", "ERR_NONFINITE",
            "ERR_EB_RANGE", "ERR_CORRUPT", "ERR_TIMEOUT", "ERR_CUDA",
            "compress_bound", "stream_min_bytes", "inspect", "shard_extent",
-           "concat_streams_host", "Batch", "C_API"]
+           "concat_streams_host", "Batch", "Server", "PENDING", "C_API"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libfz_gb300.so")
@@ -30,6 +30,7 @@ ERR_EB_RANGE = -4
 ERR_CORRUPT = -6
 ERR_TIMEOUT = -7
 ERR_CUDA = -8
+PENDING = 1
 EB_ABS = 0
 EB_REL = 1
 
@@ -42,7 +43,9 @@ C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
          "fz_compress_ranged", "fz_shard_extent", "fz_concat_streams",
          "fz_concat_streams_host", "fz_batch_create", "fz_batch_destroy",
          "fz_batch_compress", "fz_batch_set_graph", "fz_batch_autotune",
-         "fz_batch_tuning", "fz_compress_noalloc"]
+         "fz_batch_tuning", "fz_server_create", "fz_server_destroy",
+         "fz_server_submit", "fz_server_poll", "fz_server_fetch",
+         "fz_server_get_stats", "fz_compress_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -71,6 +74,20 @@ class _Field(ctypes.Structure):
     _fields_ = [("d_in", _vp), ("dims", _u64 * 3), ("ndim", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("eb", ctypes.c_double),
                 ("d_out", _vp), ("out_capacity", _u64)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("ndim", ctypes.c_int32),
+                ("dims", _u64 * 3), ("mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("eb", ctypes.c_double),
+                ("h_in", _vp), ("in_bytes", _u64)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("completed", _u64), ("failed", _u64), ("queued", _u64),
+                ("in_flight", _u64), ("pool_used", _u64), ("pool_bytes", _u64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
 
 
 def library_path() -> str:
@@ -139,6 +156,17 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_batch_autotune.argtypes = [_vp, ctypes.c_int, _vp]
         L.fz_batch_tuning.argtypes = [_vp, ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_double)]
+        L.fz_server_create.argtypes = [ctypes.c_int, _u64, ctypes.c_int,
+                                       ctypes.POINTER(_vp)]
+        L.fz_server_destroy.argtypes = [_vp]
+        L.fz_server_destroy.restype = None
+        L.fz_server_submit.argtypes = [_vp, ctypes.POINTER(_Request),
+                                       ctypes.POINTER(_u64)]
+        L.fz_server_poll.argtypes = [_vp, _u64, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(_u64)]
+        L.fz_server_fetch.argtypes = [_vp, _u64, _vp, _u64]
+        L.fz_server_get_stats.argtypes = [_vp, ctypes.POINTER(_ServerStats),
+                                          ctypes.c_int]
         _lib = L
         return L
 
@@ -267,6 +295,125 @@ class Batch:
         if self._h:
             self._L.fz_batch_destroy(self._h)
             self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A request server with continuous batching (see fz_server_create).
+    Inputs are host arrays (numpy, or CPU torch tensors; pinned memory lets
+    the server copy them without blocking); each is kept alive here until
+    its result is fetched."""
+
+    def __init__(self, device: int = 0, pool_bytes: int = 8 << 30,
+                 max_batch: int = 256):
+        self._L = load_library()
+        self._h = _vp()
+        st = self._L.fz_server_create(device, int(pool_bytes), int(max_batch),
+                                      ctypes.byref(self._h))
+        if st != OK:
+            raise FZError(st, "fz_server_create")
+        self._meta = {}
+
+    @staticmethod
+    def _host_ptr(a):
+        if hasattr(a, "data_ptr"):                   # torch CPU tensor
+            assert not a.is_cuda and a.is_contiguous()
+            return a.data_ptr(), a.numel() * a.element_size()
+        return a.ctypes.data, a.nbytes
+
+    def submit_compress(self, x, mode="rel", eb=1e-3, ndim=None):
+        """x: float32 host array indexed [z, y, x].  Returns the request id."""
+        shape = tuple(x.shape)
+        ndim = ndim or len(shape)
+        q = _Request()
+        q.op = 0
+        q.ndim = ndim
+        q.dims = (_u64 * 3)(*([int(d) for d in shape[::-1][:ndim]] + [1] * (3 - ndim)))
+        q.mode = _mode(mode)
+        q.eb = float(eb)
+        q.h_in, q.in_bytes = self._host_ptr(x)
+        rid = _u64(0)
+        st = self._L.fz_server_submit(self._h, ctypes.byref(q), ctypes.byref(rid))
+        if st != OK:
+            raise FZError(st, "fz_server_submit")
+        self._meta[rid.value] = ("c", x, None)
+        return rid.value
+
+    def submit_decompress(self, stream):
+        """stream: uint8 host array holding a whole stream.  Returns the id."""
+        info = inspect(bytes(memoryview(stream)[:64]) if not hasattr(stream, "data_ptr")
+                       else stream[:64].numpy().tobytes())
+        q = _Request()
+        q.op = 1
+        q.h_in, q.in_bytes = self._host_ptr(stream)
+        rid = _u64(0)
+        st = self._L.fz_server_submit(self._h, ctypes.byref(q), ctypes.byref(rid))
+        if st != OK:
+            raise FZError(st, "fz_server_submit")
+        d = info["dims"][: info["ndim"]]
+        self._meta[rid.value] = ("d", stream, tuple(d[::-1]))
+        return rid.value
+
+    def poll(self, rid):
+        """None while the request runs, else (status, size)."""
+        st, size = ctypes.c_int(), _u64()
+        r = self._L.fz_server_poll(self._h, rid, ctypes.byref(st), ctypes.byref(size))
+        if r == PENDING:
+            return None
+        if r != OK:
+            raise FZError(r, "fz_server_poll")
+        return st.value, size.value
+
+    def wait(self, rid, timeout: float = 60.0):
+        import time
+        t0 = time.monotonic()
+        while True:
+            r = self.poll(rid)
+            if r is not None:
+                return r
+            if time.monotonic() - t0 > timeout:
+                raise TimeoutError(f"request {rid} still running")
+            time.sleep(50e-6)
+
+    def fetch(self, rid, out=None):
+        """The result as a numpy array (the stream, or the field shaped
+        [z, y, x]); releases the request.  A failed request raises."""
+        import numpy as np
+        st, size = self.wait(rid)
+        kind, _, shape = self._meta.pop(rid)
+        if st != OK:
+            self._L.fz_server_fetch(self._h, rid, None, 0)
+            raise FZError(st, "request")
+        if out is None:
+            out = np.empty(size, np.uint8) if kind == "c" else np.empty(shape, np.float32)
+        r = self._L.fz_server_fetch(self._h, rid, _vp(out.ctypes.data), out.nbytes)
+        if r != OK:
+            raise FZError(r, "fz_server_fetch")
+        return out
+
+    def discard(self, rid):
+        """Release a done request without copying its output."""
+        self.wait(rid)
+        self._meta.pop(rid, None)
+        self._L.fz_server_fetch(self._h, rid, None, 0)
+
+    def stats(self, reset: bool = False):
+        s = _ServerStats()
+        st = self._L.fz_server_get_stats(self._h, ctypes.byref(s), int(bool(reset)))
+        if st != OK:
+            raise FZError(st, "fz_server_get_stats")
+        return {k: getattr(s, k) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            self._L.fz_server_destroy(self._h)
+            self._h = _vp()
+        self._meta.clear()
 
     def __del__(self):
         try:

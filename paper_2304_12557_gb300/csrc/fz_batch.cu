@@ -26,6 +26,7 @@
 #include "fz.h"
 #include "fz_compress_impl.cuh"
 #include "fz_device.cuh"
+#include "fz_batch_ws.h"
 #include "fz_kernels.h"
 
 namespace fz {
@@ -207,30 +208,15 @@ __global__ void __launch_bounds__(128) outlier_batch_kernel(BatchArgs b, const u
 }  // namespace fz
 
 // ====================================================================
-// host side: the plan
+// host side: the workspace and the planned batch
 // ====================================================================
-using fz::BatchArgs;
-using fz::CompressArgs;
-using fz::FieldRt;
-using fz::RangeResult;
-using fz::SetScratch;
+namespace fz {
 
 namespace {
 
-struct Cls {                       // the fields of one dimensionality
-  int ndim = 0;
-  bool check = false;              // some field needs the per-element check
-  std::vector<uint32_t> fields;    // batch field indices
-  uint64_t n_tiles = 0;
-  uint64_t n_units = 0;
-  uint64_t unit_off = 0;           // into the batch's unit map
-  uint32_t *d_ticket = nullptr;    // into the batch's counters
-};
-
 bool shape_of(const uint64_t dims[3], int ndim, uint64_t *n_chunks, uint32_t *ncx,
               uint32_t *ncy, uint64_t d[3]) {
-  const uint64_t cap = fz_stream_min_bytes(dims, ndim);
-  if (cap == 0) return false;
+  if (fz_stream_min_bytes(dims, ndim) == 0) return false;
   for (int i = 0; i < 3; ++i) d[i] = i < ndim ? dims[i] : 1;
   const uint64_t cx = ndim == 1 ? 8192 : (ndim == 2 ? 64 : 32);
   const uint64_t cy = ndim == 1 ? 1 : (ndim == 2 ? 128 : 32);
@@ -242,46 +228,7 @@ bool shape_of(const uint64_t dims[3], int ndim, uint64_t *n_chunks, uint32_t *nc
   return true;
 }
 
-}  // namespace
-
-struct fz_batch {
-  fz_ctx *ctx = nullptr;
-  int device = 0;
-  int num_sms = 1;
-  uint32_t n = 0;
-  std::vector<fz_field> host;
-  std::vector<CompressArgs> args;
-  std::vector<Cls> cls;
-  // device memory: one allocation carved into the arrays below
-  void *d_mem = nullptr;
-  size_t d_bytes = 0;
-  CompressArgs *d_args = nullptr;
-  FieldRt *d_rt = nullptr;
-  CUtensorMap *d_tmaps = nullptr;
-  uint2 *d_unit_map = nullptr;
-  SetScratch *d_sets = nullptr;        // n fields + the launch-level block
-  SetScratch *d_batch_set = nullptr;
-  RangeResult *d_ranges = nullptr;
-  fz::RangeSlots *d_slots = nullptr;
-  fz::RangeSeg *d_segs = nullptr;
-  uint64_t n_segs = 0;
-  uint64_t *d_status = nullptr;
-  uint32_t *d_tile_out = nullptr;      // outlier prefixes, then counts (batch tile order)
-  uint64_t *d_tile_off = nullptr;      // per field: first batch tile
-  uint64_t total_tiles = 0;
-  uint32_t *d_tickets = nullptr;
-  // what a run clears: [d_sets, end of the zeroed region)
-  void *d_zero = nullptr;
-  size_t zero_bytes = 0;
-  SetScratch *h_res = nullptr;      // pinned, n + 1
-  bool use_graph = true;
-  cudaGraphExec_t graph = nullptr;
-  bool tma_on = true;               // the autotuned load path for TMA-eligible fields
-  double tune_ms[2] = {0, 0};       // [tma off, tma on] when tuned
-  uint64_t wait_limit_ns = 2000000000ull;
-};
-
-namespace {
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // a0 carries only the launch-level error block and the wait limit.  CHECK:
 // some field of the class needs the per-element quantiser check (absolute
@@ -289,138 +236,304 @@ namespace {
 template <int NDIM, bool CHECK>
 cudaError_t launch_batch_compress(const CompressArgs &a0, const BatchArgs &b, int sms,
                                   cudaStream_t s) {
-  auto k = fz::compress_kernel<NDIM, 1, CHECK, NDIM >= 2, true>;
+  auto k = compress_kernel<NDIM, 1, CHECK, NDIM >= 2, true>;
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
-  k<<<sms, fz::kCompThreads, fz::kCompSmemTma, s>>>(a0, none, b);
+  k<<<sms, kCompThreads, kCompSmemTma, s>>>(a0, none, b);
   return cudaGetLastError();
 }
 
-// the batch kernels' shared-memory limits, set once before any capture
+bool tma_eligible(const fz_field &h) {
+  return h.ndim >= 2 && (h.dims[0] % 4) == 0 && (reinterpret_cast<uintptr_t>(h.d_in) & 15u) == 0;
+}
+
+}  // namespace
+
 cudaError_t batch_kernel_attrs() {
   static cudaError_t done = [] {
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    const int sm = fz::kCompSmemTma;
-    cudaError_t e = cudaFuncSetAttribute(fz::compress_kernel<3, 1, true, true, true>, at, sm);
+    const int sm = kCompSmemTma;
+    cudaError_t e = cudaFuncSetAttribute(compress_kernel<3, 1, true, true, true>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(compress_kernel<2, 1, true, true, true>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(compress_kernel<1, 1, true, false, true>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(compress_kernel<3, 1, false, true, true>, at, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(compress_kernel<2, 1, false, true, true>, at, sm);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fz::compress_kernel<2, 1, true, true, true>, at, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fz::compress_kernel<1, 1, true, false, true>, at, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fz::compress_kernel<3, 1, false, true, true>, at, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fz::compress_kernel<2, 1, false, true, true>, at, sm);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fz::compress_kernel<1, 1, false, false, true>, at, sm);
+      e = cudaFuncSetAttribute(compress_kernel<1, 1, false, false, true>, at, sm);
     return e;
   }();
   return done;
 }
 
-// everything one run puts on the stream
-int enqueue_run(fz_batch *B, cudaStream_t s) {
-  if (cudaMemsetAsync(B->d_zero, 0, B->zero_bytes, s) != cudaSuccess) return FZ_ERR_CUDA;
-  if (B->n_segs) {
-    const uint64_t want = B->n_segs;
-    const unsigned blocks = (unsigned)std::min<uint64_t>(want, (uint64_t)B->num_sms * 8);
-    fz::range_batch_kernel<<<blocks, 256, 0, s>>>(B->d_segs, B->n_segs, B->d_slots);
+void BatchWs::release() {
+  if (d_mem_) cudaFree(d_mem_);
+  if (h_stage_) cudaFreeHost(h_stage_);
+  if (h_res_) cudaFreeHost(h_res_);
+  d_mem_ = nullptr;
+  h_stage_ = nullptr;
+  h_res_ = nullptr;
+  d_cap_ = stage_cap_ = 0;
+  res_cap_ = 0;
+  n_ = 0;
+}
+
+int BatchWs::set(int device, const fz_field *fields, int n, cudaStream_t s) {
+  if (!fields || n < 1 || n > FZ_BATCH_MAX_FIELDS) return FZ_ERR_ARG;
+  if (batch_kernel_attrs() != cudaSuccess) return FZ_ERR_CUDA;
+  device_ = device;
+  cudaDeviceGetAttribute(&num_sms_, cudaDevAttrMultiProcessorCount, device);
+  if (num_sms_ < 1) num_sms_ = 1;
+  std::vector<CompressArgs> args(n);
+  std::vector<uint64_t> tile_off(n), status_off(n);
+  std::vector<RangeSeg> segs;
+  WsClass by_ndim[4];
+  for (int d = 1; d <= 3; ++d) by_ndim[d].ndim = d;
+  uint64_t total_tiles = 0, total_status = 0;
+  for (int f = 0; f < n; ++f) {
+    const fz_field &h = fields[f];
+    CompressArgs &a = args[f];
+    a = CompressArgs{};
+    uint64_t nch = 0, d[3];
+    uint32_t ncx = 0, ncy = 0;
+    if (!h.d_in || !h.d_out || (h.mode != FZ_EB_ABS && h.mode != FZ_EB_REL) ||
+        !(h.eb > 0.0) || !std::isfinite(h.eb) || (reinterpret_cast<uintptr_t>(h.d_out) & 15u) ||
+        (reinterpret_cast<uintptr_t>(h.d_in) & 3u) ||
+        !shape_of(h.dims, h.ndim, &nch, &ncx, &ncy, d))
+      return FZ_ERR_ARG;
+    const uint64_t tiles = nch * kTilesPerChunk;
+    if (h.out_capacity < 64 + 32 * tiles) return FZ_ERR_CAPACITY;
+    a.x = h.d_in;
+    a.ndim = h.ndim;
+    for (int i = 0; i < 3; ++i) a.dims[i] = d[i];
+    a.ncx = ncx;
+    a.ncy = ncy;
+    a.n_chunks = nch;
+    a.mode = h.mode;
+    a.eb_req = h.eb;
+    a.out = static_cast<uint8_t *>(h.d_out);
+    a.out_capacity = h.out_capacity;
+    a.wait_limit_ns = wait_limit_ns;
+    a.skip_publish_chunk = ~0ull;
+    tile_off[f] = total_tiles;
+    total_tiles += tiles;
+    const uint64_t units = (tiles + kCompWarps - 1) / kCompWarps;
+    status_off[f] = total_status;
+    total_status += units;
+    WsClass &c = by_ndim[h.ndim];
+    c.fields.push_back((uint32_t)f);
+    if (h.mode == FZ_EB_ABS) c.check = true;
+    c.n_units += units;
+    if (h.mode == FZ_EB_REL) {
+      const uint64_t elems = d[0] * d[1] * d[2];
+      for (uint64_t s0 = 0; s0 < elems; s0 += kRangeSegElems)
+        segs.push_back({h.d_in + s0, std::min<uint64_t>(kRangeSegElems, elems - s0),
+                        (uint32_t)f, 0});
+    }
   }
-  fz::prepare_kernel<<<(B->n + 127) / 128, 128, 0, s>>>(B->d_args, B->d_ranges, B->d_slots,
-                                                        B->d_rt, B->n);
+  std::vector<WsClass> cls;
+  for (int d = 3; d >= 1; --d)
+    if (!by_ndim[d].fields.empty()) cls.push_back(by_ndim[d]);
+  uint64_t total_units = 0;
+  for (WsClass &c : cls) {
+    c.unit_off = total_units;
+    total_units += c.n_units;
+  }
+
+  // layout: uploaded descriptors, then device-written arrays, then the
+  // region every run clears
+  size_t off = 0;
+  auto take = [&](size_t bytes, size_t al) {
+    off = align_up(off, al);
+    const size_t at = off;
+    off += bytes;
+    return at;
+  };
+  const size_t o_args = take(n * sizeof(CompressArgs), 64);
+  const size_t o_tmaps = take(n * sizeof(CUtensorMap), 128);
+  const size_t o_map = take(std::max<uint64_t>(total_units, 1) * sizeof(uint2), 64);
+  const size_t o_segs = take(std::max<size_t>(segs.size(), 1) * sizeof(RangeSeg), 64);
+  const size_t o_toff = take(n * sizeof(uint64_t), 64);
+  const size_t desc = align_up(off, 256);
+  const size_t o_rt = take(n * sizeof(FieldRt), 64);
+  const size_t o_ranges = take(n * sizeof(RangeResult), 64);
+  const size_t o_zero = align_up(off, 256);
+  off = o_zero;
+  const size_t o_sets = take((n + 1) * sizeof(SetScratch), 256);
+  const size_t o_slots = take(n * sizeof(RangeSlots), 64);
+  const size_t o_tick = take(8 * sizeof(uint32_t), 64);
+  const size_t o_status = take(total_status * kStatusStride * sizeof(uint64_t), 128);
+  const size_t o_tout = take(2 * total_tiles * sizeof(uint32_t), 64);
+  const size_t end = align_up(off, 256);
+  if (end > d_cap_) {
+    if (d_mem_) cudaFree(d_mem_);
+    d_mem_ = nullptr;
+    d_cap_ = 0;
+    const size_t want = end + end / 4;
+    if (cudaMalloc(&d_mem_, want) != cudaSuccess) return FZ_ERR_CUDA;
+    d_cap_ = want;
+  }
+  if (desc > stage_cap_) {
+    if (h_stage_) cudaFreeHost(h_stage_);
+    h_stage_ = nullptr;
+    stage_cap_ = 0;
+    const size_t want = desc + desc / 4;
+    if (cudaMallocHost(&h_stage_, want) != cudaSuccess) return FZ_ERR_CUDA;
+    stage_cap_ = want;
+  }
+  if ((uint32_t)n + 1 > res_cap_) {
+    if (h_res_) cudaFreeHost(h_res_);
+    h_res_ = nullptr;
+    res_cap_ = 0;
+    if (cudaMallocHost(&h_res_, (n + 1) * 2 * sizeof(SetScratch)) != cudaSuccess)
+      return FZ_ERR_CUDA;
+    res_cap_ = (uint32_t)(n + 1) * 2;
+  }
+  uint8_t *m = static_cast<uint8_t *>(d_mem_);
+  d_args_ = reinterpret_cast<CompressArgs *>(m + o_args);
+  d_tmaps_ = reinterpret_cast<CUtensorMap *>(m + o_tmaps);
+  d_unit_map_ = reinterpret_cast<uint2 *>(m + o_map);
+  d_segs_ = reinterpret_cast<RangeSeg *>(m + o_segs);
+  d_tile_off_ = reinterpret_cast<uint64_t *>(m + o_toff);
+  d_rt_ = reinterpret_cast<FieldRt *>(m + o_rt);
+  d_ranges_ = reinterpret_cast<RangeResult *>(m + o_ranges);
+  d_sets_ = reinterpret_cast<SetScratch *>(m + o_sets);
+  d_slots_ = reinterpret_cast<RangeSlots *>(m + o_slots);
+  d_tickets_ = reinterpret_cast<uint32_t *>(m + o_tick);
+  d_tile_out_ = reinterpret_cast<uint32_t *>(m + o_tout);
+  desc_bytes_ = desc;
+  zero_off_ = o_zero;
+  zero_bytes_ = end - o_zero;
+  uint64_t *d_status = reinterpret_cast<uint64_t *>(m + o_status);
+  for (int f = 0; f < n; ++f) {
+    CompressArgs &a = args[f];
+    a.range = d_ranges_ + f;
+    a.set_cur = d_sets_ + f;
+    a.status_cur = d_status + status_off[f] * kStatusStride;
+    a.tile_out_prefix = d_tile_out_ + tile_off[f];
+    a.tile_out_count = d_tile_out_ + total_tiles + tile_off[f];
+  }
+  // the descriptor image in pinned memory (units in class order)
+  uint8_t *hs = static_cast<uint8_t *>(h_stage_);
+  uint2 *map = reinterpret_cast<uint2 *>(hs + o_map);
+  for (const WsClass &c : cls) {
+    uint64_t u = c.unit_off;
+    for (uint32_t f : c.fields) {
+      const uint64_t units = (args[f].n_chunks * kTilesPerChunk + kCompWarps - 1) / kCompWarps;
+      for (uint64_t k = 0; k < units; ++k) map[u++] = make_uint2(f, (uint32_t)k);
+    }
+  }
+  if (!segs.empty()) std::memcpy(hs + o_segs, segs.data(), segs.size() * sizeof(RangeSeg));
+  std::memcpy(hs + o_toff, tile_off.data(), n * sizeof(uint64_t));
+  host_.assign(fields, fields + n);
+  args_.swap(args);
+  cls_.swap(cls);
+  n_ = (uint32_t)n;
+  total_tiles_ = total_tiles;
+  total_units_ = total_units;
+  n_segs_ = segs.size();
+  return upload(s);
+}
+
+// tensor maps under the current load-path choice, then the whole
+// descriptor image to the device
+int BatchWs::upload(cudaStream_t s) {
+  uint8_t *hs = static_cast<uint8_t *>(h_stage_);
+  const size_t o_args = reinterpret_cast<uint8_t *>(d_args_) - static_cast<uint8_t *>(d_mem_);
+  const size_t o_tmaps = reinterpret_cast<uint8_t *>(d_tmaps_) - static_cast<uint8_t *>(d_mem_);
+  CUtensorMap *maps = reinterpret_cast<CUtensorMap *>(hs + o_tmaps);
+  for (uint32_t f = 0; f < n_; ++f) {
+    CompressArgs &a = args_[f];
+    std::memset(&maps[f], 0, sizeof(CUtensorMap));
+    a.use_tma = 0;
+    if (tma_on_ && tma_eligible(host_[f]) && encode_field_tmap(a.ndim, a.dims, a.x, &maps[f]))
+      a.use_tma = 1;
+  }
+  std::memcpy(hs + o_args, args_.data(), n_ * sizeof(CompressArgs));
+  if (cudaMemcpyAsync(d_mem_, h_stage_, desc_bytes_, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  return FZ_OK;
+}
+
+int BatchWs::set_tma(bool on, cudaStream_t s) {
+  tma_on_ = on;
+  return n_ ? upload(s) : FZ_OK;
+}
+
+int BatchWs::enqueue(cudaStream_t s) {
+  if (!n_) return FZ_ERR_ARG;
+  uint8_t *m = static_cast<uint8_t *>(d_mem_);
+  if (cudaMemsetAsync(m + zero_off_, 0, zero_bytes_, s) != cudaSuccess) return FZ_ERR_CUDA;
+  if (n_segs_) {
+    const unsigned blocks = (unsigned)std::min<uint64_t>(n_segs_, (uint64_t)num_sms_ * 8);
+    range_batch_kernel<<<blocks, 256, 0, s>>>(d_segs_, n_segs_, d_slots_);
+  }
+  prepare_kernel<<<(n_ + 127) / 128, 128, 0, s>>>(d_args_, d_ranges_, d_slots_, d_rt_, n_);
   if (cudaGetLastError() != cudaSuccess) return FZ_ERR_CUDA;
-  for (const Cls &c : B->cls) {
+  int ci = 0;
+  for (const WsClass &c : cls_) {
     BatchArgs b{};
-    b.fields = B->d_args;
-    b.rt = B->d_rt;
-    b.tmaps = B->d_tmaps;
-    b.unit_map = B->d_unit_map + c.unit_off;
+    b.fields = d_args_;
+    b.rt = d_rt_;
+    b.tmaps = d_tmaps_;
+    b.unit_map = d_unit_map_ + c.unit_off;
     b.n_units = c.n_units;
-    b.ticket = c.d_ticket;
+    b.ticket = d_tickets_ + ci++;
     CompressArgs a0{};
-    a0.set_cur = B->d_batch_set;
-    a0.wait_limit_ns = B->wait_limit_ns;
+    a0.set_cur = d_sets_ + n_;
+    a0.wait_limit_ns = wait_limit_ns;
     cudaError_t e;
     if (c.check)
-      e = c.ndim == 3   ? launch_batch_compress<3, true>(a0, b, B->num_sms, s)
-          : c.ndim == 2 ? launch_batch_compress<2, true>(a0, b, B->num_sms, s)
-                        : launch_batch_compress<1, true>(a0, b, B->num_sms, s);
+      e = c.ndim == 3   ? launch_batch_compress<3, true>(a0, b, num_sms_, s)
+          : c.ndim == 2 ? launch_batch_compress<2, true>(a0, b, num_sms_, s)
+                        : launch_batch_compress<1, true>(a0, b, num_sms_, s);
     else
-      e = c.ndim == 3   ? launch_batch_compress<3, false>(a0, b, B->num_sms, s)
-          : c.ndim == 2 ? launch_batch_compress<2, false>(a0, b, B->num_sms, s)
-                        : launch_batch_compress<1, false>(a0, b, B->num_sms, s);
+      e = c.ndim == 3   ? launch_batch_compress<3, false>(a0, b, num_sms_, s)
+          : c.ndim == 2 ? launch_batch_compress<2, false>(a0, b, num_sms_, s)
+                        : launch_batch_compress<1, false>(a0, b, num_sms_, s);
     if (e != cudaSuccess) return FZ_ERR_CUDA;
   }
   {
     BatchArgs b{};
-    b.fields = B->d_args;
-    b.rt = B->d_rt;
-    const uint64_t warps = (B->total_tiles + 31) / 32;
+    b.fields = d_args_;
+    b.rt = d_rt_;
+    const uint64_t warps = (total_tiles_ + 31) / 32;
     const unsigned blocks =
-        (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 3) / 4, B->num_sms * 8ull));
-    fz::outlier_batch_kernel<<<blocks, 128, 0, s>>>(b, B->d_tile_off, B->n, B->total_tiles,
-                                                     B->d_tile_out + B->total_tiles);
+        (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 3) / 4, num_sms_ * 8ull));
+    outlier_batch_kernel<<<blocks, 128, 0, s>>>(b, d_tile_off_, n_, total_tiles_,
+                                                 d_tile_out_ + total_tiles_);
     if (cudaGetLastError() != cudaSuccess) return FZ_ERR_CUDA;
   }
   // the fields' result blocks and the launch-level one behind them
-  if (cudaMemcpyAsync(B->h_res, B->d_sets, (B->n + 1) * sizeof(SetScratch),
-                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  if (cudaMemcpyAsync(h_res_, d_sets_, (n_ + 1) * sizeof(SetScratch), cudaMemcpyDeviceToHost,
+                      s) != cudaSuccess)
     return FZ_ERR_CUDA;
   return FZ_OK;
 }
 
-void drop_graph(fz_batch *B) {
-  if (B->graph) cudaGraphExecDestroy(B->graph);
-  B->graph = nullptr;
-}
-
-// the fields' tensor maps under the current load-path choice
-int write_args(fz_batch *B) {
-  std::vector<CUtensorMap> maps(B->n);
-  for (uint32_t f = 0; f < B->n; ++f) {
-    CompressArgs &a = B->args[f];
-    std::memset(&maps[f], 0, sizeof(CUtensorMap));
-    const fz_field &h = B->host[f];
-    const bool eligible = h.ndim >= 2 && (h.dims[0] % 4) == 0 &&
-                          (reinterpret_cast<uintptr_t>(h.d_in) & 15u) == 0;
-    a.use_tma = 0;
-    if (eligible && B->tma_on && fz::encode_field_tmap(h.ndim, a.dims, a.x, &maps[f]))
-      a.use_tma = 1;
-  }
-  if (cudaMemcpy(B->d_args, B->args.data(), B->n * sizeof(CompressArgs),
-                 cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(B->d_tmaps, maps.data(), B->n * sizeof(CUtensorMap), cudaMemcpyHostToDevice) !=
-          cudaSuccess)
-    return FZ_ERR_CUDA;
-  return FZ_OK;
-}
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-// per-field statuses and sizes from the result blocks of the last run
-int collect_results(fz_batch *B, uint64_t *out_sizes, int *statuses, cudaStream_t s) {
-  const bool launch_timeout = (B->h_res[B->n].err & fz::kErrTimeout) != 0;
+int BatchWs::collect(fz_ctx *ctx, uint64_t *out_sizes, int *statuses, cudaStream_t s) const {
+  const bool launch_timeout = (h_res_[n_].err & kErrTimeout) != 0;
   int worst = FZ_OK;
-  for (uint32_t f = 0; f < B->n; ++f) {
-    const SetScratch r = B->h_res[f];
-    const fz_field &h = B->host[f];
-    const uint64_t tiles = B->args[f].n_chunks * fz::kTilesPerChunk;
+  for (uint32_t f = 0; f < n_; ++f) {
+    const SetScratch r = h_res_[f];
+    const fz_field &h = host_[f];
+    const uint64_t tiles = args_[f].n_chunks * kTilesPerChunk;
     const uint64_t total = 64 + 32 * tiles + 16 * r.nnz + 8 * r.nout;
     int fs = FZ_OK;
-    if (r.err & fz::kErrNonFinite) {
+    if (r.err & kErrNonFinite) {
       fs = FZ_ERR_NONFINITE;
-    } else if (r.err & (fz::kErrEbParam | fz::kErrRange)) {
+    } else if (r.err & (kErrEbParam | kErrRange)) {
       fs = FZ_ERR_EB_RANGE;
-      if (h.mode == FZ_EB_ABS && !(r.err & fz::kErrEbParam)) {
+      if (h.mode == FZ_EB_ABS && !(r.err & kErrEbParam) && ctx) {
         // an absolute bound checks elements one by one: NaN/Inf fail there too
         float lo, hi;
         int bad = 0;
-        const uint64_t elems = B->args[f].dims[0] * B->args[f].dims[1] * B->args[f].dims[2];
-        if (fz_range(B->ctx, h.d_in, elems, &lo, &hi, &bad, s) == FZ_OK && bad)
+        const uint64_t elems = args_[f].dims[0] * args_[f].dims[1] * args_[f].dims[2];
+        if (fz_range(ctx, h.d_in, elems, &lo, &hi, &bad, s) == FZ_OK && bad)
           fs = FZ_ERR_NONFINITE;
       }
-    } else if ((r.err & fz::kErrTimeout) || launch_timeout) {
+    } else if ((r.err & kErrTimeout) || launch_timeout) {
       fs = FZ_ERR_TIMEOUT;
-    } else if ((r.err & fz::kErrCapacity) || total > h.out_capacity) {
+    } else if ((r.err & kErrCapacity) || total > h.out_capacity) {
       fs = FZ_ERR_CAPACITY;
     }
     statuses[f] = fs;
@@ -429,6 +542,35 @@ int collect_results(fz_batch *B, uint64_t *out_sizes, int *statuses, cudaStream_
   }
   return worst;
 }
+
+}  // namespace fz
+
+struct fz_batch {
+  fz_ctx *ctx = nullptr;
+  int device = 0;
+  fz::BatchWs ws;
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  double tune_ms[2] = {0, 0};       // [direct, TMA] when tuned
+};
+
+namespace {
+
+void drop_graph(fz_batch *B) {
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  B->graph = nullptr;
+}
+
+struct DeviceScope {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceScope(int dev) {
+    ok = cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 }  // namespace
 
@@ -440,169 +582,17 @@ int fz_batch_create(fz_ctx *ctx, const fz_field *fields, int n, fz_batch **out) 
   if (!ctx || !fields || n < 1 || n > FZ_BATCH_MAX_FIELDS) return FZ_ERR_ARG;
   const int device = fz::context_device(ctx);
   if (device < 0) return FZ_ERR_ARG;
-  int prev = -1;
-  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess)
-    return FZ_ERR_CUDA;
-  struct Restore {
-    int d;
-    ~Restore() {
-      if (d >= 0) cudaSetDevice(d);
-    }
-  } restore{prev};
-
-  if (batch_kernel_attrs() != cudaSuccess) return FZ_ERR_CUDA;
+  DeviceScope scope(device);
+  if (!scope.ok) return FZ_ERR_CUDA;
   fz_batch *B = new (std::nothrow) fz_batch();
   if (!B) return FZ_ERR_CUDA;
   B->ctx = ctx;
   B->device = device;
-  cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (B->num_sms < 1) B->num_sms = 1;
-  B->n = (uint32_t)n;
-  B->host.assign(fields, fields + n);
-  B->args.resize(n);
-
-  // per-field arguments, classes, units, range segments
-  uint64_t total_tiles = 0;
-  std::vector<uint64_t> tile_off(n), status_off(n);
-  uint64_t total_status = 0;
-  std::vector<fz::RangeSeg> segs;
-  Cls by_ndim[4];
-  for (int d = 1; d <= 3; ++d) by_ndim[d].ndim = d;
-  for (int f = 0; f < n; ++f) {
-    const fz_field &h = fields[f];
-    CompressArgs &a = B->args[f];
-    uint64_t nch = 0, d[3];
-    uint32_t ncx = 0, ncy = 0;
-    if (!h.d_in || !h.d_out || (h.mode != FZ_EB_ABS && h.mode != FZ_EB_REL) ||
-        !(h.eb > 0.0) || !std::isfinite(h.eb) || (reinterpret_cast<uintptr_t>(h.d_out) & 15u) ||
-        (reinterpret_cast<uintptr_t>(h.d_in) & 3u) ||
-        !shape_of(h.dims, h.ndim, &nch, &ncx, &ncy, d)) {
-      delete B;
-      return FZ_ERR_ARG;
-    }
-    const uint64_t tiles = nch * fz::kTilesPerChunk;
-    if (h.out_capacity < 64 + 32 * tiles) {
-      delete B;
-      return FZ_ERR_CAPACITY;
-    }
-    a.x = h.d_in;
-    a.ndim = h.ndim;
-    for (int i = 0; i < 3; ++i) a.dims[i] = d[i];
-    a.ncx = ncx;
-    a.ncy = ncy;
-    a.n_chunks = nch;
-    a.mode = h.mode;
-    a.eb_req = h.eb;
-    a.out = static_cast<uint8_t *>(h.d_out);
-    a.out_capacity = h.out_capacity;
-    a.wait_limit_ns = B->wait_limit_ns;
-    a.skip_publish_chunk = ~0ull;
-    tile_off[f] = total_tiles;
-    total_tiles += tiles;
-    const uint64_t units = (tiles + fz::kCompWarps - 1) / fz::kCompWarps;
-    status_off[f] = total_status;
-    total_status += units;
-    Cls &c = by_ndim[h.ndim];
-    c.fields.push_back((uint32_t)f);
-    if (h.mode == FZ_EB_ABS) c.check = true;
-    c.n_tiles += tiles;
-    c.n_units += units;
-    if (h.mode == FZ_EB_REL) {
-      const uint64_t elems = d[0] * d[1] * d[2];
-      for (uint64_t s0 = 0; s0 < elems; s0 += fz::kRangeSegElems)
-        segs.push_back({h.d_in + s0, std::min<uint64_t>(fz::kRangeSegElems, elems - s0),
-                        (uint32_t)f, 0});
-    }
-  }
-  for (int d = 3; d >= 1; --d)
-    if (!by_ndim[d].fields.empty()) B->cls.push_back(by_ndim[d]);
-  uint64_t total_units = 0;
-  for (Cls &c : B->cls) {
-    c.unit_off = total_units;
-    total_units += c.n_units;
-  }
-  std::vector<uint2> unit_map(total_units);
-  for (const Cls &c : B->cls) {
-    uint64_t u = c.unit_off;
-    for (uint32_t f : c.fields) {
-      const uint64_t units =
-          (B->args[f].n_chunks * fz::kTilesPerChunk + fz::kCompWarps - 1) / fz::kCompWarps;
-      for (uint64_t k = 0; k < units; ++k) unit_map[u++] = make_uint2(f, (uint32_t)k);
-    }
-  }
-  B->n_segs = segs.size();
-
-  // one device allocation; the zeroed region (results, slots, counters,
-  // status words, outlier counts) is contiguous
-  size_t off = 0;
-  auto take = [&](size_t bytes, size_t al) {
-    off = align_up(off, al);
-    const size_t at = off;
-    off += bytes;
-    return at;
-  };
-  const size_t o_args = take(n * sizeof(CompressArgs), 64);
-  const size_t o_rt = take(n * sizeof(FieldRt), 64);
-  const size_t o_tmaps = take(n * sizeof(CUtensorMap), 128);
-  const size_t o_map = take(std::max<uint64_t>(total_units, 1) * sizeof(uint2), 64);
-  const size_t o_segs = take(std::max<uint64_t>(B->n_segs, 1) * sizeof(fz::RangeSeg), 64);
-  const size_t o_ranges = take(n * sizeof(RangeResult), 64);
-  const size_t o_toff = take(n * sizeof(uint64_t), 64);
-  const size_t o_zero = align_up(off, 256);
-  const size_t o_sets = take((n + 1) * sizeof(SetScratch), 256);
-  const size_t o_slots = take(n * sizeof(fz::RangeSlots), 64);
-  const size_t o_tick = take(8 * sizeof(uint32_t), 64);
-  const size_t o_status = take(total_status * fz::kStatusStride * sizeof(uint64_t), 128);
-  const size_t o_tout = take(2 * total_tiles * sizeof(uint32_t), 64);
-  const size_t end = align_up(off, 256);
-  B->d_bytes = end;
-  if (cudaMalloc(&B->d_mem, end) != cudaSuccess ||
-      cudaMallocHost(&B->h_res, (n + 1) * sizeof(SetScratch)) != cudaSuccess) {
-    fz_batch_destroy(B);
-    return FZ_ERR_CUDA;
-  }
-  uint8_t *m = static_cast<uint8_t *>(B->d_mem);
-  B->d_args = reinterpret_cast<CompressArgs *>(m + o_args);
-  B->d_rt = reinterpret_cast<FieldRt *>(m + o_rt);
-  B->d_tmaps = reinterpret_cast<CUtensorMap *>(m + o_tmaps);
-  B->d_unit_map = reinterpret_cast<uint2 *>(m + o_map);
-  B->d_segs = reinterpret_cast<fz::RangeSeg *>(m + o_segs);
-  B->d_ranges = reinterpret_cast<RangeResult *>(m + o_ranges);
-  B->d_sets = reinterpret_cast<SetScratch *>(m + o_sets);
-  B->d_batch_set = B->d_sets + n;
-  B->d_slots = reinterpret_cast<fz::RangeSlots *>(m + o_slots);
-  B->d_tickets = reinterpret_cast<uint32_t *>(m + o_tick);
-  B->d_status = reinterpret_cast<uint64_t *>(m + o_status);
-  B->d_tile_out = reinterpret_cast<uint32_t *>(m + o_tout);
-  B->d_zero = m + o_zero;
-  B->zero_bytes = end - o_zero;
-  int ci = 0;
-  for (Cls &c : B->cls) c.d_ticket = B->d_tickets + ci++;
-  B->total_tiles = total_tiles;
-  B->d_tile_off = reinterpret_cast<uint64_t *>(m + o_toff);
-  if (cudaMemcpy(B->d_tile_off, tile_off.data(), n * sizeof(uint64_t), cudaMemcpyHostToDevice) !=
-      cudaSuccess) {
-    fz_batch_destroy(B);
-    return FZ_ERR_CUDA;
-  }
-  for (int f = 0; f < n; ++f) {
-    CompressArgs &a = B->args[f];
-    a.range = B->d_ranges + f;
-    a.set_cur = B->d_sets + f;
-    a.set_next = nullptr;
-    a.status_cur = B->d_status + status_off[f] * fz::kStatusStride;
-    a.status_next = nullptr;
-    a.tile_out_prefix = B->d_tile_out + tile_off[f];
-    a.tile_out_count = B->d_tile_out + total_tiles + tile_off[f];
-  }
-  if (write_args(B) != FZ_OK ||
-      (total_units &&
-       cudaMemcpy(B->d_unit_map, unit_map.data(), total_units * sizeof(uint2),
-                  cudaMemcpyHostToDevice) != cudaSuccess) ||
-      (B->n_segs && cudaMemcpy(B->d_segs, segs.data(), B->n_segs * sizeof(fz::RangeSeg),
-                               cudaMemcpyHostToDevice) != cudaSuccess)) {
-    fz_batch_destroy(B);
-    return FZ_ERR_CUDA;
+  int st = B->ws.set(device, fields, n, nullptr);
+  if (st == FZ_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = FZ_ERR_CUDA;
+  if (st != FZ_OK) {
+    delete B;
+    return st;
   }
   *out = B;
   return FZ_OK;
@@ -610,13 +600,9 @@ int fz_batch_create(fz_ctx *ctx, const fz_field *fields, int n, fz_batch **out) 
 
 void fz_batch_destroy(fz_batch *B) {
   if (!B) return;
-  int prev = -1;
-  cudaGetDevice(&prev);
-  cudaSetDevice(B->device);
+  DeviceScope scope(B->device);
   drop_graph(B);
-  cudaFree(B->d_mem);
-  if (B->h_res) cudaFreeHost(B->h_res);
-  if (prev >= 0) cudaSetDevice(prev);
+  B->ws.release();
   delete B;
 }
 
@@ -629,20 +615,12 @@ int fz_batch_set_graph(fz_batch *B, int on) {
 
 int fz_batch_compress(fz_batch *B, uint64_t *out_sizes, int *statuses, void *stream) {
   if (!B || !out_sizes || !statuses) return FZ_ERR_ARG;
-  int prev = -1;
-  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(B->device) != cudaSuccess)
-    return FZ_ERR_CUDA;
-  struct Restore {
-    int d;
-    ~Restore() {
-      if (d >= 0) cudaSetDevice(d);
-    }
-  } restore{prev};
+  DeviceScope scope(B->device);
+  if (!scope.ok) return FZ_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int st = FZ_OK;
   if (B->use_graph) {
     if (!B->graph) {
-      drop_graph(B);
       // capture on a private stream, launch on the caller's
       cudaStream_t cs;
       if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return FZ_ERR_CUDA;
@@ -651,7 +629,7 @@ int fz_batch_compress(fz_batch *B, uint64_t *out_sizes, int *statuses, void *str
         cudaStreamDestroy(cs);
         return FZ_ERR_CUDA;
       }
-      st = enqueue_run(B, cs);
+      st = B->ws.enqueue(cs);
       const cudaError_t ec = cudaStreamEndCapture(cs, &g);
       cudaStreamDestroy(cs);
       if (st != FZ_OK || ec != cudaSuccess ||
@@ -663,24 +641,27 @@ int fz_batch_compress(fz_batch *B, uint64_t *out_sizes, int *statuses, void *str
       cudaGraphDestroy(g);
     }
     if (cudaGraphLaunch(B->graph, s) != cudaSuccess) return FZ_ERR_CUDA;
-  } else {
-    if ((st = enqueue_run(B, s)) != FZ_OK) return st;
+  } else if ((st = B->ws.enqueue(s)) != FZ_OK) {
+    return st;
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return FZ_ERR_CUDA;
-  return collect_results(B, out_sizes, statuses, s);
+  return B->ws.collect(B->ctx, out_sizes, statuses, s);
 }
 
 int fz_batch_autotune(fz_batch *B, int reps, void *stream) {
   if (!B || reps < 1) return FZ_ERR_ARG;
-  std::vector<uint64_t> sizes(B->n);
-  std::vector<int> sts(B->n);
+  DeviceScope scope(B->device);
+  if (!scope.ok) return FZ_ERR_CUDA;
+  const uint32_t n = B->ws.size();
+  std::vector<uint64_t> sizes(n);
+  std::vector<int> sts(n);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double best = 0.0;
-  bool best_tma = B->tma_on;
+  bool best_tma = B->ws.tma_on();
   for (int choice = 0; choice < 2; ++choice) {
-    B->tma_on = choice == 1;
     drop_graph(B);
-    if (write_args(B) != FZ_OK) return FZ_ERR_CUDA;
+    if (B->ws.set_tma(choice == 1, s) != FZ_OK || cudaStreamSynchronize(s) != cudaSuccess)
+      return FZ_ERR_CUDA;
     fz_batch_compress(B, sizes.data(), sts.data(), stream);       // warm-up (and graph)
     std::vector<double> t;
     for (int r = 0; r < reps; ++r) {
@@ -694,18 +675,18 @@ int fz_batch_autotune(fz_batch *B, int reps, void *stream) {
     B->tune_ms[choice] = t[t.size() / 2];
     if (choice == 0 || B->tune_ms[choice] < best) {
       best = B->tune_ms[choice];
-      best_tma = B->tma_on;
+      best_tma = choice == 1;
     }
   }
-  (void)s;
-  B->tma_on = best_tma;
   drop_graph(B);
-  return write_args(B);
+  if (B->ws.set_tma(best_tma, s) != FZ_OK || cudaStreamSynchronize(s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  return FZ_OK;
 }
 
 int fz_batch_tuning(const fz_batch *B, int *tma_on, double ms[2]) {
   if (!B || !tma_on || !ms) return FZ_ERR_ARG;
-  *tma_on = B->tma_on ? 1 : 0;
+  *tma_on = B->ws.tma_on() ? 1 : 0;
   ms[0] = B->tune_ms[0];
   ms[1] = B->tune_ms[1];
   return FZ_OK;
