@@ -484,6 +484,115 @@ def run_batch(args, rank, world, local_rank):
     codec.close()
 
 
+def run_serve(args, rank, world, local_rank):
+    """The served workload: Poisson arrivals swept over rates of 100 to 5000
+    requests/s, half compress and half decompress, fields drawn as in the
+    batched workload plus a 1 GiB 3-D field on 2% of the requests, relative
+    bounds from {1e-2,1e-3,1e-4}; a 40 GB device pool.  Inputs and outputs
+    are pinned host buffers; a client thread submits at the arrival times
+    while another fetches the results in order."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2304_12557_gb300 as fz
+    from paper_2304_12557_gb300 import build, fields
+
+    if rank == 0:
+        build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    gen = torch.Generator(device=dev).manual_seed(5 + 1000 * rank)
+    rng = np.random.default_rng(5 + 1000 * rank)
+    ebs = [1e-2, 1e-3, 1e-4]
+    lib = []                       # (host field, ndim, streams per eb, host outputs)
+    codec = fz.Codec(local_rank)
+    shapes = [(s, nd, beta) for s, nd, beta, _ in fields.batch_shapes(48, 5)]
+    shapes.append(((1024, 512, 512), 3, -3.0))          # the 1 GiB field
+    for shape, nd, beta in shapes:
+        xd = grf_on_device(torch, shape, beta, gen, dev)
+        xh = torch.empty(shape, dtype=torch.float32).pin_memory()
+        xh.copy_(xd)
+        streams = []
+        for eb in ebs:
+            s = codec.compress(xd, mode="rel", eb=eb, ndim=nd)
+            sh = torch.empty(s.numel(), dtype=torch.uint8).pin_memory()
+            sh.copy_(s)
+            streams.append(sh)
+        cap = max(int(sh.numel()) for sh in streams)
+        outs = (np.empty(0), torch.empty(cap + (1 << 20), dtype=torch.uint8).pin_memory(),
+                torch.empty(shape, dtype=torch.float32).pin_memory())
+        lib.append((xh, nd, streams, outs))
+        del xd
+    codec.close()
+    torch.cuda.synchronize()
+    srv = fz.Server(local_rank, pool_bytes=40 << 30, max_batch=256)
+    lams = [100, 200, 500, 1000, 2000, 5000]
+    sweep = []
+    for lam in lams:
+        n = int(min(max(lam * 1.0, 50), 2000))           # about a second of arrivals
+        gaps = rng.exponential(1.0 / lam, n)
+        t_arr = np.cumsum(gaps)
+        kinds = rng.uniform(size=n) < 0.5                  # True: compress
+        big = rng.uniform(size=n) < 0.02
+        which = np.where(big, len(lib) - 1, rng.integers(0, len(lib) - 1, n))
+        eb_i = rng.integers(0, 3, n)
+        ids = [None] * n
+        nbytes = np.array([4 * lib[w][0].numel() for w in which], dtype=np.float64)
+        done_t = [0.0] * n
+        srv.stats(reset=True)
+        t0 = time.perf_counter()
+        ready = threading.Semaphore(0)
+
+        def submit():
+            for i in range(n):
+                dt = t0 + t_arr[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                xh, nd, streams, _ = lib[which[i]]
+                if kinds[i]:
+                    ids[i] = srv.submit_compress(xh, "rel", ebs[eb_i[i]], nd)
+                else:
+                    ids[i] = srv.submit_decompress(streams[eb_i[i]])
+                ready.release()
+
+        th = threading.Thread(target=submit)
+        th.start()
+        for i in range(n):
+            ready.acquire()
+            _, _, _, outs = lib[which[i]]
+            srv.fetch(ids[i], out=(outs[1] if kinds[i] else outs[2]).numpy())
+            done_t[i] = time.perf_counter() - t0
+        th.join()
+        st = srv.stats()
+        span = max(done_t) - 0.0
+        lat = [done_t[i] - t_arr[i] for i in range(n)]
+        sweep.append({"rate_req_s": lam, "requests": n,
+                      "offered_GB_s": float(nbytes.sum() / t_arr[-1] / 1e9),
+                      "served_GB_s": float(nbytes.sum() / span / 1e9),
+                      "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                      "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                      "server_p50_ms": st["p50_ms"], "server_p99_ms": st["p99_ms"],
+                      "failed": st["failed"]})
+    srv.close()
+    best = max(sweep, key=lambda r: r["served_GB_s"])
+    if rank == 0:
+        line = {
+            "metric": "served GB/s of fp32 input and p50/p99 latency (Poisson arrivals, 50/50 "
+                      "compress/decompress)",
+            "value": best["served_GB_s"], "unit": "GB/s", "n_gpus": world, "steps": len(lams),
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Gaussian random fields, pinned host buffers)",
+            "config": {"workload": "serve", "pool_bytes": 40 << 30, "max_batch": 256,
+                       "fields": len(lib), "rel_eb": ebs, "big_field": "1024x512x512 (1 GiB)",
+                       "parallelism": f"{world} independent server(s), one per GPU"},
+            "sweep": sweep, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -492,9 +601,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="cosmo3d_512", choices=["cosmo3d_512", "batch256"],
+    ap.add_argument("--workload", default="cosmo3d_512",
+                    choices=["cosmo3d_512", "batch256", "serve"],
                     help="cosmo3d_512: the single-field round trip (default); batch256: "
-                         "256 uneven fields through one planned batch")
+                         "256 uneven fields through one planned batch; serve: the request "
+                         "server under Poisson arrivals")
     ap.add_argument("--size", type=int, default=512,
                     help="edge of the cubic field (512 = the workload; smaller "
                          "sizes only for profiling captures)")
@@ -513,6 +624,8 @@ def main():
         run_reference(args, rank)
     elif args.workload == "batch256":
         run_batch(args, rank, world, local_rank)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank, dist)
     if dist is not None:
