@@ -483,20 +483,20 @@ __device__ __forceinline__ void issue_box(const CompressArgs &a, const ChunkGrid
 
 // the compacted blocks of a finished tile, stored two rounds later
 struct Pending {
-  uint64_t T;          // tile index in its field (~0: none)
+  uint32_t T;          // tile index in its field (kNoTile: none; < 2^21)
   uint32_t field;      // its field (batches)
   uint64_t agg;        // (blocks << 32) | outliers
   uint32_t F, P;       // lane b: flag byte and exclusive block rank of plane b
-  uint32_t *pb;        // its plane buffer
-  uint32_t round;      // the block round it belongs to
+  uint32_t round;      // the block round it belongs to (its plane buffer: round % 3)
 };
+constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
 // Take a finished tile's exclusive prefix from the scan warp and store its
 // compacted blocks (Listing 2's copy: block (b, i) -> payload[PreSum]).
 template <int NDIM>
 __device__ __forceinline__ void finish_tile(const CompressArgs &a, CompShared *sh,
-                                            const Pending &d, const FieldRt &rt, int g,
-                                            int wid) {
+                                            const Pending &d, const uint32_t *pb,
+                                            const FieldRt &rt, int g, int wid) {
   SetScratch *cur = a.set_cur;
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
   const uint64_t pay = 64 + 32 * n_tiles;
@@ -538,7 +538,7 @@ __device__ __forceinline__ void finish_tile(const CompressArgs &a, CompShared *s
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       if ((d.F >> i) & 1u) {
-        const uint4 blk = *reinterpret_cast<const uint4 *>(d.pb + 32 * g + 4 * (i ^ (g & 7)));
+        const uint4 blk = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
         __stcs(reinterpret_cast<uint4 *>(out + dst), blk);
         dst += 16;
       }
@@ -625,9 +625,8 @@ __device__ __forceinline__ void scan_warp(const CompressArgs &a0, const BatchArg
 // the batch's descriptors.
 template <int NDIM, int V, bool CHECK, bool TMA, bool BATCH>
 __global__ void __launch_bounds__(kCompThreads, 1)
-    compress_kernel(const __grid_constant__ CompressArgs a0,
-                    const __grid_constant__ CUtensorMap tmap0,
-                    const __grid_constant__ BatchArgs b) {
+    compress_kernel(const CompressArgs a0, const __grid_constant__ CUtensorMap tmap0,
+                    const BatchArgs b) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -675,19 +674,18 @@ __global__ void __launch_bounds__(kCompThreads, 1)
   uint8_t *box = smem + wid * stride;
   uint32_t *const pb0 = reinterpret_cast<uint32_t *>(box + (TMA ? kPlaneOff : 0));
   uint64_t *bar = &sh->box_bar[wid];
-  const uint64_t limit = a0.wait_limit_ns;
   // a unit's tile for this warp, and whether this warp computes it (the
   // unit exists, the tile lies in the field and the field can be quantised)
   struct Work {
-    uint64_t u, T;
-    uint32_t field;
+    uint64_t u;
+    uint32_t T, field;             // T < 2^21: tiles of one field
     bool run;
   };
   auto work_of = [&](int s) {
     Work w;
     w.u = sh->slot[s].unit;
-    w.field = sh->slot[s].field;
-    w.T = (uint64_t)sh->slot[s].local * kCompWarps + wid;
+    w.field = BATCH ? sh->slot[s].field : 0u;
+    w.T = sh->slot[s].local * kCompWarps + wid;
     w.run = false;
     if (w.u < n_units) {
       if constexpr (BATCH) {
@@ -715,33 +713,34 @@ __global__ void __launch_bounds__(kCompThreads, 1)
     }
   };
 
-  Work cw{n_units, 0, 0, false};
-  if (warp_wait(&sh->ticket_bar[0], 0, limit)) cw = work_of(0);
+  Work cw{n_units, 0u, 0u, false};
+  if (warp_wait(&sh->ticket_bar[0], 0, a0.wait_limit_ns)) cw = work_of(0);
   else if (g == 0) atomicOr(&a0.set_cur->err, kErrTimeout);
   uint32_t phase = 0;
   if constexpr (TMA) {
     if (g == 0 && tma_of(cw)) issue(cw);
     __syncwarp();
   }
-  Pending prev1{~0ull, 0, 0, 0, 0, pb0, 0};         // last round's tile
-  Pending prev2{~0ull, 0, 0, 0, 0, pb0, 0};         // the round before's
-  uint32_t buf = 0;                                  // plane buffer of this round
+  Pending prev1{kNoTile, 0, 0, 0, 0, 0};            // last round's tile
+  Pending prev2{kNoTile, 0, 0, 0, 0, 0};            // the round before's
+  // a pending tile's plane buffer: rounds cycle through the three
+  auto pb_of = [&](const Pending &d) { return pb0 + 1024 * (d.round % kPlaneBufs); };
   uint32_t cached = ~0u;                             // the field in wfield (batches)
   for (uint32_t r = 0; cw.u < n_units; ++r) {
     const int s = (int)(r % kRing);
     const uint64_t T = cw.T;
     // the next round's unit (the scan warp posts tickets two rounds ahead)
-    Work nw{n_units, 0, 0, false};
+    Work nw{n_units, 0u, 0u, false};
     auto next_unit = [&] {
       const int s1 = (int)((r + 1) % kRing);
-      if (warp_wait(&sh->ticket_bar[s1], ((r + 1) / kRing) & 1u, limit))
+      if (warp_wait(&sh->ticket_bar[s1], ((r + 1) / kRing) & 1u, a0.wait_limit_ns))
         nw = work_of(s1);
       else if (g == 0)
         atomicOr(&a0.set_cur->err, kErrTimeout);
     };
     uint64_t agg = 0;
     uint32_t F = 0, P = 0;
-    uint32_t *pb = pb0 + 1024 * buf;
+    uint32_t *pb = pb0 + 1024 * (r % kPlaneBufs);
     if (cw.run) {
       if constexpr (BATCH) {
         if (cw.field != cached) {                    // this warp's field changed
@@ -769,8 +768,11 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       else load_halo<NDIM, V>(a, q, hf);
       int32_t v[64];
       uint32_t qmax = 0;
-      if (tma_of(cw)) {
-        if (!mbar_wait_bounded(bar, phase, limit) && g == 0) atomicOr(&cur->err, kErrTimeout);
+      // a single field's launch compiles one load path; a batch picks per field
+      const bool use_box = BATCH ? tma_of(cw) : TMA;
+      if (use_box) {
+        if (!mbar_wait_bounded(bar, phase, a0.wait_limit_ns) && g == 0)
+          atomicOr(&cur->err, kErrTimeout);
         phase ^= 1u;
         residuals_first<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, g, rt.p.ebx2_r, hf, v,
                                      qmax);
@@ -828,19 +830,20 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       mbar_arrive(&sh->agg_bar[s]);
     }
     // the prefix of the tile two rounds back has had two tiles' time to settle
-    if (prev2.T != ~0ull) {
+    if (prev2.T != kNoTile) {
       const CompressArgs &a = BATCH ? b.fields[prev2.field] : a0;
-      finish_tile<NDIM>(a, sh, prev2, rt_of(prev2.field), g, wid);
+      finish_tile<NDIM>(a, sh, prev2, pb_of(prev2), rt_of(prev2.field), g, wid);
     }
     prev2 = prev1;
-    prev1 = Pending{cw.run ? T : ~0ull, cw.field, agg, F, P, pb, r};
-    buf = buf == kPlaneBufs - 1 ? 0 : buf + 1;
+    prev1 = Pending{cw.run ? (uint32_t)T : kNoTile, BATCH ? cw.field : 0u, agg, F, P, r};
     cw = nw;
   }
-  if (prev2.T != ~0ull)
-    finish_tile<NDIM>(BATCH ? b.fields[prev2.field] : a0, sh, prev2, rt_of(prev2.field), g, wid);
-  if (prev1.T != ~0ull)
-    finish_tile<NDIM>(BATCH ? b.fields[prev1.field] : a0, sh, prev1, rt_of(prev1.field), g, wid);
+  if (prev2.T != kNoTile)
+    finish_tile<NDIM>(BATCH ? b.fields[prev2.field] : a0, sh, prev2, pb_of(prev2),
+                      rt_of(prev2.field), g, wid);
+  if (prev1.T != kNoTile)
+    finish_tile<NDIM>(BATCH ? b.fields[prev1.field] : a0, sh, prev1, pb_of(prev1),
+                      rt_of(prev1.field), g, wid);
 }
 
 // ====================================================================
