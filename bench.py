@@ -299,6 +299,20 @@ def run_ours(args, rank, world, local_rank, dist):
                             "traffic": traffic_bytes(k, args.size)}
                         for k, v in kern.items()}}
 
+    # the same compression as the paper's separate kernels (codes and
+    # shuffled words through HBM): what fusing them saves on this GPU
+    st_ms = []
+    for _ in range(6):
+        _, ssize, ms = codec.compress_staged_into(x_d, s_d, "rel", 1e-3, 3)
+        st_ms.append(ms)
+    assert ssize == size
+    med = [statistics.median(m[k] for m in st_ms[1:]) for k in range(5)]
+    ablation = {"staged_kernel_ms": {"quantise": med[1], "shuffle_mark": med[2],
+                                     "scan": med[3], "encode": med[4]},
+                "staged_compress_ms": sum(med[1:]),
+                "fused_compress_ms": mean(k_comp),
+                "fusion_speedup": sum(med[1:]) / mean(k_comp)}
+
     # end to end through the host-buffer calls (pinned host memory)
     e2e = None
     if not args.no_e2e:
@@ -334,7 +348,7 @@ def run_ours(args, rank, world, local_rank, dist):
                           "outliers": mean(k_out), "decompress_offsets": mean(k_doff),
                           "decompress": mean(k_dec)},
             "ratio": field_bytes / size, "stream_bytes": size,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "ablation": ablation, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

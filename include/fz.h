@@ -216,6 +216,21 @@ int fz_concat_streams_host(const void *const *h_parts,
                            const uint64_t *part_sizes, int n_parts, void *h_out,
                            uint64_t out_capacity, uint64_t *out_size);
 
+/* The same compression as fz_compress (byte for byte the same stream), run
+ * as the paper's sequence of separate kernels with the intermediate data in
+ * HBM (Sec. 3, Fig. 4 / Table 2's breakdown): pre-quantisation + Lorenzo
+ * writing the 16-bit codes, bitshuffle + mark writing the shuffled words and
+ * flags, the prefix sum, and the encoding copy.  For measuring what fusing
+ * them into one kernel saves.  ms (host, 5 entries, may be NULL) receives
+ * the times of the range pass (0 for absolute bounds) and of the four
+ * kernels, in ms.  Allocates its intermediate buffers (4 KiB per tile
+ * each) in the context on first use.  Same arguments and errors as
+ * fz_compress otherwise. */
+int fz_compress_staged(fz_ctx *ctx, const float *d_in, const uint64_t dims[3],
+                       int ndim, int mode, double eb, void *d_out,
+                       uint64_t out_capacity, uint64_t *out_size, double ms[5],
+                       void *stream);
+
 /* ---------------------------------------------------------------------
  * Many fields in one persistent launch.  A batch is planned once for a fixed
  * list of fields (their device buffers, dims and bounds); every run

@@ -45,7 +45,7 @@ C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
          "fz_batch_compress", "fz_batch_set_graph", "fz_batch_autotune",
          "fz_batch_tuning", "fz_server_create", "fz_server_destroy",
          "fz_server_submit", "fz_server_poll", "fz_server_fetch",
-         "fz_server_get_stats", "fz_compress_noalloc"]
+         "fz_server_get_stats", "fz_compress_staged", "fz_compress_noalloc"]
 
 _lib = None
 _lock = threading.Lock()
@@ -167,6 +167,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_server_fetch.argtypes = [_vp, _u64, _vp, _u64]
         L.fz_server_get_stats.argtypes = [_vp, ctypes.POINTER(_ServerStats),
                                           ctypes.c_int]
+        L.fz_compress_staged.argtypes = [_vp, _vp, dims_t, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, _vp, _u64,
+                                         ctypes.POINTER(_u64),
+                                         ctypes.POINTER(ctypes.c_double), _vp]
         _lib = L
         return L
 
@@ -527,6 +531,24 @@ class Codec:
         if st != OK:
             raise FZError(st, "fz_compress")
         return out[:size]
+
+    def compress_staged_into(self, x, out, mode="rel", eb=1e-3, ndim=None,
+                             stream=None, raise_on_error=True):
+        """The same stream through the unfused kernel sequence (codes and
+        shuffled words in HBM).  Returns (status, size, stage_ms) with
+        stage_ms = [range, quantise, shuffle+mark, scan, encode]."""
+        ndim = ndim or x.dim()
+        dims = list(x.shape[::-1])[:ndim]
+        assert x.is_cuda and x.is_contiguous(), "x must be a contiguous CUDA tensor"
+        size = _u64(0)
+        ms = (ctypes.c_double * 5)()
+        st = self._L.fz_compress_staged(self._ctx, _vp(x.data_ptr()), _dims(dims), ndim,
+                                        _mode(mode), float(eb), _vp(out.data_ptr()),
+                                        out.numel() * out.element_size(),
+                                        ctypes.byref(size), ms, self._stream(stream))
+        if st != OK and raise_on_error:
+            raise FZError(st, "fz_compress_staged")
+        return st, int(size.value), list(ms)
 
     def value_range(self, x, stream=None):
         """(min, max, nonfinite) of a float32 CUDA tensor (the range pass)."""

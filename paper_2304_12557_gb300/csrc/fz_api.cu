@@ -40,6 +40,10 @@ struct fz_ctx {
   uint64_t stage_in_cap = 0;
   void *stage_out = nullptr;
   uint64_t stage_out_cap = 0;
+  // the unfused path's scratch (fz_compress_staged), grown on demand
+  void *staged = nullptr;
+  uint64_t staged_tiles = 0;
+  cudaEvent_t staged_ev[6] = {};
   // profiling: events around each kernel of the last call
   bool profiling = false;
   cudaEvent_t ev[2 * fz::kProfSlots] = {};
@@ -259,6 +263,9 @@ void fz_destroy(fz_ctx *c) {
   if (!c) return;
   DeviceGuard guard(c->device);
   free_scratch(c);
+  cudaFree(c->staged);
+  for (cudaEvent_t e : c->staged_ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(c->range);
   cudaFree(c->partial);
   cudaFree(c->stage_in);
@@ -457,6 +464,125 @@ int fz_range(fz_ctx *c, const float *d_in, uint64_t n, float *h_min, float *h_ma
   *h_min = c->h_range->fmin;
   *h_max = c->h_range->fmax;
   *h_nonfinite = c->h_range->nonfinite ? 1 : 0;
+  return FZ_OK;
+}
+
+// scratch of the unfused path for n_tiles tiles: codes, shuffled words,
+// counts, prefixes and the scan's status words
+static int ensure_staged(fz_ctx *c, uint64_t n_tiles, fz::StagedScratch *w) {
+  const uint64_t units = fz::staged_status_words(n_tiles);
+  auto layout = [&](uint64_t tiles, uint8_t *base, fz::StagedScratch *o) {
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) {
+      const uint64_t at = off;
+      off = (off + bytes + 255) / 256 * 256;
+      return base + at;
+    };
+    o->codes = reinterpret_cast<uint32_t *>(take(tiles * 4096));
+    o->shuf = reinterpret_cast<uint32_t *>(take(tiles * 4096));
+    o->tile_nnz = reinterpret_cast<uint32_t *>(take(tiles * 4));
+    o->tile_excl = reinterpret_cast<uint64_t *>(take(tiles * 8));
+    o->status = reinterpret_cast<uint64_t *>(take(fz::staged_status_words(tiles) *
+                                                  fz::kStatusStride * 8));
+    return off;
+  };
+  if (n_tiles > c->staged_tiles || !c->staged) {
+    cudaFree(c->staged);
+    c->staged = nullptr;
+    c->staged_tiles = 0;
+    fz::StagedScratch tmp;
+    const uint64_t bytes = layout(n_tiles, nullptr, &tmp);
+    if (cudaMalloc(&c->staged, bytes) != cudaSuccess) return FZ_ERR_CUDA;
+    c->staged_tiles = n_tiles;
+    for (cudaEvent_t &e : c->staged_ev)
+      if (!e && cudaEventCreate(&e) != cudaSuccess) return FZ_ERR_CUDA;
+  }
+  layout(c->staged_tiles, static_cast<uint8_t *>(c->staged), w);
+  (void)units;
+  return FZ_OK;
+}
+
+int fz_compress_staged(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, int mode,
+                       double eb, void *d_out, uint64_t cap, uint64_t *out_size, double ms[5],
+                       void *stream) {
+  if (out_size) *out_size = 0;
+  Shape sh;
+  if (!c || !d_in || !d_out || !out_size || !make_shape(dims, ndim, &sh)) return FZ_ERR_ARG;
+  if (mode != FZ_EB_ABS && mode != FZ_EB_REL) return FZ_ERR_ARG;
+  if (!(eb > 0.0) || !std::isfinite(eb)) return FZ_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_out) & 15u) || (reinterpret_cast<uintptr_t>(d_in) & 3u))
+    return FZ_ERR_ARG;
+  const uint64_t min_bytes = 64 + 32 * sh.n_tiles;
+  if (cap < min_bytes) {
+    *out_size = min_bytes;
+    return FZ_ERR_CAPACITY;
+  }
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  fz::StagedScratch w;
+  int st = ensure_cap(c, sh.n_tiles);
+  if (st || (st = ensure_staged(c, sh.n_tiles, &w)) || (st = prepare_set(c, s))) return st;
+  if (cudaMemsetAsync(w.status, 0,
+                      fz::staged_status_words(sh.n_tiles) * fz::kStatusStride * 8, s) !=
+      cudaSuccess)
+    return FZ_ERR_CUDA;
+  cudaEvent_t *ev = ms ? c->staged_ev : nullptr;
+  if (ev) cudaEventRecord(ev[5], s);
+  if (mode == FZ_EB_REL && (st = range_pass(c, d_in, sh.n_elems, s))) return st;
+  const int A = c->cur;
+  fz::CompressArgs a{};
+  a.x = d_in;
+  for (int i = 0; i < 3; ++i) a.dims[i] = sh.d[i];
+  a.ncx = (uint32_t)sh.ncx;
+  a.ncy = (uint32_t)sh.ncy;
+  a.n_chunks = sh.n_chunks;
+  a.mode = mode;
+  a.eb_req = eb;
+  a.range = c->range;
+  a.set_cur = c->sets + A;
+  a.tile_out_prefix = c->out_prefix;
+  a.tile_out_count = c->out_count;
+  a.out = static_cast<uint8_t *>(d_out);
+  a.out_capacity = cap;
+  a.wait_limit_ns = c->wait_limit_ns;
+  a.skip_publish_chunk = ~0ull;
+  if (fz::launch_staged(sh.ndim, a, w, c->num_sms, ev, s) != cudaSuccess) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  c->hdr_dirty[A] = true;                         // this set's block is used; cleared next call
+  if ((st = read_set(c, A, s))) return st;
+  SetScratch r = *c->h_res;
+  if (ms) {
+    float t[5] = {0, 0, 0, 0, 0};
+    cudaEventElapsedTime(&t[0], ev[5], ev[0]);
+    for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&t[k + 1], ev[k], ev[k + 1]);
+    for (int k = 0; k < 5; ++k) ms[k] = t[k];
+  }
+  if (r.err & fz::kErrNonFinite) return FZ_ERR_NONFINITE;
+  if (r.err & (fz::kErrEbParam | fz::kErrRange)) {
+    if (mode == FZ_EB_ABS) return classify_range_error(c, d_in, sh.n_elems, s);
+    return FZ_ERR_EB_RANGE;
+  }
+  if (r.err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
+  const uint64_t total = min_bytes + 16 * r.nnz + 8 * r.nout;
+  if ((r.err & fz::kErrCapacity) || total > cap) {
+    *out_size = total;
+    return FZ_ERR_CAPACITY;
+  }
+  if (r.nout > 0) {
+    if (fz::launch_outliers(sh.ndim, a, min_bytes + 16 * r.nnz, s) != cudaSuccess) {
+      mark_all_dirty(c);
+      return FZ_ERR_CUDA;
+    }
+    if ((st = read_set(c, A, s))) return st;
+    if (c->h_res->err & fz::kErrCapacity) {
+      *out_size = total;
+      return FZ_ERR_CAPACITY;
+    }
+  }
+  *out_size = total;
   return FZ_OK;
 }
 

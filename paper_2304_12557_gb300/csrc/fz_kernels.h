@@ -77,6 +77,19 @@ cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s)
 // look-back status words the offsets pass uses and clears in the other set
 uint64_t decompress_status_words(uint64_t n_chunks);
 
+// the unfused compression path (fz_staged.cu): intermediate data in HBM
+struct StagedScratch {
+  uint32_t *codes;             // per tile: 1024 code words
+  uint32_t *shuf;              // per tile: 1024 shuffled words
+  uint32_t *tile_nnz;          // per tile: non-zero blocks
+  uint64_t *tile_excl;         // per tile: exclusive (blocks << 32 | escapes)
+  uint64_t *status;            // look-back words of the scan (zero at launch)
+};
+// ev (may be NULL): 5 events recorded before, between and after the 4 kernels
+cudaError_t launch_staged(int ndim, const CompressArgs &a, const StagedScratch &w, int sms,
+                          cudaEvent_t *ev, cudaStream_t s);
+uint64_t staged_status_words(uint64_t n_tiles);
+
 // concatenation of slab streams (fz_shard.cu)
 struct ConcatPart {
   uint64_t tiles, nnz, nout;              // the part's own counts
