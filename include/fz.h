@@ -218,7 +218,7 @@ int fz_concat_streams_host(const void *const *h_parts,
 
 /* The same compression as fz_compress (byte for byte the same stream), run
  * as the paper's sequence of separate kernels with the intermediate data in
- * HBM (Sec. 3, Fig. 4 / Table 2's breakdown): pre-quantisation + Lorenzo
+ * HBM (Sec. 3; the per-kernel evaluation of Sec. 4.5): pre-quantisation + Lorenzo
  * writing the 16-bit codes, bitshuffle + mark writing the shuffled words and
  * flags, the prefix sum, and the encoding copy.  For measuring what fusing
  * them into one kernel saves.  ms (host, 5 entries, may be NULL) receives
