@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -607,6 +608,66 @@ def run_serve(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def ssim_2d(torch, a, b, data_range):
+    """Mean SSIM of two 2-D fields (8x8 box windows, the usual constants):
+    an evaluation aid, computed with torch ops."""
+    import torch.nn.functional as F
+    c1, c2 = (0.01 * data_range) ** 2, (0.03 * data_range) ** 2
+    a = a[None, None].double()
+    b = b[None, None].double()
+    k = torch.ones(1, 1, 8, 8, dtype=torch.float64, device=a.device) / 64.0
+    mu_a, mu_b = F.conv2d(a, k), F.conv2d(b, k)
+    s_aa = F.conv2d(a * a, k) - mu_a ** 2
+    s_bb = F.conv2d(b * b, k) - mu_b ** 2
+    s_ab = F.conv2d(a * b, k) - mu_a * mu_b
+    s = ((2 * mu_a * mu_b + c1) * (2 * s_ab + c2)) / ((mu_a ** 2 + mu_b ** 2 + c1) * (s_aa + s_bb + c2))
+    return float(s.mean())
+
+
+def run_quality(args, rank):
+    """Rate-distortion of the synthetic fields (the paper's quality metrics,
+    Sec. 4.2-4.3): compression ratio, bit rate, max |x - x'| / eb, PSNR
+    (value range over RMSE) and SSIM (2-D: the field; 3-D: the mean over z
+    slices) at relative bounds 1e-2, 1e-3, 1e-4."""
+    import torch
+
+    import paper_2304_12557_gb300 as fz
+    from paper_2304_12557_gb300 import build, fields
+
+    if rank != 0:
+        return
+    build.build()
+    dev = torch.device("cuda", 0)
+    codec = fz.Codec(0)
+    cases = [("bumps3d_64", fields.bumps3d(64)), ("climate2d_1800x3600", fields.climate2d()),
+             ("cosmo3d_512", fields.cosmo3d(args.size))]
+    rows = []
+    for name, x_h in cases:
+        x = torch.from_numpy(x_h).to(dev)
+        vr = float(x.max() - x.min())
+        for eb in (1e-2, 5e-3, 1e-3, 5e-4, 1e-4):
+            s = codec.compress(x, mode="rel", eb=eb)
+            y = codec.decompress(s).view(x.shape)
+            info = fz.inspect(s[:64].cpu().numpy().tobytes())
+            d = (x.double() - y.double())
+            rmse = float(d.pow(2).mean().sqrt())
+            if x.dim() == 2:
+                ss = ssim_2d(torch, x, y, vr)
+            else:
+                ss = statistics.mean(ssim_2d(torch, x[z], y[z], vr)
+                                     for z in range(0, x.shape[0], max(1, x.shape[0] // 16)))
+            rows.append({"field": name, "rel_eb": eb, "ratio": 4 * x.numel() / s.numel(),
+                         "bits_per_value": 8 * s.numel() / x.numel(),
+                         "max_err_over_eb": float(d.abs().max()) / info["eb"],
+                         "psnr_db": 20 * math.log10(vr / rmse) if rmse > 0 else float("inf"),
+                         "ssim": ss, "nnz_block_fraction": info["nnz_blocks"] / (256 * info["n_tiles"]),
+                         "outliers": info["n_outliers"]})
+    codec.close()
+    print(json.dumps({"metric": "rate-distortion of the synthetic fields (ratio, PSNR, SSIM)",
+                      "value": None, "unit": None, "config": {"workload": "quality"},
+                      "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -616,10 +677,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="cosmo3d_512",
-                    choices=["cosmo3d_512", "batch256", "serve"],
+                    choices=["cosmo3d_512", "batch256", "serve", "quality"],
                     help="cosmo3d_512: the single-field round trip (default); batch256: "
                          "256 uneven fields through one planned batch; serve: the request "
-                         "server under Poisson arrivals")
+                         "server under Poisson arrivals; quality: rate-distortion report")
     ap.add_argument("--size", type=int, default=512,
                     help="edge of the cubic field (512 = the workload; smaller "
                          "sizes only for profiling captures)")
@@ -640,6 +701,8 @@ def main():
         run_batch(args, rank, world, local_rank)
     elif args.workload == "serve":
         run_serve(args, rank, world, local_rank)
+    elif args.workload == "quality":
+        run_quality(args, rank)
     else:
         run_ours(args, rank, world, local_rank, dist)
     if dist is not None:
