@@ -139,7 +139,7 @@ const char *fz_strerror(int status);
 int fz_set_wait_limit_ns(fz_ctx *ctx, uint64_t ns);
 
 /* Fault injection for tests of the bounded waits: the look-back unit that
- * holds this chunk (the compressor's unit of 11 consecutive tiles, the
+ * holds this chunk (the compressor's unit of 14 consecutive tiles, the
  * decompressor's unit of 512 consecutive chunks) skips publishing its
  * aggregate, so later units' waits run out and the call returns
  * FZ_ERR_TIMEOUT.  UINT64_MAX disables. */

@@ -239,7 +239,7 @@ cudaError_t launch_batch_compress(const CompressArgs &a0, const BatchArgs &b, in
   auto k = compress_kernel<NDIM, 1, CHECK, NDIM >= 2, true>;
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
-  k<<<sms, kCompThreads, kCompSmemTma, s>>>(a0, none, b);
+  k<<<sms, kCompThreads, kCompSmemBatch, s>>>(a0, none, b);
   return cudaGetLastError();
 }
 
@@ -252,7 +252,7 @@ bool tma_eligible(const fz_field &h) {
 cudaError_t batch_kernel_attrs() {
   static cudaError_t done = [] {
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    const int sm = kCompSmemTma;
+    const int sm = kCompSmemBatch;
     cudaError_t e = cudaFuncSetAttribute(compress_kernel<3, 1, true, true, true>, at, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(compress_kernel<2, 1, true, true, true>, at, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(compress_kernel<1, 1, true, false, true>, at, sm);

@@ -30,22 +30,31 @@ namespace fz {
 // Lorenzo, codes, bitshuffle, flags, and posts the tile's aggregate (blocks,
 // outliers) in shared memory.  The scan warp sums the unit, runs the
 // decoupled look-back on the unit index and hands every warp its tile's
-// exclusive prefix, which the warp uses two rounds later to store the
-// compacted blocks.  The look-back therefore walks one status word per
-// unit, and its latency is hidden behind the compute warps' next tiles.
+// exclusive prefix, which the warp uses one round later (a batch: midway
+// through the next round) to store the compacted blocks.  The look-back
+// therefore walks one status word per unit, and its latency is hidden
+// behind the compute warps' next tiles.
 // A compute warp's input comes either from a per-warp TMA box (its tile,
 // loaded one round ahead) or, for fields whose rows are not 16-byte aligned
 // and for 1-D fields, straight from global memory.
 
-constexpr int kCompWarps = 11;                  // compute warps per block
+constexpr int kCompWarps = 14;                  // compute warps per block
 constexpr int kCompThreads = 32 * (kCompWarps + 1);   // + the scan warp
 constexpr int kRing = 4;                        // rounds in flight per block
-// Each warp stores a tile's compacted blocks two rounds after computing it,
-// so that the scan warp has two tiles' time to resolve the tile's prefix:
-// three plane buffers per warp.
-constexpr int kPlaneBufs = 3;
-// per compute warp: [TMA box 8 KB][plane buffers 0..2, 4 KB each]
-constexpr int kBoxStride = 8192 + kPlaneBufs * 4096;
+// A warp stores a tile's compacted blocks defer_rounds() rounds after
+// computing it, so that the scan warp has that long to resolve the tile's
+// prefix.  The tile's bit planes wait in one of plane_bufs() plane buffers.
+// With no deferral the single buffer is drained (the previous tile's blocks
+// stored) right before the next tile's planes are written, so the prefix
+// still has most of a round's time.  A batch keeps each warp's field
+// arguments in shared memory as well and has room for one buffer only.
+template <bool BATCH>
+__host__ __device__ constexpr int defer_rounds() { return BATCH ? 0 : 1; }
+template <bool BATCH>
+__host__ __device__ constexpr int plane_bufs() { return defer_rounds<BATCH>() == 0 ? 1 : defer_rounds<BATCH>() + 1; }
+// per compute warp: [TMA box 8 KB][plane buffers, 4 KB each]
+template <bool BATCH>
+__host__ __device__ constexpr int box_stride() { return 8192 + plane_bufs<BATCH>() * 4096; }
 constexpr int kPlaneOff = 8192;
 constexpr int kHalf2D = 4096;                   // second x half of a 2-D box
 constexpr uint32_t kTileBoxBytes = 32 * 32 * 2 * 4;  // one tile (3-D: 2 planes; 2-D: 2 halves)
@@ -96,11 +105,13 @@ struct __align__(16) WarpField {
 };
 constexpr int kWarpFieldBytes = (int)((sizeof(WarpField) + 15) / 16 * 16);
 
-constexpr int kCompSmemTma =
-    kCompWarps * kBoxStride + (int)sizeof(CompShared) + kCompWarps * kWarpFieldBytes + 1024;
-constexpr int kCompSmemLdg = kCompWarps * kPlaneBufs * 4096 + (int)sizeof(CompShared) +
-                             kCompWarps * kWarpFieldBytes + 1024;
-static_assert(kCompSmemTma <= 227 * 1024, "shared memory per block");
+constexpr int kCompShBytes = (int)((sizeof(CompShared) + 15) / 16 * 16);
+constexpr int kCompSmemTma = kCompWarps * box_stride<false>() + kCompShBytes + 1024;
+constexpr int kCompSmemLdg = kCompWarps * plane_bufs<false>() * 4096 + kCompShBytes + 1024;
+constexpr int kCompSmemBatch =
+    kCompWarps * box_stride<true>() + kCompShBytes + kCompWarps * kWarpFieldBytes + 1024;
+static_assert(kCompSmemTma <= 227 * 1024 && kCompSmemBatch <= 227 * 1024,
+              "shared memory per block");
 static_assert(sizeof(CompressArgs) % 8 == 0 && sizeof(FieldRt) % 8 == 0, "copied as u64 words");
 
 // bounded wait on an mbarrier phase by a whole warp; the result is uniform
@@ -481,7 +492,7 @@ __device__ __forceinline__ void issue_box(const CompressArgs &a, const ChunkGrid
   }
 }
 
-// the compacted blocks of a finished tile, stored two rounds later
+// the compacted blocks of a finished tile, stored in a later round
 struct Pending {
   uint32_t T;          // tile index in its field (kNoTile: none; < 2^21)
   uint32_t field;      // its field (batches)
@@ -632,12 +643,13 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const unsigned full = 0xffffffffu;
   const int g = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // per compute warp: [TMA box 8 KB] (TMA only) [plane buffers 0..2]
-  constexpr int stride = TMA ? kBoxStride : kPlaneBufs * 4096;
+  constexpr int kDef = defer_rounds<BATCH>(), kBufs = plane_bufs<BATCH>();
+  // per compute warp: [TMA box 8 KB] (TMA only) [plane buffers]; then the
+  // block's CompShared; then (batches) one WarpField per compute warp
+  constexpr int stride = TMA ? box_stride<BATCH>() : kBufs * 4096;
   CompShared *sh = reinterpret_cast<CompShared *>(smem + kCompWarps * stride);
   WarpField *wfield = reinterpret_cast<WarpField *>(
-      smem + kCompWarps * stride + ((sizeof(CompShared) + 15) / 16 * 16) +
-      (wid < kCompWarps ? wid : 0) * kWarpFieldBytes);
+      smem + kCompWarps * stride + kCompShBytes + (wid < kCompWarps ? wid : 0) * kWarpFieldBytes);
 
   uint64_t n_units;
   FieldRt rt0{};
@@ -724,7 +736,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
   Pending prev1{kNoTile, 0, 0, 0, 0, 0};            // last round's tile
   Pending prev2{kNoTile, 0, 0, 0, 0, 0};            // the round before's
   // a pending tile's plane buffer: rounds cycle through the three
-  auto pb_of = [&](const Pending &d) { return pb0 + 1024 * (d.round % kPlaneBufs); };
+  auto pb_of = [&](const Pending &d) { return pb0 + 1024 * (d.round % kBufs); };
   uint32_t cached = ~0u;                             // the field in wfield (batches)
   for (uint32_t r = 0; cw.u < n_units; ++r) {
     const int s = (int)(r % kRing);
@@ -740,7 +752,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
     };
     uint64_t agg = 0;
     uint32_t F = 0, P = 0;
-    uint32_t *pb = pb0 + 1024 * (r % kPlaneBufs);
+    uint32_t *pb = pb0 + 1024 * (r % kBufs);
     if (cw.run) {
       if constexpr (BATCH) {
         if (cw.field != cached) {                    // this warp's field changed
@@ -789,8 +801,11 @@ __global__ void __launch_bounds__(kCompThreads, 1)
 
       uint32_t w[32];
       const uint32_t orabs = pack_codes(v, w);       // v is dead from here on
+      // every code of the tile fits in 7 bits and the sign: the planes of
+      // magnitude bits 7..14 are zero and half the transpose is skipped
+      const bool narrow = !__any_sync(full, orabs > 127u);
       uint32_t nout_lane = 0;
-      if (__any_sync(full, (orabs >> 15) != 0)) {
+      if (!narrow && __any_sync(full, (orabs >> 15) != 0)) {
         // rare: some |residual| needs more than 15 bits; recompute and repack
         // with escapes out of line (through the plane buffer)
         nout_lane = escape_repack<NDIM, V>(a, T, g, rt.p.ebx2_r, pb);
@@ -798,17 +813,38 @@ __global__ void __launch_bounds__(kCompThreads, 1)
         for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
         __syncwarp();
       }
-      transpose32(w);                                // lane g: out[32b + g]
+      if constexpr (kDef == 0) {                     // drain the single plane buffer
+        if (prev1.T != kNoTile) {
+          const CompressArgs &a1 = BATCH ? b.fields[prev1.field] : a0;
+          finish_tile<NDIM>(a1, sh, prev1, pb_of(prev1), rt_of(prev1.field), g, wid);
+          prev1.T = kNoTile;
+        }
+      }
 
-      // plane buffer: lane b collects plane b's 32 words (8 blocks)
+      // plane buffer: lane b collects plane b's 32 words (8 blocks); a
+      // narrow tile writes its 16 nonzero planes only
+      if (narrow) {
+        uint32_t u[16];
+        squeeze_narrow(w, u);
+        transpose16(u);
 #pragma unroll
-      for (int b2 = 0; b2 < 32; ++b2) pb[32 * b2 + 4 * ((g >> 2) ^ (b2 & 7)) + (g & 3)] = w[b2];
+        for (int k = 0; k < 16; ++k) {
+          const int b2 = narrow_row(k);
+          pb[32 * b2 + 4 * ((g >> 2) ^ (b2 & 7)) + (g & 3)] = u[k];
+        }
+      } else {
+        transpose32(w);                              // lane g: out[32b + g]
+#pragma unroll
+        for (int b2 = 0; b2 < 32; ++b2) pb[32 * b2 + 4 * ((g >> 2) ^ (b2 & 7)) + (g & 3)] = w[b2];
+      }
       __syncwarp();
 #pragma unroll
       for (int i = 0; i < 8; ++i) {                  // lane b: flag byte of plane b
         const uint4 blk = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
         F |= ((blk.x | blk.y | blk.z | blk.w) != 0u ? 1u : 0u) << i;
       }
+      if (narrow && (g & 15) >= 7 && (g & 15) != 15) F = 0;   // rows not written
+
       const uint32_t pc = __popc(F);
       P = pc;
 #pragma unroll
@@ -829,12 +865,14 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       sh->slot[s].agg[wid] = agg;
       mbar_arrive(&sh->agg_bar[s]);
     }
-    // the prefix of the tile two rounds back has had two tiles' time to settle
-    if (prev2.T != kNoTile) {
-      const CompressArgs &a = BATCH ? b.fields[prev2.field] : a0;
-      finish_tile<NDIM>(a, sh, prev2, pb_of(prev2), rt_of(prev2.field), g, wid);
+    // the oldest pending tile's prefix has had kDef tiles' time to settle
+    // (kDef = 0: prev1 is still pending only if this round ran no tile)
+    Pending &old = kDef == 2 ? prev2 : prev1;
+    if (old.T != kNoTile) {
+      const CompressArgs &a = BATCH ? b.fields[old.field] : a0;
+      finish_tile<NDIM>(a, sh, old, pb_of(old), rt_of(old.field), g, wid);
     }
-    prev2 = prev1;
+    if constexpr (kDef == 2) prev2 = prev1;
     prev1 = Pending{cw.run ? (uint32_t)T : kNoTile, BATCH ? cw.field : 0u, agg, F, P, r};
     cw = nw;
   }

@@ -425,6 +425,63 @@ __host__ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
   }
 }
 
+// The same transpose for a brick whose 64 codes all have magnitude < 128
+// (7 magnitude bits and the sign: 16 of the 32 bit-plane rows are nonzero).
+// squeeze_narrow turns the 32 code-pair words w[i] = c(2i) | c(2i+1) << 16
+// into 16 words of byte codes (magnitude in bits 0..6, sign in bit 7)
+//   u[j] = c(2j) | c(2j+1) << 8 | c(32+2j) << 16 | c(33+2j) << 24,
+// and transpose16 swaps bit and word index within each 16-bit half of u
+// (the 8-, 4-, 2- and 1-bit stages of transpose32 over 16 words).  Then
+// u[r] is transpose32's row narrow_row(r) and the other rows are zero.
+__host__ __device__ __forceinline__ void squeeze_narrow(const uint32_t (&w)[32],
+                                                        uint32_t (&u)[16]) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    // byte 0 / 2 of w | w >> 8: a code's magnitude byte with its sign bit
+    const uint32_t lo = w[j] | (w[j] >> 8), hi = w[j + 16] | (w[j + 16] >> 8);
+    u[j] = byte_perm(lo, hi, 0x6420);
+  }
+}
+
+__host__ __device__ __forceinline__ void transpose16(uint32_t (&a)[16]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    uint32_t x = a[k], y = a[k + 8];
+    a[k] = byte_perm(x, y, 0x6240);
+    a[k + 8] = byte_perm(x, y, 0x7351);
+  }
+#pragma unroll
+  for (int k0 = 0; k0 < 16; k0 += 8) {
+#pragma unroll
+    for (int k = k0; k < k0 + 4; ++k) {
+      uint32_t x = a[k], y = a[k + 4];
+      a[k] = (x & 0x0F0F0F0Fu) | ((y << 4) & 0xF0F0F0F0u);
+      a[k + 4] = ((x >> 4) & 0x0F0F0F0Fu) | (y & 0xF0F0F0F0u);
+    }
+  }
+#pragma unroll
+  for (int k0 = 0; k0 < 16; k0 += 4) {
+#pragma unroll
+    for (int k = k0; k < k0 + 2; ++k) {
+      uint32_t x = a[k], y = a[k + 2];
+      a[k] = (x & 0x33333333u) | ((y << 2) & 0xCCCCCCCCu);
+      a[k + 2] = ((x >> 2) & 0x33333333u) | (y & 0xCCCCCCCCu);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 16; k += 2) {
+    uint32_t x = a[k], y = a[k + 1];
+    a[k] = (x & 0x55555555u) | ((y << 1) & 0xAAAAAAAAu);
+    a[k + 1] = ((x >> 1) & 0x55555555u) | (y & 0xAAAAAAAAu);
+  }
+}
+
+// transpose32's row held by transpose16's word r: even codes' planes 0..6
+// and 15 (sign), then odd codes' planes 16..22 and 31
+__host__ __device__ __forceinline__ constexpr int narrow_row(int r) {
+  return 16 * (r >> 3) + ((r & 7) == 7 ? 15 : (r & 7));
+}
+
 // ------------------------------------------------------------ eb derivation
 // Sec. 4.1: the absolute bound from the request (relative bounds scale the
 // value range).  Same rules as the stream format: double arithmetic, the
