@@ -129,6 +129,22 @@ __device__ __forceinline__ void decode_codes(const uint32_t (&w)[32], int32_t (&
   }
 }
 
+// decode a narrow tile's 16 byte-code words (transpose16's output: byte k of
+// u[j] is code 2j, 2j+1, 32+2j, 33+2j for k = 0..3; magnitude in bits 0..6,
+// sign in bit 7) to residuals; an escape (sign only) decodes to 0
+__device__ __forceinline__ void decode_narrow(const uint32_t (&u)[16], int32_t (&v)[64]) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const uint32_t x = u[j];
+    const uint32_t s0 = prmt_sign(x, 0x8888), s1 = prmt_sign(x, 0x9999);
+    const uint32_t s2 = prmt_sign(x, 0xAAAA), s3 = prmt_sign(x, 0xBBBB);
+    v[2 * j] = (int32_t)(((x & 0x7Fu) ^ s0) - s0);
+    v[2 * j + 1] = (int32_t)((((x >> 8) & 0x7Fu) ^ s1) - s1);
+    v[32 + 2 * j] = (int32_t)((((x >> 16) & 0x7Fu) ^ s2) - s2);
+    v[33 + 2 * j] = (int32_t)((((x >> 24) & 0x7Fu) ^ s3) - s3);
+  }
+}
+
 // inverse Lorenzo inside the tile: v holds residuals in, q out.  `carry`
 // holds the previous tile's boundary values of q (3-D: this brick's last
 // plane, 2-D: the last row, 1-D: the last element) and is updated.
@@ -292,6 +308,7 @@ __device__ __forceinline__ bool gather_tile(const uint8_t *payload, uint64_t nnz
 // chunk's 32) and, per tile, the payload index of lane b's first block.
 struct ChunkPlan {
   uint32_t fw;
+  uint32_t narrow;            // bit t: tile t's planes of magnitude bits 7..14 are all absent
   uint64_t base;              // the chunk's first payload block
   uint32_t p01, p23;          // per-lane exclusive ranks, tiles 0/1 and 2/3 (16-bit halves)
   uint32_t c01, c23;          // tile block counts, same packing
@@ -302,6 +319,14 @@ __device__ __forceinline__ ChunkPlan plan_chunk(uint32_t fw, uint64_t base, int 
   ChunkPlan p;
   p.fw = fw;
   p.base = base;
+  // lane l holds flag bytes 4(l & 7) .. +3 of tile l >> 3: the bytes of
+  // planes 7..14 and 23..30
+  const uint32_t wi = (uint32_t)g & 3u;
+  const uint32_t hm = wi == 1 ? 0xFF000000u : wi == 2 ? 0xFFFFFFFFu : wi == 3 ? 0x00FFFFFFu : 0u;
+  const uint32_t wide = __ballot_sync(full, (fw & hm) != 0u);
+  p.narrow = 0;
+#pragma unroll
+  for (int t = 0; t < kTilesPerChunk; ++t) p.narrow |= (((wide >> (8 * t)) & 0xFFu) == 0u) << t;
   uint32_t a = __popc(plane_flags(fw, 0, g)) | (__popc(plane_flags(fw, 1, g)) << 16);
   uint32_t b = __popc(plane_flags(fw, 2, g)) | (__popc(plane_flags(fw, 3, g)) << 16);
   uint32_t ia = a, ib = b;                    // two tiles per scan: sums <= 256
@@ -361,6 +386,7 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
   };
   // the first chunk's four tiles are requested up front
   ChunkPlan cp = load_plan(c);
+  uint32_t cur_narrow = cp.narrow;   // the current chunk's narrow tiles
 #pragma unroll
   for (int t = 0; t < kTilesPerChunk; ++t) {
     if (c < h.n_chunks) oob |= gather_tile(payload, h.nnz, pbuf + 1024 * t, plane_flags(cp.fw, t, g),
@@ -396,6 +422,7 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
       x0 = cx * 8192 + 64 * g; y0 = 0; z0 = 0;
     }
     ChunkPlan np{};
+    const uint32_t narrow_c = cur_narrow;
     int32_t carry[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) carry[e] = 0;
@@ -404,9 +431,20 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
       cp_async_wait<3>();                // this tile's group (3 newer ones may pend)
       __syncwarp();
       uint32_t *pb = pbuf + 1024 * t;
+      // a narrow tile (every code within 7 bits and the sign) has 16 live
+      // planes, read into w[0..15] (plane narrow_row(k) in w[k])
+      const bool narrow = (narrow_c >> t) & 1u;
       uint32_t w[32];
+      if (narrow) {
 #pragma unroll
-      for (int b = 0; b < 32; ++b) w[b] = pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)];
+        for (int k = 0; k < 16; ++k) {
+          const int b = narrow_row(k);
+          w[k] = pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)];
+        }
+      } else {
+#pragma unroll
+        for (int b = 0; b < 32; ++b) w[b] = pb[32 * b + 4 * ((g >> 2) ^ (b & 7)) + (g & 3)];
+      }
       __syncwarp();                      // the buffer is free: refill it for the next chunk
       if (t == 0) np = plan_chunk(fw_n, base_n, g);
       if (cn < h.n_chunks)
@@ -415,10 +453,17 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
         cp_async_commit();
       // codes on the bit planes (before the transpose): bit t of a mask is
       // word t of this lane's brick, low code (even element) or high code
-      uint32_t lo_or = 0, hi_or = 0;
+      uint32_t lo_or = 0, hi_or = 0, sg_ev, sg_od;
+      if (narrow) {
 #pragma unroll
-      for (int b = 0; b < 15; ++b) { lo_or |= w[b]; hi_or |= w[b + 16]; }
-      uint32_t esc_ev = w[15] & ~lo_or, esc_od = w[31] & ~hi_or;   // 0x8000: an escape
+        for (int k = 0; k < 7; ++k) { lo_or |= w[k]; hi_or |= w[k + 8]; }
+        sg_ev = w[7]; sg_od = w[15];
+      } else {
+#pragma unroll
+        for (int b = 0; b < 15; ++b) { lo_or |= w[b]; hi_or |= w[b + 16]; }
+        sg_ev = w[15]; sg_od = w[31];
+      }
+      uint32_t esc_ev = sg_ev & ~lo_or, esc_od = sg_od & ~hi_or;   // 0x8000: an escape
       // this tile's brick origin
       uint64_t bxo = x0, byo = y0, bzo = z0;
       if constexpr (NDIM == 3) bzo += 2 * t;
@@ -431,13 +476,19 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
         const uint32_t lz = extent_in(bzo, h.dims[2], G::BZ);
         uint32_t in_ev, in_od;
         inside_masks<NDIM>(lx, ly, lz, in_ev, in_od);
-        bad |= ((lo_or | w[15]) & ~in_ev) | ((hi_or | w[31]) & ~in_od);
+        bad |= ((lo_or | sg_ev) & ~in_ev) | ((hi_or | sg_od) & ~in_od);
         esc_ev &= in_ev;
         esc_od &= in_od;
       }
-      transpose32(w);                    // lane g: the 32 code words of brick g
       int32_t v[64];
-      decode_codes(w, v);                // an escape decodes to 0
+      if (narrow) {
+        uint32_t(&u)[16] = *reinterpret_cast<uint32_t(*)[16]>(&w[0]);
+        transpose16(u);                  // lane g: brick g's codes as bytes
+        decode_narrow(u, v);
+      } else {
+        transpose32(w);                  // lane g: the 32 code words of brick g
+        decode_codes(w, v);              // an escape decodes to 0
+      }
       if (__any_sync(full, (esc_ev | esc_od) != 0)) {
         // rare: patch each escape with its recorded residual
         const uint32_t tile_code0 = (uint32_t)((c * kTilesPerChunk + t) * kTileCodes) + 64 * g;
@@ -494,6 +545,7 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
       if (g == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&cur->nout), (unsigned long long)m);
       matched = 0;
     }
+    cur_narrow = np.narrow;
     c = cn;
   }
   cp_async_wait<0>();
