@@ -48,7 +48,7 @@ WORKLOAD_DESC = ("512x512x512 float32 lognormal density exp(0.5 g), g a unit-std
 # (summarised in profiles/launches_cosmo3d_512.md).  A figure stands only while
 # the kernel's sources are the ones that were captured (SHA-256 over them).
 TRAFFIC = {
-    "compress_kernel": (("fz_compress.cu", "fz_device.cuh", "fz_kernels.h"),
+    "compress_kernel": (("fz_compress.cu", "fz_compress_impl.cuh", "fz_device.cuh", "fz_kernels.h"),
                         "7848fa3be9332971cd7adf5c3acfb507362f658e856f28641d94bd81efee1463",
                         537911552 + 75093504),
     "decompress_kernel": (("fz_decompress.cu", "fz_device.cuh", "fz_kernels.h"),

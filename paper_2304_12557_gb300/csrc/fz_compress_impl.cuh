@@ -586,7 +586,9 @@ __device__ __forceinline__ void post_ticket(const CompressArgs &a0, const BatchA
 
 // The scan warp: tickets two rounds ahead, then per round the unit's
 // aggregate, its decoupled look-back (in its field's domain) and the tiles'
-// exclusive prefixes.
+// exclusive prefixes.  Round r + 2's ticket reuses round r - 2's ring
+// entry, which every compute warp has read once round r's aggregates are
+// all posted.
 template <bool BATCH>
 __device__ __forceinline__ void scan_warp(const CompressArgs &a0, const BatchArgs &b,
                                           CompShared *sh, uint64_t n_units, int g) {
@@ -606,11 +608,16 @@ __device__ __forceinline__ void scan_warp(const CompressArgs &a0, const BatchArg
     if (u >= n_units) break;
     const CompressArgs &a = BATCH ? b.fields[f] : a0;
     SetScratch *cur = a.set_cur;
-    if (g == 0) post_ticket<BATCH>(a0, b, sh, r + 2, n_units);
     if (!warp_wait(&sh->agg_bar[s], (r / kRing) & 1u, a.wait_limit_ns)) {
       if (g == 0) atomicOr(&cur->err, kErrTimeout);
       break;
     }
+    // The ticket for round r + 2 is taken once this block has finished
+    // round r: the later units are handed out, the closer their order is
+    // to the order in which blocks finish them, and the less a look-back
+    // waits for a predecessor's aggregate.  (Taken earlier, or by a compute
+    // warp at the start of a round, the compressor ran 1 to 6% slower.)
+    if (g == 0) post_ticket<BATCH>(a0, b, sh, r + 2, n_units);
     const uint64_t t_agg = g < kCompWarps ? sh->slot[s].agg[g] : 0;
     uint64_t inc = t_agg;
 #pragma unroll
