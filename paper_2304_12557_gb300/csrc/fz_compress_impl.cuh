@@ -811,21 +811,22 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       // every code of the tile fits in 7 bits and the sign: the planes of
       // magnitude bits 7..14 are zero and half the transpose is skipped
       const bool narrow = !__any_sync(full, orabs > 127u);
-      uint32_t nout_lane = 0;
-      if (!narrow && __any_sync(full, (orabs >> 15) != 0)) {
-        // rare: some |residual| needs more than 15 bits; recompute and repack
-        // with escapes out of line (through the plane buffer)
-        nout_lane = escape_repack<NDIM, V>(a, T, g, rt.p.ebx2_r, pb);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
-        __syncwarp();
-      }
-      if constexpr (kDef == 0) {                     // drain the single plane buffer
+      if constexpr (kDef == 0) {
+        // drain the single plane buffer before anything below writes it
         if (prev1.T != kNoTile) {
           const CompressArgs &a1 = BATCH ? b.fields[prev1.field] : a0;
           finish_tile<NDIM>(a1, sh, prev1, pb_of(prev1), rt_of(prev1.field), g, wid);
           prev1.T = kNoTile;
         }
+      }
+      uint32_t nout_lane = 0;
+      if (!narrow && __any_sync(full, (orabs >> 15) != 0)) {
+        // rare: some |residual| needs more than 15 bits; recompute and repack
+        // with escapes out of line (through this round's plane buffer)
+        nout_lane = escape_repack<NDIM, V>(a, T, g, rt.p.ebx2_r, pb);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
+        __syncwarp();
       }
 
       // plane buffer: lane b collects plane b's 32 words (8 blocks); a

@@ -121,6 +121,27 @@ def test_batch_equals_single_field_streams(codec, torch):
         b.close()
 
 
+def test_batch_escapes_in_consecutive_rounds(codec, torch):
+    """Fields with escapes in nearly every tile and several rounds of work
+    per block: a warp repacks an escaped tile while its previous tile's
+    blocks are still waiting to be stored (the batch keeps one plane buffer
+    per warp), in 2-D and 3-D, and in a relative-bound field."""
+    specs = [
+        (_outliers((96, 256, 256), 12000, 31), 3, "abs", 0.5),
+        (_outliers((1024, 1536), 4000, 32), 2, "abs", 0.5),
+        (_outliers((64, 128, 256), 6000, 33), 3, "rel", 1e-6),
+        (fields.bumps3d(64), 3, "rel", 1e-3),
+    ]
+    xs, outs, b = _make_batch(codec, torch, specs)
+    try:
+        sizes, sts = b.compress()
+        _check(codec, specs, xs, outs, sizes, sts)
+        for i in range(3):
+            assert fz.inspect(outs[i][:64].cpu().numpy().tobytes())["n_outliers"] >= 3000
+    finally:
+        b.close()
+
+
 def test_batch_relative_only(codec, torch):
     """A batch of relative bounds only: its kernels skip the per-element
     quantiser check (the range pass has bounded every element)."""
