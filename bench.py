@@ -49,14 +49,14 @@ WORKLOAD_DESC = ("512x512x512 float32 lognormal density exp(0.5 g), g a unit-std
 # the kernel's sources are the ones that were captured (SHA-256 over them).
 TRAFFIC = {
     "compress_kernel": (("fz_compress.cu", "fz_compress_impl.cuh", "fz_device.cuh", "fz_kernels.h"),
-                        "7848fa3be9332971cd7adf5c3acfb507362f658e856f28641d94bd81efee1463",
-                        537911552 + 75093504),
+                        "ed8ff315521d5da5d8881d1990c8685a249c5370ba22054d09e2fab6529b70fe",
+                        537792153 + 75886796),
     "decompress_kernel": (("fz_decompress.cu", "fz_device.cuh", "fz_kernels.h"),
-                          "a2b4d2184226bfdbc91457a554e229f0e0184ada3926d18b2c5e6100ad6be55c",
-                          96762624 + 471520512),
+                          "c8fceaa7e3398959cd0d919313cc37b500f0b4df04da441fad812c248a8aabad",
+                          96726988 + 471463577),
     "range_kernel": (("fz_compress.cu", "fz_device.cuh", "fz_kernels.h"),
-                     "7848fa3be9332971cd7adf5c3acfb507362f658e856f28641d94bd81efee1463",
-                     536888832 + 2733312),
+                     "d406611d5b0289bea3e6a49d4f7b3911bdeb0221e5b207086201ee3ea759d7c3",
+                     536893835 + 325585),
 }
 
 
