@@ -21,7 +21,10 @@ namespace fz {
 
 constexpr int kDecWarps = 4;                    // decompression: warps per block
 constexpr int kOffChunks = 512;                 // offsets pass: chunks (threads) per block
-constexpr int kDecSmemBytes = kDecWarps * kTilesPerChunk * 4096;
+// per warp: four tile buffers (the next chunk's tiles, gathered ahead) and a
+// 1 KB staging area for row stores of fields whose rows are not 16-byte aligned
+constexpr int kDecWarpSmem = kTilesPerChunk * 4096 + 1024;
+constexpr int kDecSmemBytes = kDecWarps * kDecWarpSmem;
 
 struct Hdr {
   int ndim, mode;
@@ -510,32 +513,66 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
       if (t == 0 && g == 0) v[0] += (int32_t)kMagicBits;
       inverse_lorenzo<NDIM>(v, carry, g);
       // q -> fl(float(q) * 2eb), 8-float rows
-      float *base = a.out + bxo + X * (byo + Y * bzo);
-#pragma unroll
-      for (int row = 0; row < 8; ++row) {
-        float f[8];
+      auto row_floats = [&](int row, float (&f)[8]) {
 #pragma unroll
         for (int k = 0; k < 8; ++k)
           f[k] = __fmul_rn(__fsub_rn(__int_as_float(v[8 * row + k]), kRoundMagic), e2);
-        int iy, iz, ix;
-        if constexpr (NDIM == 3) { ix = 0; iy = row % 4; iz = row / 4; }
-        else if constexpr (NDIM == 2) { ix = 0; iy = row; iz = 0; }
-        else { ix = 8 * row; iy = 0; iz = 0; }
-        float *dst = base + ix + X * (iy + Y * iz);
-        const bool row_in = !edge || (byo + iy < Y && bzo + iz < h.dims[2]);
-        const bool full_row = !edge || (row_in && bxo + ix + 8 <= X);
-        if (full_row && vw == 8) {
-          asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst),
-                       "f"(f[0]), "f"(f[1]), "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]),
-                       "f"(f[6]), "f"(f[7])
-                       : "memory");
-        } else if (full_row && vw == 4) {
-          __stcs(reinterpret_cast<float4 *>(dst), make_float4(f[0], f[1], f[2], f[3]));
-          __stcs(reinterpret_cast<float4 *>(dst) + 1, make_float4(f[4], f[5], f[6], f[7]));
-        } else if (row_in) {
+      };
+      bool staged = false;
+      if constexpr (NDIM >= 2) staged = vw == 1;
+      if (staged) {
+        // rows not 16-byte aligned: per row index, stage the warp's 8 (3-D)
+        // or 4 (2-D) row segments in shared memory and store them 32
+        // consecutive floats per instruction
+        constexpr int SEG = 8 * G::NBX;              // floats per row segment
+        float *st = reinterpret_cast<float *>(pbuf + kTilesPerChunk * 1024);
+        float4 *s4 = reinterpret_cast<float4 *>(st + (g / G::NBX) * SEG + 8 * (g % G::NBX));
+        // segment origin: the chunk's x, this tile's rows
+        const uint64_t xc = bxo - 8 * (g % G::NBX);
+        const uint64_t yc = byo - (uint64_t)G::BY * (g / G::NBX);
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            if (bxo + ix + k < X) __stcs(dst + k, f[k]);
+        for (int row = 0; row < 8; ++row) {
+          float f[8];
+          row_floats(row, f);
+          const int iy = NDIM == 3 ? row % 4 : row, iz = NDIM == 3 ? row / 4 : 0;
+          s4[0] = make_float4(f[0], f[1], f[2], f[3]);
+          s4[1] = make_float4(f[4], f[5], f[6], f[7]);
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int e = 32 * j + g, sb = e / SEG, xo = e % SEG;
+            const uint64_t x = xc + xo, y = yc + (uint64_t)G::BY * sb + iy, z = bzo + iz;
+            if (!edge || (x < X && y < Y && z < h.dims[2]))
+              __stcs(a.out + x + X * (y + Y * z), st[e]);
+          }
+          __syncwarp();                      // the staging area is free again
+        }
+      } else {
+        float *base = a.out + bxo + X * (byo + Y * bzo);
+#pragma unroll
+        for (int row = 0; row < 8; ++row) {
+          float f[8];
+          row_floats(row, f);
+          int iy, iz, ix;
+          if constexpr (NDIM == 3) { ix = 0; iy = row % 4; iz = row / 4; }
+          else if constexpr (NDIM == 2) { ix = 0; iy = row; iz = 0; }
+          else { ix = 8 * row; iy = 0; iz = 0; }
+          float *dst = base + ix + X * (iy + Y * iz);
+          const bool row_in = !edge || (byo + iy < Y && bzo + iz < h.dims[2]);
+          const bool full_row = !edge || (row_in && bxo + ix + 8 <= X);
+          if (full_row && vw == 8) {
+            asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst),
+                         "f"(f[0]), "f"(f[1]), "f"(f[2]), "f"(f[3]), "f"(f[4]), "f"(f[5]),
+                         "f"(f[6]), "f"(f[7])
+                         : "memory");
+          } else if (full_row && vw == 4) {
+            __stcs(reinterpret_cast<float4 *>(dst), make_float4(f[0], f[1], f[2], f[3]));
+            __stcs(reinterpret_cast<float4 *>(dst) + 1, make_float4(f[4], f[5], f[6], f[7]));
+          } else if (row_in) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (bxo + ix + k < X) __stcs(dst + k, f[k]);
+          }
         }
       }
     }
@@ -637,7 +674,7 @@ __global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const Dec
   const int w = threadIdx.x >> 5;
   const Hdr h = read_header(a);
   if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
-  uint32_t *pbuf = dsmem + w * kTilesPerChunk * 1024;
+  uint32_t *pbuf = dsmem + w * (kDecWarpSmem / 4);
   if (h.ndim == 3) decompress_chunks<3>(a, h, pbuf, cur);
   else if (h.ndim == 2) decompress_chunks<2>(a, h, pbuf, cur);
   else decompress_chunks<1>(a, h, pbuf, cur);
