@@ -52,8 +52,8 @@ TRAFFIC = {
                         "ed8ff315521d5da5d8881d1990c8685a249c5370ba22054d09e2fab6529b70fe",
                         537792153 + 75886796),
     "decompress_kernel": (("fz_decompress.cu", "fz_device.cuh", "fz_kernels.h"),
-                          "c8fceaa7e3398959cd0d919313cc37b500f0b4df04da441fad812c248a8aabad",
-                          96726988 + 471463577),
+                          "cde1068fa26470b922029f9a3fa6d00eb527389b5550293f4e5d99cbaebb996c",
+                          96757964 + 471637555),
     "range_kernel": (("fz_compress.cu", "fz_device.cuh", "fz_kernels.h"),
                      "d406611d5b0289bea3e6a49d4f7b3911bdeb0221e5b207086201ee3ea759d7c3",
                      536893835 + 325585),
