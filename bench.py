@@ -662,10 +662,43 @@ def run_quality(args, rank):
                          "psnr_db": 20 * math.log10(vr / rmse) if rmse > 0 else float("inf"),
                          "ssim": ss, "nnz_block_fraction": info["nnz_blocks"] / (256 * info["n_tiles"]),
                          "outliers": info["n_outliers"]})
+    # point-wise relative bounds through the log transform (Sec. 4.1's
+    # particle data): sign words count towards the compressed size
+    xp = torch.from_numpy(fields.particles1d(1 << 24)).to(dev)
+    pw_rows = []
+    for eps in (1e-2, 1e-3, 1e-4):
+        y, signs = codec.pwrel_forward(xp)
+        s = codec.compress(y, mode="abs", eb=fz.pwrel_bound(eps), ndim=1)
+        xr = codec.pwrel_inverse(codec.decompress(s), signs)
+        nz = xp != 0
+        rel = ((xr.double() - xp.double()).abs()[nz] / xp.double().abs()[nz]).max().item()
+        nbytes = s.numel() + signs.numel() * 4
+        pw_rows.append({"field": "particles1d_16M", "pw_rel_eps": eps,
+                        "ratio": 4 * xp.numel() / nbytes,
+                        "bits_per_value": 8 * nbytes / xp.numel(),
+                        "sign_bits_per_value": 32 * signs.numel() / xp.numel(),
+                        "max_rel_err_over_eps": rel / eps,
+                        "exact_zeros": bool((xr[~nz] == 0).all().item())})
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_f, t_i = [], []
+    for _ in range(10):
+        ev[0].record()
+        y, signs = codec.pwrel_forward(xp)
+        ev[1].record()
+        codec.pwrel_inverse(y, signs)
+        ev[2].record()
+        torch.cuda.synchronize()
+        t_f.append(ev[0].elapsed_time(ev[1]))
+        t_i.append(ev[1].elapsed_time(ev[2]))
     codec.close()
     print(json.dumps({"metric": "rate-distortion of the synthetic fields (ratio, PSNR, SSIM)",
                       "value": None, "unit": None, "config": {"workload": "quality"},
-                      "rows": rows}), flush=True)
+                      "rows": rows, "pwrel_rows": pw_rows,
+                      "pwrel_transform_ms": {"forward_p50": statistics.median(t_f),
+                                             "inverse_p50": statistics.median(t_i),
+                                             "elements": xp.numel(),
+                                             "note": "forward includes its flag read-back"}}),
+          flush=True)
 
 
 def main():

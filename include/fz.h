@@ -378,6 +378,42 @@ int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], int ndim,
                         uint64_t out_capacity, uint64_t *out_size,
                         void *stream);
 
+/* ---------------------------------------------------------------------
+ * Point-wise relative error bounds by log transform (Sec. 4.1: the
+ * particle dataset is compressed log-transformed, with the absolute bound
+ * that the point-wise relative bound implies).  The caller runs
+ *
+ *   fz_pwrel_forward(x) -> y, signs;   fz_compress(y, FZ_EB_ABS, eb_abs)
+ *   fz_decompress -> y';               fz_pwrel_inverse(y', signs) -> x'
+ *
+ * with eb_abs from fz_pwrel_bound(eps); then |x' - x| <= eps |x| for every
+ * element whose magnitude is 0 or at least FLT_MIN (2^-126), and
+ * |x' - x| <= max(eps |x|, 2^-149) for the subnormal ones (the spacing of
+ * the subnormal grid).  The sign bits travel beside the stream: one 32-bit
+ * word per 32 elements, bit i % 32 of word i / 32 set for a negative x[i]
+ * (or -0).
+ *
+ * fz_pwrel_bound: eb_abs = log2(1 + eps) - 2^-14 (the margin covers the
+ * fp32 rounding of the log values, of the quantiser and of the
+ * reconstruction at log magnitudes up to 160, and of the transforms
+ * themselves).  FZ_OK, or FZ_ERR_ARG unless 1e-4 <= eps <= 0.5.
+ *
+ * fz_pwrel_forward: y[i] = log2|x[i]| (fp32; -160 for a zero, which
+ * fz_pwrel_inverse maps back to 0 exactly: every nonzero float has
+ * log2 >= -149), signs as above.  d_x, d_y: n floats each, 4-byte aligned;
+ * d_signs: (n + 31) / 32 words.  Synchronises `stream`.  FZ_OK,
+ * FZ_ERR_NONFINITE (NaN or Inf in x; y and signs are then unspecified),
+ * FZ_ERR_ARG or FZ_ERR_CUDA.
+ *
+ * fz_pwrel_inverse: x[i] = +-2^y[i] with the sign from d_signs, 0 where
+ * y[i] < -154, +-FLT_MAX where y[i] >= 128.  Asynchronous on `stream`.
+ * FZ_OK, FZ_ERR_ARG or FZ_ERR_CUDA. */
+int fz_pwrel_bound(double eps, double *eb_abs);
+int fz_pwrel_forward(fz_ctx *ctx, const float *d_x, uint64_t n, float *d_y,
+                     uint32_t *d_signs, void *stream);
+int fz_pwrel_inverse(fz_ctx *ctx, const float *d_y, uint64_t n, const uint32_t *d_signs,
+                     float *d_x, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

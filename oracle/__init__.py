@@ -101,6 +101,14 @@ def lib() -> ctypes.CDLL:
             L.fzo_reconstruct_closed_form.argtypes = [_f32p, ctypes.c_uint64,
                                                       ctypes.c_float,
                                                       ctypes.c_float, _f32p]
+            L.fzo_pwrel_bound.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+            L.fzo_pw_log2.argtypes = [ctypes.c_float]
+            L.fzo_pw_log2.restype = ctypes.c_float
+            L.fzo_pw_exp2.argtypes = [ctypes.c_float]
+            L.fzo_pw_exp2.restype = ctypes.c_float
+            L.fzo_pwrel_forward.argtypes = [_f32p, ctypes.c_uint64, _f32p, _u32p]
+            L.fzo_pwrel_inverse.argtypes = [_f32p, ctypes.c_uint64, _u32p, _f32p]
+            L.fzo_pwrel_inverse.restype = None
             _lib = L
     return _lib
 
@@ -266,3 +274,37 @@ def reconstruct_closed_form(x: np.ndarray, ebx2_r, ebx2):
                                            float(ebx2_r), float(ebx2),
                                            _ptr(out, _f32p))
     return st, out
+
+
+# ------------------------------------------- point-wise relative bounds
+def pwrel_bound(eps: float):
+    """(status, eb_abs): the absolute bound for the log values (Sec. 4.1)."""
+    e = ctypes.c_double()
+    st = lib().fzo_pwrel_bound(eps, ctypes.byref(e))
+    return st, e.value
+
+
+def pw_log2(a: float) -> np.float32:
+    return np.float32(lib().fzo_pw_log2(a))
+
+
+def pw_exp2(y: float) -> np.float32:
+    return np.float32(lib().fzo_pw_exp2(y))
+
+
+def pwrel_forward(x: np.ndarray):
+    """(status, y, signs): y = log2|x| (-160 for zeros), sign bits packed
+    32 per uint32 word."""
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+    y = np.empty_like(x)
+    signs = np.zeros((x.size + 31) // 32, np.uint32)
+    st = lib().fzo_pwrel_forward(_ptr(x, _f32p), x.size, _ptr(y, _f32p), _ptr(signs, _u32p))
+    return st, y, signs
+
+
+def pwrel_inverse(y: np.ndarray, signs: np.ndarray) -> np.ndarray:
+    y = np.ascontiguousarray(y, dtype=np.float32).reshape(-1)
+    signs = np.ascontiguousarray(signs, dtype=np.uint32)
+    x = np.empty_like(y)
+    lib().fzo_pwrel_inverse(_ptr(y, _f32p), y.size, _ptr(signs, _u32p), _ptr(x, _f32p))
+    return x

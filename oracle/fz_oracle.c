@@ -589,3 +589,89 @@ int fzo_reconstruct_closed_form(const float *x, uint64_t n, float ebx2_r,
   }
   return FZO_OK;
 }
+
+
+/* ====================================================================
+ * point-wise relative bounds by log transform (Sec. 4.1)
+ * ==================================================================== */
+int fzo_pwrel_bound(double eps, double *eb_abs) {
+  if (!eb_abs || !(eps >= 1e-4 && eps <= 0.5)) return FZO_ERR_ARG;
+  *eb_abs = log2(1.0 + eps) - ldexp(1.0, -14);
+  return FZO_OK;
+}
+
+static uint32_t f2u(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+static float u2f(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+
+float fzo_pw_log2(float a) {
+  uint32_t b = f2u(a);
+  int e = 0;
+  if (b < 0x00800000u) {                 /* subnormal: times 2^23, exact */
+    a = a * 8388608.0f;
+    b = f2u(a);
+    e = -23;
+  }
+  e += (int)(b >> 23) - 127;
+  float m = u2f((b & 0x007FFFFFu) | 0x3F800000u);
+  float num = m - 1.0f;
+  float den = m + 1.0f;
+  float s = num / den;
+  float s2 = s * s;
+  /* 2 atanh(s) = 2 s (1 + s^2/3 + s^4/5 + ... + s^12/13), inner sum by Horner */
+  float p = 0.07692308f;
+  p = p * s2; p = p + 0.09090909f;
+  p = p * s2; p = p + 0.11111111f;
+  p = p * s2; p = p + 0.14285715f;
+  p = p * s2; p = p + 0.2f;
+  p = p * s2; p = p + 0.33333334f;
+  p = p * s2; p = p + 1.0f;
+  float two_s = 2.0f * s;
+  float ln_m = two_s * p;
+  float l2 = ln_m * 1.442695f;            /* 1 / ln 2 */
+  return (float)e + l2;
+}
+
+float fzo_pw_exp2(float y) {
+  if (!(y < 128.0f)) return FLT_MAX;
+  if (y < -150.0f) return 0.0f;
+  float k = floorf(y);
+  float f = y - k;                        /* exact, in [0, 1) */
+  float u = f * 0.6931472f;               /* ln 2 */
+  /* exp(u) = 1 + u (1 + u/2 (1 + u/3 (...))), written as the power series
+   * sum u^n / n!, n = 0..10, by Horner from the top */
+  float p = 2.755732e-07f;
+  p = p * u; p = p + 2.7557319e-06f;
+  p = p * u; p = p + 2.4801588e-05f;
+  p = p * u; p = p + 0.0001984127f;
+  p = p * u; p = p + 0.0013888889f;
+  p = p * u; p = p + 0.008333334f;
+  p = p * u; p = p + 0.041666668f;
+  p = p * u; p = p + 0.16666667f;
+  p = p * u; p = p + 0.5f;
+  p = p * u; p = p + 1.0f;
+  p = p * u; p = p + 1.0f;
+  int ki = (int)k;
+  if (ki >= -126) return p * u2f((uint32_t)(ki + 127) << 23);
+  float t = p * u2f((uint32_t)(ki + 126 + 127) << 23);
+  return t * 1.17549435e-38f;             /* 2^-126 */
+}
+
+int fzo_pwrel_forward(const float *x, uint64_t n, float *y, uint32_t *signs) {
+  int bad = 0;
+  for (uint64_t w = 0; w < (n + 31) / 32; ++w) signs[w] = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    uint32_t b = f2u(x[i]);
+    if (b >> 31) signs[i / 32] |= 1u << (i % 32);
+    if ((b & 0x7F800000u) == 0x7F800000u) { bad = 1; y[i] = -160.0f; continue; }
+    float a = fabsf(x[i]);
+    y[i] = a == 0.0f ? -160.0f : fzo_pw_log2(a);
+  }
+  return bad ? FZO_ERR_NONFINITE : FZO_OK;
+}
+
+void fzo_pwrel_inverse(const float *y, uint64_t n, const uint32_t *signs, float *x) {
+  for (uint64_t i = 0; i < n; ++i) {
+    float a = y[i] < -154.0f ? 0.0f : fzo_pw_exp2(y[i]);
+    x[i] = ((signs[i / 32] >> (i % 32)) & 1u) ? -a : a;
+  }
+}

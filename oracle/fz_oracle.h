@@ -114,6 +114,32 @@ int fzo_decompress(const uint8_t *in, uint64_t in_size, float *x,
 int fzo_reconstruct_closed_form(const float *x, uint64_t n, float ebx2_r,
                                 float ebx2, float *xr);
 
+/* --- point-wise relative bounds by log transform ---------------------
+ * Sec. 4.1 compresses the particle dataset log-transformed, with the
+ * absolute bound a point-wise relative bound implies.  The transform is
+ * y = log2|x| with the sign kept as a bit; a zero becomes -160 (every
+ * nonzero float has log2 >= -149) and comes back as 0 below -154.
+ * log2 and exp2 are evaluated in fp32 by fixed formulas, one IEEE
+ * round-to-nearest operation at a time:
+ *   log2 a = e + ln(m) / ln 2 for a = m 2^e, m in [1, 2), with
+ *     ln m = 2 (s + s^3/3 + ... + s^13/13), s = (m - 1) / (m + 1);
+ *   2^y = 2^k exp(u), k = floor(y), u = (y - k) ln 2, with
+ *     exp(u) = sum of u^n / n! for n <= 10 (Horner).
+ * These are approximations, pinned by the tests against the closed forms
+ * (math.log2, 2**y), exact at powers of two, and by the end-to-end bound
+ * |x' - x| <= eps |x| through the compressor. */
+
+/* eb_abs = log2(1 + eps) - 2^-14; FZO_ERR_ARG unless 1e-4 <= eps <= 0.5 */
+int fzo_pwrel_bound(double eps, double *eb_abs);
+float fzo_pw_log2(float a);     /* a > 0, finite */
+float fzo_pw_exp2(float y);     /* finite y */
+/* y[i] = log2|x[i]| (-160 for zeros); signs: (n + 31) / 32 words, bit i % 32
+ * of word i / 32 set for a negative (or -0) x[i].  FZO_OK or
+ * FZO_ERR_NONFINITE (y then unspecified). */
+int fzo_pwrel_forward(const float *x, uint64_t n, float *y, uint32_t *signs);
+/* x[i] = +-2^y[i] (0 below -154, +-FLT_MAX from 128 up) */
+void fzo_pwrel_inverse(const float *y, uint64_t n, const uint32_t *signs, float *x);
+
 #ifdef __cplusplus
 }
 #endif

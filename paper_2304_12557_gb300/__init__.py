@@ -45,7 +45,8 @@ C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
          "fz_batch_compress", "fz_batch_set_graph", "fz_batch_autotune",
          "fz_batch_tuning", "fz_server_create", "fz_server_destroy",
          "fz_server_submit", "fz_server_poll", "fz_server_fetch",
-         "fz_server_get_stats", "fz_compress_staged", "fz_compress_noalloc"]
+         "fz_server_get_stats", "fz_compress_staged", "fz_compress_noalloc",
+         "fz_pwrel_bound", "fz_pwrel_forward", "fz_pwrel_inverse"]
 
 _lib = None
 _lock = threading.Lock()
@@ -130,6 +131,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_compress_noalloc.argtypes = [_vp, dims_t, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, _vp, _u64,
                                           ctypes.POINTER(_u64), _vp]
+        L.fz_pwrel_bound.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+        L.fz_pwrel_forward.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp]
+        L.fz_pwrel_inverse.argtypes = [_vp, _vp, _u64, _vp, _vp, _vp]
         L.fz_range.argtypes = [_vp, _vp, _u64, ctypes.POINTER(ctypes.c_float),
                                ctypes.POINTER(ctypes.c_float),
                                ctypes.POINTER(ctypes.c_int), _vp]
@@ -203,6 +207,16 @@ def inspect(header: bytes) -> dict:
             "range_min": info.range_min, "range_max": info.range_max,
             "n_tiles": info.n_tiles, "nnz_blocks": info.nnz_blocks,
             "n_outliers": info.n_outliers, "stream_bytes": info.stream_bytes}
+
+
+def pwrel_bound(eps: float) -> float:
+    """Absolute bound on the log values that gives the point-wise relative
+    bound eps (Sec. 4.1's log-transformed particle data)."""
+    e = ctypes.c_double()
+    st = load_library().fz_pwrel_bound(float(eps), ctypes.byref(e))
+    if st != OK:
+        raise FZError(st, "fz_pwrel_bound")
+    return e.value
 
 
 def shard_extent(dims, ndim: int, n_shards: int, shard: int):
@@ -559,6 +573,33 @@ class Codec:
         if st != OK:
             raise FZError(st, "fz_range")
         return lo.value, hi.value, bool(bad.value)
+
+    def pwrel_forward(self, x, stream=None):
+        """(y, signs) for a float32 CUDA tensor x: y = log2|x| (-160 for
+        zeros), signs one int32 word per 32 elements (bit set: negative)."""
+        import torch
+        assert x.is_cuda and x.is_contiguous() and x.dtype == torch.float32
+        y = torch.empty_like(x)
+        signs = torch.empty((x.numel() + 31) // 32, dtype=torch.int32, device=x.device)
+        st = self._L.fz_pwrel_forward(self._ctx, _vp(x.data_ptr()), x.numel(),
+                                      _vp(y.data_ptr()), _vp(signs.data_ptr()),
+                                      self._stream(stream))
+        if st != OK:
+            raise FZError(st, "fz_pwrel_forward")
+        return y, signs
+
+    def pwrel_inverse(self, y, signs, stream=None):
+        """x' = +-2^y (0 below -154) for float32 CUDA y and the forward's signs."""
+        import torch
+        assert y.is_cuda and y.is_contiguous() and y.dtype == torch.float32
+        assert signs.is_cuda and signs.numel() >= (y.numel() + 31) // 32
+        x = torch.empty_like(y)
+        st = self._L.fz_pwrel_inverse(self._ctx, _vp(y.data_ptr()), y.numel(),
+                                      _vp(signs.data_ptr()), _vp(x.data_ptr()),
+                                      self._stream(stream))
+        if st != OK:
+            raise FZError(st, "fz_pwrel_inverse")
+        return x
 
     def compress_ranged_into(self, x, out, eb, range_min, range_max, ndim=None,
                              stream=None, raise_on_error=True):

@@ -467,6 +467,45 @@ int fz_range(fz_ctx *c, const float *d_in, uint64_t n, float *h_min, float *h_ma
   return FZ_OK;
 }
 
+// ---------------------------------------------------------------- pwrel
+int fz_pwrel_bound(double eps, double *eb_abs) {
+  if (!eb_abs || !(eps >= 1e-4 && eps <= 0.5)) return FZ_ERR_ARG;
+  *eb_abs = std::log2(1.0 + eps) - std::ldexp(1.0, -14);
+  return FZ_OK;
+}
+
+int fz_pwrel_forward(fz_ctx *c, const float *d_x, uint64_t n, float *d_y, uint32_t *d_signs,
+                     void *stream) {
+  if (!c || !d_x || !d_y || !d_signs || n == 0 || (reinterpret_cast<uintptr_t>(d_x) & 3u) ||
+      (reinterpret_cast<uintptr_t>(d_y) & 3u) || (reinterpret_cast<uintptr_t>(d_signs) & 3u))
+    return FZ_ERR_ARG;
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the range block's non-finite word serves as this call's flag
+  uint32_t *flag = &c->range->nonfinite;
+  if (cudaMemsetAsync(flag, 0, sizeof(uint32_t), s) != cudaSuccess ||
+      fz::launch_pwrel_forward(d_x, n, d_y, d_signs, flag, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->h_range, c->range, sizeof(RangeResult), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  return c->h_range->nonfinite ? FZ_ERR_NONFINITE : FZ_OK;
+}
+
+int fz_pwrel_inverse(fz_ctx *c, const float *d_y, uint64_t n, const uint32_t *d_signs,
+                     float *d_x, void *stream) {
+  if (!c || !d_y || !d_x || !d_signs || n == 0 || (reinterpret_cast<uintptr_t>(d_x) & 3u) ||
+      (reinterpret_cast<uintptr_t>(d_y) & 3u) || (reinterpret_cast<uintptr_t>(d_signs) & 3u))
+    return FZ_ERR_ARG;
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  return fz::launch_pwrel_inverse(d_y, n, d_signs, d_x, static_cast<cudaStream_t>(stream)) ==
+                 cudaSuccess
+             ? FZ_OK
+             : FZ_ERR_CUDA;
+}
+
 // scratch of the unfused path for n_tiles tiles: codes, shuffled words,
 // counts, prefixes and the scan's status words
 static int ensure_staged(fz_ctx *c, uint64_t n_tiles, fz::StagedScratch *w) {

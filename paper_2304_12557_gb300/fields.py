@@ -15,6 +15,9 @@ the same shapes and a comparable smoothness:
   std, field = exp(0.5 g) (seed 3; a lognormal density like Nyx's baryon
   density)
 * ``grf`` -- any shape and spectral slope, used for ragged and batched cases
+* ``particles1d`` -- particle velocities in particle order (seed 5; stands
+  in for HACC's 1-D velocity arrays, which the paper compresses
+  log-transformed with a point-wise relative bound)
 
 Arrays are returned in numpy C order indexed [z, y, x] (x fastest), i.e. the
 layout the C ABI expects with dims given fastest-first.
@@ -139,6 +142,28 @@ def batch_shapes(count: int = 256, seed: int = 4, lo: int = 64 << 10,
         eb = float(rng.choice([1e-2, 1e-3, 1e-4]))
         out.append((shape, ndim, beta, eb))
     return out
+
+
+def particles1d(n: int = 1 << 24, seed: int = 5, zero_frac: float = 1e-4) -> np.ndarray:
+    """Particle velocities, float32, in particle order: groups of particles
+    (halos of 64 to 4096 members) share a bulk velocity, members scatter
+    around it (normal, 20% of the bulk spread); signs mix; a fraction of
+    exact zeros.  Neighbouring values are related as in a sorted particle
+    file, and magnitudes span several decades."""
+    rng = np.random.default_rng(seed)
+    sizes = []
+    tot = 0
+    while tot < n:
+        s = int(rng.integers(64, 4097))
+        sizes.append(s)
+        tot += s
+    sizes = np.asarray(sizes)
+    bulk = rng.normal(0.0, 300.0, sizes.size)
+    v = np.repeat(bulk, sizes)[:n] + rng.normal(0.0, 60.0, n)
+    v = v.astype(np.float32)
+    z = rng.random(n) < zero_frac
+    v[z] = 0.0
+    return v
 
 
 def small_cases():
