@@ -73,40 +73,71 @@ __device__ __forceinline__ float pw_exp2(float y) {
                    1.17549435e-38f);
 }
 
+// Each warp takes chunks of kPwU consecutive 32-element words (one word per
+// load, kPwU independent evaluations in flight per thread); chunk c covers
+// elements [32 kPwU c, 32 kPwU (c + 1)) and sign words [kPwU c, kPwU (c + 1)).
+constexpr int kPwU = 4;
+
 __global__ void pwrel_forward_kernel(const float *__restrict__ x, uint64_t n,
                                      float *__restrict__ y, uint32_t *__restrict__ signs,
                                      uint32_t *flag) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const unsigned full = 0xffffffffu;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   bool bad = false;
-  // whole warps walk whole 32-element words, so that the ballot is a word
-  for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u);
-       i0 < n; i0 += stride) {
-    const uint64_t i = i0 + (threadIdx.x & 31u);
-    const float v = i < n ? x[i] : 1.0f;
-    const uint32_t bits = __float_as_uint(v);
-    const bool finite = (bits & 0x7F800000u) != 0x7F800000u;
-    bad |= !finite;
-    const float a = fabsf(v);
-    const uint32_t neg = __ballot_sync(0xffffffffu, (bits >> 31) != 0u);
-    if (i < n) y[i] = (a == 0.0f || !finite) ? kPwZeroLog : pw_log2(a);
-    if ((threadIdx.x & 31u) == 0) signs[i0 >> 5] = neg;
+  for (uint64_t ch = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+       ch * 32 * kPwU < n; ch += warps) {
+    const uint64_t base = ch * 32 * kPwU;
+    float v[kPwU];
+#pragma unroll
+    for (int u = 0; u < kPwU; ++u) {
+      const uint64_t i = base + 32 * u + lane;
+      v[u] = i < n ? x[i] : 1.0f;
+    }
+    uint32_t word = 0;                       // lane u keeps sign word u
+#pragma unroll
+    for (int u = 0; u < kPwU; ++u) {
+      const uint64_t i = base + 32 * u + lane;
+      const uint32_t bits = __float_as_uint(v[u]);
+      const bool finite = (bits & 0x7F800000u) != 0x7F800000u;
+      bad |= !finite;
+      const float a = fabsf(v[u]);
+      const uint32_t neg = __ballot_sync(full, (bits >> 31) != 0u);
+      if (lane == (uint32_t)u) word = neg;
+      if (i < n) y[i] = (a == 0.0f || !finite) ? kPwZeroLog : pw_log2(a);
+    }
+    if (lane < (uint32_t)kPwU && base + 32 * lane < n) signs[ch * kPwU + lane] = word;
   }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31u) == 0) atomicOr(flag, 1u);
+  if (__any_sync(full, bad) && lane == 0) atomicOr(flag, 1u);
 }
 
 __global__ void pwrel_inverse_kernel(const float *__restrict__ y, uint64_t n,
                                      const uint32_t *__restrict__ signs, float *__restrict__ x) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const float v = y[i];
-    const float a = v < kPwZeroCut ? 0.0f : pw_exp2(v);
-    const bool neg = (signs[i >> 5] >> (i & 31u)) & 1u;
-    x[i] = neg ? -a : a;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t ch = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+       ch * 32 * kPwU < n; ch += warps) {
+    const uint64_t base = ch * 32 * kPwU;
+    float v[kPwU];
+    uint32_t w[kPwU];
+#pragma unroll
+    for (int u = 0; u < kPwU; ++u) {
+      const uint64_t i = base + 32 * u + lane;
+      const bool in = i < n;
+      v[u] = in ? y[i] : 0.0f;
+      w[u] = in ? signs[ch * kPwU + u] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kPwU; ++u) {
+      const uint64_t i = base + 32 * u + lane;
+      const float a = v[u] < kPwZeroCut ? 0.0f : pw_exp2(v[u]);
+      if (i < n) x[i] = ((w[u] >> lane) & 1u) ? -a : a;
+    }
   }
 }
 
 static int grid_for(uint64_t n) {
-  const uint64_t blocks = (n + 255) / 256;
+  const uint64_t blocks = (n + 256 * kPwU - 1) / (256 * kPwU);
   return (int)(blocks < 152ull * 8 ? (blocks ? blocks : 1) : 152ull * 8);
 }
 
