@@ -299,6 +299,22 @@ def run_ours(args, rank, world, local_rank, dist):
                             "frac": v[1] / (v[0] / 1e3) / 1e9 / peak,
                             "traffic": traffic_bytes(k, args.size)}
                         for k, v in kern.items()}}
+    # The two directions as kernel sequences: relative-bound compression is
+    # the range pass plus the compressor, whose algorithmic bytes are two
+    # reads of the input and the stream (8 + 4/CR bytes per element);
+    # decompression is the offsets pass plus the decompressor (4/CR + 4).
+    rel_ms = mean(k_range) + mean(k_comp)
+    dec_path_ms = mean(k_doff) + mean(k_dec)
+    roof["paths"] = {
+        "compress_rel (range_kernel + compress_kernel)": {
+            "ms": rel_ms, "bytes": 2 * field_bytes + size,
+            "GB/s": (2 * field_bytes + size) / (rel_ms / 1e3) / 1e9,
+            "frac": (2 * field_bytes + size) / (rel_ms / 1e3) / 1e9 / peak},
+        "decompress (dec_offsets_kernel + decompress_kernel)": {
+            "ms": dec_path_ms, "bytes": size + field_bytes,
+            "GB/s": (size + field_bytes) / (dec_path_ms / 1e3) / 1e9,
+            "frac": (size + field_bytes) / (dec_path_ms / 1e3) / 1e9 / peak},
+    }
 
     # the same compression as the paper's separate kernels (codes and
     # shuffled words through HBM): what fusing them saves on this GPU
