@@ -11,6 +11,7 @@
 #include "fz.h"
 #include "fz_device.cuh"
 #include "fz_kernels.h"
+#include "fz_pwrel.h"
 
 using fz::RangeResult;
 using fz::SetScratch;

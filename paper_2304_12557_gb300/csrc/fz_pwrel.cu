@@ -23,7 +23,7 @@
 #include <cstdint>
 
 #include "fz_device.cuh"
-#include "fz_kernels.h"
+#include "fz_pwrel.h"
 
 namespace fz {
 
