@@ -130,6 +130,43 @@ def test_cosmo3d_512(codec, torch, cosmo512, eb):
 
 
 # ------------------------------------------------------------ edge cases
+def _tile_kinds(stream: bytes):
+    """(narrow, wide, narrow with escapes) tile counts of a stream, from its
+    flag bytes: a tile is narrow when the planes of magnitude bits 7..14
+    (flag bytes 7..14 and 23..30 of its 32) are all absent.  A narrow tile
+    whose stream has outliers in it holds sign-only escape codes; counted
+    here from the outlier records' code indices."""
+    nt = fz.inspect(stream[:64])["n_tiles"]
+    info = fz.inspect(stream[:64])
+    f = np.frombuffer(stream, np.uint8, 32 * nt, 64).reshape(nt, 32)
+    narrow = (np.concatenate([f[:, 7:15], f[:, 23:31]], axis=1) == 0).all(axis=1)
+    recs = np.frombuffer(stream, np.uint32, 2 * info["n_outliers"],
+                         len(stream) - 8 * info["n_outliers"]).reshape(-1, 2)
+    esc_tiles = np.unique(recs[:, 0] // 2048)
+    return (int(narrow.sum()), int((~narrow).sum()),
+            int(narrow[esc_tiles[esc_tiles < nt]].sum()))
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_narrow_and_wide_tiles_mix(codec, torch, ndim):
+    """Smooth regions (codes within 7 bits: the 16-plane transposes) beside
+    noisy ones (wider codes: the 32-plane transposes) and isolated spikes
+    (escapes: a narrow-by-flags tile holding sign-only escape codes, which
+    the decompressor's narrow path must patch)."""
+    rng = np.random.default_rng(40 + ndim)
+    shape = {1: (3 * 8192 + 77,), 2: (2 * 128 + 9, 3 * 64 + 5), 3: (3 * 8 + 3, 2 * 32 + 7, 3 * 32 + 1)}[ndim]
+    x = fields.grf(shape, -3.0, 50 + ndim).astype(np.float32)
+    flat = x.reshape(-1)
+    half = flat.size // 2
+    flat[half:] += rng.normal(0, 2.0, flat.size - half).astype(np.float32)    # noisy half
+    spikes = rng.choice(half, 6, replace=False)
+    flat[spikes] = 5000.0                                                  # escapes in the smooth half
+    g, _ = check_parity(codec, torch, x, ndim, fz.EB_ABS, 1e-2)
+    n_narrow, n_wide, n_narrow_esc = _tile_kinds(g)
+    assert n_narrow > 0 and n_wide > 0 and n_narrow_esc > 0, (n_narrow, n_wide, n_narrow_esc)
+    assert fz.inspect(g[:64])["n_outliers"] > 0
+
+
 def test_all_zero_and_constant(codec, torch):
     check_parity(codec, torch, np.zeros((40, 70, 33), np.float32), 3, fz.EB_ABS, 0.1)
     check_parity(codec, torch, np.full((40, 70, 33), 7.25, np.float32), 3, fz.EB_REL, 1e-3)
