@@ -109,7 +109,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -248,8 +248,17 @@ def run_ours(args, rank, world, local_rank, dist):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    # the sampler runs through 0.3 s of untimed steps right before the timed
+    # region and through the region itself, so that its samples see the GPU
+    # under this load
     sampler.start()
-    time.sleep(0.3)
+    t_load = time.time()
+    while time.time() - t_load < 0.3:
+        step(None)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     recs = []
@@ -454,8 +463,11 @@ def run_batch(args, rank, world, local_rank):
         assert torch.equal(single, outs[i][: sizes[i]]), i
     sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ
                            else int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank]))
-    sampler.start()
-    time.sleep(0.3)
+    sampler.start()                      # samples under load: untimed runs first
+    t_load = time.time()
+    while time.time() - t_load < 0.3:
+        batch.compress()
+    torch.cuda.synchronize()
     ev = []
     for _ in range(args.steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
