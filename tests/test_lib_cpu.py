@@ -160,3 +160,69 @@ int main() {
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
     bad, checked = (int(v) for v in out.split())
     assert checked > 4_000_000 and bad == 0
+
+
+def test_narrow_transpose_host_build():
+    """The narrow tiles' transpose (16 byte-code words, 16-word transpose),
+    compiled as host code, against the 32x32 transpose: for code pairs whose
+    magnitudes fit in 7 bits, word k is row narrow_row(k) of transpose32 and
+    the other 16 rows are zero -- the identity both kernels rely on."""
+    src = r'''
+#include <cstdio>
+#include <cstdint>
+#include "fz_device.cuh"
+int main() {
+  uint64_t s = 0x9E3779B97F4A7C15ull, bad = 0, cases = 0;
+  for (int rep = 0; rep < 100000; ++rep) {
+    const int m = rep % 8;                       // magnitude bits of this case
+    uint32_t w[32];
+    for (int i = 0; i < 32; ++i) {
+      uint32_t c[2];
+      for (int h = 0; h < 2; ++h) {
+        s ^= s << 13; s ^= s >> 7; s ^= s << 17;
+        uint32_t mag = m ? (uint32_t)(s & ((1u << m) - 1u)) : 0u;
+        uint32_t sgn = ((s >> 20) & 1u) ? 0x8000u : 0u;   // includes sign-only (escape) codes
+        if (((s >> 24) & 3u) == 0) { mag = 0; sgn = 0; }
+        c[h] = mag | sgn;
+      }
+      w[i] = c[0] | c[1] << 16;
+    }
+    uint32_t a[32];
+    for (int i = 0; i < 32; ++i) a[i] = w[i];
+    fz::transpose32(a);
+    uint32_t u[16];
+    fz::squeeze_narrow(w, u);
+    fz::transpose16(u);
+    bool live[32] = {};
+    for (int k = 0; k < 16; ++k) {
+      live[fz::narrow_row(k)] = true;
+      bad += u[k] != a[fz::narrow_row(k)];
+    }
+    for (int b = 0; b < 32; ++b) bad += !live[b] && a[b] != 0u;
+    ++cases;
+  }
+  printf("%llu %llu\n", (unsigned long long)bad, (unsigned long long)cases);
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        cpp = os.path.join(d, "t.cu")
+        exe = os.path.join(d, "t")
+        open(cpp, "w").write(src)
+        inc = os.path.join(ROOT, "paper_2304_12557_gb300", "csrc")
+        subprocess.run(["nvcc", "-std=c++17", "-I", inc, "-o", exe, cpp],
+                       check=True, capture_output=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    bad, cases = (int(t) for t in out.split())
+    assert cases == 100000 and bad == 0
+
+
+def test_pwrel_bound_through_the_library(lib):
+    """The library's bound for the log transform equals the oracle's
+    formula, and the domain is enforced (host-only call, no GPU)."""
+    import math
+    assert fz.pwrel_bound(1e-3) == math.log2(1.001) - 2.0 ** -14
+    for eps in (9e-5, 0.6, float("nan")):
+        with pytest.raises(fz.FZError) as e:
+            fz.pwrel_bound(eps)
+        assert e.value.status == fz.ERR_ARG
