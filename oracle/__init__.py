@@ -101,6 +101,13 @@ def lib() -> ctypes.CDLL:
             L.fzo_reconstruct_closed_form.argtypes = [_f32p, ctypes.c_uint64,
                                                       ctypes.c_float,
                                                       ctypes.c_float, _f32p]
+            L.fzo_lorenzo_whole.argtypes = [_i32p, _u32p, ctypes.c_int, _i32p]
+            L.fzo_lorenzo_whole.restype = None
+            L.fzo_lorenzo_whole_inverse.argtypes = [_i32p, _u32p, ctypes.c_int, _i64p]
+            L.fzo_lorenzo_whole_inverse.restype = None
+            L.fzo_compress_whole.argtypes = [_f32p, _u32p, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, _u8p, ctypes.c_uint64,
+                                             ctypes.POINTER(ctypes.c_uint64)]
             L.fzo_pwrel_bound.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
             L.fzo_pw_log2.argtypes = [ctypes.c_float]
             L.fzo_pw_log2.restype = ctypes.c_float
@@ -161,6 +168,24 @@ def lorenzo_inverse(delta: np.ndarray, ndim: int) -> np.ndarray:
     return out
 
 
+def lorenzo_whole(q: np.ndarray, ndim: int) -> np.ndarray:
+    """Whole-field Lorenzo residuals (zero only outside the field)."""
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    dims = _dims3(q.shape[::-1])
+    out = np.empty_like(q)
+    lib().fzo_lorenzo_whole(_ptr(q, _i32p), _ptr(dims, _u32p), ndim, _ptr(out, _i32p))
+    return out
+
+
+def lorenzo_whole_inverse(delta: np.ndarray, ndim: int) -> np.ndarray:
+    delta = np.ascontiguousarray(delta, dtype=np.int32)
+    dims = _dims3(delta.shape[::-1])
+    out = np.empty(delta.shape, np.int64)
+    lib().fzo_lorenzo_whole_inverse(_ptr(delta, _i32p), _ptr(dims, _u32p), ndim,
+                                    _ptr(out, _i64p))
+    return out
+
+
 def encode(d: int) -> int:
     return int(lib().fzo_encode(d))
 
@@ -210,21 +235,22 @@ def compress_bound(ndim: int, dims) -> int:
     return int(lib().fzo_compress_bound(ndim, _ptr(d, _u32p)))
 
 
-def compress(x: np.ndarray, ndim: int, mode: int, eb: float):
-    """x indexed [z, y, x] (x fastest).  Returns (status, bytes)."""
+def compress(x: np.ndarray, ndim: int, mode: int, eb: float, whole: bool = False):
+    """x indexed [z, y, x] (x fastest).  Returns (status, bytes).  whole:
+    the whole-field Lorenzo variant (stream version 2)."""
+    fn = lib().fzo_compress_whole if whole else lib().fzo_compress
     x = np.ascontiguousarray(x, dtype=np.float32)
     dims = _dims3(x.shape[::-1][:ndim])
     cap = compress_bound(ndim, dims)
     cap = min(cap, 64 + 32 * num_tiles(ndim, dims) * 129 + 8 * x.size)
     out = np.empty(cap, np.uint8)
     size = ctypes.c_uint64()
-    st = lib().fzo_compress(_ptr(x, _f32p), _ptr(dims, _u32p), ndim, mode, eb,
-                            _ptr(out, _u8p), cap, ctypes.byref(size))
+    st = fn(_ptr(x, _f32p), _ptr(dims, _u32p), ndim, mode, eb,
+            _ptr(out, _u8p), cap, ctypes.byref(size))
     if st == ERR_CAPACITY:
         out = np.empty(size.value, np.uint8)
-        st = lib().fzo_compress(_ptr(x, _f32p), _ptr(dims, _u32p), ndim, mode,
-                                eb, _ptr(out, _u8p), size.value,
-                                ctypes.byref(size))
+        st = fn(_ptr(x, _f32p), _ptr(dims, _u32p), ndim, mode,
+                eb, _ptr(out, _u8p), size.value, ctypes.byref(size))
     if st != OK:
         return st, b""
     return st, out[: size.value].tobytes()

@@ -143,6 +143,15 @@ static void chunk_origin(int ndim, uint64_t x, uint64_t y, uint64_t z,
   o[2] = z / ch[2] * ch[2];
 }
 
+/* the origin neighbours are cut off at: the chunk's, or for the
+ * whole-field variant the field's (every neighbour inside the field counts;
+ * the paper's chunks trade this for independence, Sec. 2.3) */
+static void pred_origin(int ndim, int whole, uint64_t x, uint64_t y, uint64_t z,
+                        uint64_t o[3]) {
+  if (whole) { o[0] = o[1] = o[2] = 0; return; }
+  chunk_origin(ndim, x, y, z, o);
+}
+
 /* the 1-, 2- and 3-D Lorenzo predictions (neighbours at lower indices) */
 static int64_t lorenzo_pred(const int32_t *q, const uint64_t d[3],
                             const uint64_t o[3], int ndim, int64_t x,
@@ -157,20 +166,30 @@ static int64_t lorenzo_pred(const int32_t *q, const uint64_t d[3],
          qt(q, d, o, x - 1, y - 1, z - 1);
 }
 
-void fzo_lorenzo(const int32_t *q, const uint32_t dims[3], int ndim,
-                 int32_t *delta) {
+static void lorenzo_mode(const int32_t *q, const uint32_t dims[3], int ndim,
+                         int whole, int32_t *delta) {
   uint64_t d[3];
   norm_dims(ndim, dims, d);
   for (uint64_t z = 0; z < d[2]; z++)
     for (uint64_t y = 0; y < d[1]; y++)
       for (uint64_t x = 0; x < d[0]; x++) {
         uint64_t o[3];
-        chunk_origin(ndim, x, y, z, o);
+        pred_origin(ndim, whole, x, y, z, o);
         uint64_t i = x + d[0] * (y + d[1] * z);
         int64_t pred = lorenzo_pred(q, d, o, ndim, (int64_t)x, (int64_t)y,
                                     (int64_t)z);
         delta[i] = (int32_t)((int64_t)q[i] - pred);
       }
+}
+
+void fzo_lorenzo(const int32_t *q, const uint32_t dims[3], int ndim,
+                 int32_t *delta) {
+  lorenzo_mode(q, dims, ndim, 0, delta);
+}
+
+void fzo_lorenzo_whole(const int32_t *q, const uint32_t dims[3], int ndim,
+                       int32_t *delta) {
+  lorenzo_mode(q, dims, ndim, 1, delta);
 }
 
 /* Sec. 4.4 (decompression mirrors compression): rebuild q point by point
@@ -183,15 +202,15 @@ static int64_t qt64(const int64_t *q, const uint64_t d[3], const uint64_t o[3],
   return q[(uint64_t)x + d[0] * ((uint64_t)y + d[1] * (uint64_t)z)];
 }
 
-void fzo_lorenzo_inverse(const int32_t *delta, const uint32_t dims[3],
-                         int ndim, int64_t *q) {
+static void lorenzo_inverse_mode(const int32_t *delta, const uint32_t dims[3],
+                                 int ndim, int whole, int64_t *q) {
   uint64_t d[3];
   norm_dims(ndim, dims, d);
   for (uint64_t z = 0; z < d[2]; z++)
     for (uint64_t y = 0; y < d[1]; y++)
       for (uint64_t x = 0; x < d[0]; x++) {
         uint64_t o[3];
-        chunk_origin(ndim, x, y, z, o);
+        pred_origin(ndim, whole, x, y, z, o);
         int64_t X = (int64_t)x, Y = (int64_t)y, Z = (int64_t)z;
         int64_t pred;
         if (ndim == 1)
@@ -208,6 +227,16 @@ void fzo_lorenzo_inverse(const int32_t *delta, const uint32_t dims[3],
         uint64_t i = x + d[0] * (y + d[1] * z);
         q[i] = (int64_t)delta[i] + pred;
       }
+}
+
+void fzo_lorenzo_inverse(const int32_t *delta, const uint32_t dims[3],
+                         int ndim, int64_t *q) {
+  lorenzo_inverse_mode(delta, dims, ndim, 0, q);
+}
+
+void fzo_lorenzo_whole_inverse(const int32_t *delta, const uint32_t dims[3],
+                               int ndim, int64_t *q) {
+  lorenzo_inverse_mode(delta, dims, ndim, 1, q);
 }
 
 /* ------------------------------------------------------------------ */
@@ -298,7 +327,8 @@ void fzo_block_flags(const uint32_t out[1024], uint32_t flags[8]) {
 
 /* ------------------------------------------------------------------ */
 /* stream layout (little-endian)                                        */
-/*   0  "FZG1"            4 version=1   5 ndim   6 eb mode   7 reserved  */
+/*   0  "FZG1"            4 version     5 ndim   6 eb mode   7 reserved  */
+/*      (version 1: chunk-local Lorenzo; 2: whole-field Lorenzo)         */
 /*   8  u32 dims[3]      20 u32 n_tiles 24 f64 eb as requested           */
 /*  32  f32 eb (abs)     36 f32 2eb     40 f32 1/(2eb)                   */
 /*  44  u32 nnz blocks   48 u32 n outliers                               */
@@ -324,12 +354,19 @@ static int check_dims(int ndim, const uint32_t dims[3]) {
 /* Shared by fzo_compress and fzo_compress_ranged: rng == NULL takes the
  * relative bound's value range from x itself. */
 static int compress_common(const float *x, const uint32_t dims[3], int ndim,
-                           int mode, double eb, const float *rng,
+                           int mode, double eb, const float *rng, int whole,
                            uint8_t *out, uint64_t cap, uint64_t *out_size);
 
 int fzo_compress(const float *x, const uint32_t dims[3], int ndim, int mode,
                  double eb, uint8_t *out, uint64_t cap, uint64_t *out_size) {
-  return compress_common(x, dims, ndim, mode, eb, NULL, out, cap, out_size);
+  return compress_common(x, dims, ndim, mode, eb, NULL, 0, out, cap, out_size);
+}
+
+/* The whole-field Lorenzo variant: the same stream with version 2, whose
+ * residuals take every neighbour inside the field (no chunk cut-offs). */
+int fzo_compress_whole(const float *x, const uint32_t dims[3], int ndim, int mode,
+                       double eb, uint8_t *out, uint64_t cap, uint64_t *out_size) {
+  return compress_common(x, dims, ndim, mode, eb, NULL, 1, out, cap, out_size);
 }
 
 /* Sec. 4.1's value-range-relative bound with the range supplied by the
@@ -343,11 +380,11 @@ int fzo_compress_ranged(const float *x, const uint32_t dims[3], int ndim,
     *out_size = 0;
     return FZO_ERR_ARG;
   }
-  return compress_common(x, dims, ndim, FZO_EB_REL, eb, rng, out, cap, out_size);
+  return compress_common(x, dims, ndim, FZO_EB_REL, eb, rng, 0, out, cap, out_size);
 }
 
 static int compress_common(const float *x, const uint32_t dims[3], int ndim,
-                           int mode, double eb, const float *rng,
+                           int mode, double eb, const float *rng, int whole,
                            uint8_t *out, uint64_t cap, uint64_t *out_size) {
   *out_size = 0;
   if (!x || !out || !check_dims(ndim, dims)) return FZO_ERR_ARG;
@@ -392,7 +429,7 @@ static int compress_common(const float *x, const uint32_t dims[3], int ndim,
     }
 
   /* step 2: chunk-local Lorenzo residuals */
-  fzo_lorenzo(q, dims, ndim, delta);
+  lorenzo_mode(q, dims, ndim, whole, delta);
   free(q);
 
   /* step 3: codes in stream order, outliers, words, bitshuffle, flags */
@@ -450,7 +487,7 @@ static int compress_common(const float *x, const uint32_t dims[3], int ndim,
   }
   memset(out, 0, FZO_HEADER_BYTES);
   out[0] = 'F'; out[1] = 'Z'; out[2] = 'G'; out[3] = '1';
-  out[4] = 1; out[5] = (uint8_t)ndim; out[6] = (uint8_t)mode; out[7] = 0;
+  out[4] = whole ? 2 : 1; out[5] = (uint8_t)ndim; out[6] = (uint8_t)mode; out[7] = 0;
   put_u32(out + 8, (uint32_t)d[0]);
   put_u32(out + 12, (uint32_t)d[1]);
   put_u32(out + 16, (uint32_t)d[2]);
@@ -492,8 +529,9 @@ int fzo_decompress(const uint8_t *in, uint64_t in_size, float *x,
   if (!in || !x) return FZO_ERR_ARG;
   if (in_size < FZO_HEADER_BYTES) return FZO_ERR_CORRUPT;
   if (in[0] != 'F' || in[1] != 'Z' || in[2] != 'G' || in[3] != '1' ||
-      in[4] != 1 || in[7] != 0)
+      (in[4] != 1 && in[4] != 2) || in[7] != 0)
     return FZO_ERR_CORRUPT;
+  const int whole = in[4] == 2;
   int ndim = in[5], mode = in[6];
   uint32_t dims[3] = {get_u32(in + 8), get_u32(in + 12), get_u32(in + 16)};
   if (ndim < 1 || ndim > 3 || mode > 1) return FZO_ERR_CORRUPT;
@@ -569,7 +607,7 @@ int fzo_decompress(const uint8_t *in, uint64_t in_size, float *x,
   if (!bad && oi != n_out) bad = 1;
   if (bad) { free(delta); free(q); return FZO_ERR_CORRUPT; }
 
-  fzo_lorenzo_inverse(delta, dims, ndim, q);
+  lorenzo_inverse_mode(delta, dims, ndim, whole, q);
   for (uint64_t i = 0; i < n; i++) {
     volatile float qf = (float)q[i];
     x[i] = qf * ebx2;

@@ -114,6 +114,20 @@ int fzo_decompress(const uint8_t *in, uint64_t in_size, float *x,
 int fzo_reconstruct_closed_form(const float *x, uint64_t n, float ebx2_r,
                                 float ebx2, float *xr);
 
+/* --- the whole-field Lorenzo variant ----------------------------------
+ * The paper's chunks make every chunk independent (Sec. 2.3) at the price
+ * of a residual spike at each chunk's lower faces.  The variant takes every
+ * neighbour inside the field instead (zero only outside the field).  Its
+ * stream is the same apart from the version byte (2), which the
+ * decompressor reads to choose the inverse.  Only the oracle has it; the
+ * GPU library rejects version-2 streams. */
+void fzo_lorenzo_whole(const int32_t *q, const uint32_t dims[3], int ndim,
+                       int32_t *delta);
+void fzo_lorenzo_whole_inverse(const int32_t *delta, const uint32_t dims[3],
+                               int ndim, int64_t *q);
+int fzo_compress_whole(const float *x, const uint32_t dims[3], int ndim, int mode,
+                       double eb, uint8_t *out, uint64_t cap, uint64_t *out_size);
+
 /* --- point-wise relative bounds by log transform ---------------------
  * Sec. 4.1 compresses the particle dataset log-transformed, with the
  * absolute bound a point-wise relative bound implies.  The transform is
