@@ -51,8 +51,8 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.run(
-            ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-             "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC, "-lm"],
+            ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+             "-fPIC", "-shared", "-Wall", "-pthread", "-o", tmp, _SRC, "-lm"],
             check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -116,6 +116,9 @@ def lib() -> ctypes.CDLL:
             L.fzo_pwrel_forward.argtypes = [_f32p, ctypes.c_uint64, _f32p, _u32p]
             L.fzo_pwrel_inverse.argtypes = [_f32p, ctypes.c_uint64, _u32p, _f32p]
             L.fzo_pwrel_inverse.restype = None
+            L.fzo_threads.argtypes = []
+            L.fzo_compress_mt.argtypes = L.fzo_compress.argtypes
+            L.fzo_decompress_mt.argtypes = L.fzo_decompress.argtypes
             _lib = L
     return _lib
 
@@ -235,10 +238,19 @@ def compress_bound(ndim: int, dims) -> int:
     return int(lib().fzo_compress_bound(ndim, _ptr(d, _u32p)))
 
 
-def compress(x: np.ndarray, ndim: int, mode: int, eb: float, whole: bool = False):
+def threads() -> int:
+    """Threads the all-cores calls use (one per online host core)."""
+    return int(lib().fzo_threads())
+
+
+def compress(x: np.ndarray, ndim: int, mode: int, eb: float, whole: bool = False,
+             all_cores: bool = False):
     """x indexed [z, y, x] (x fastest).  Returns (status, bytes).  whole:
-    the whole-field Lorenzo variant (stream version 2)."""
-    fn = lib().fzo_compress_whole if whole else lib().fzo_compress
+    the whole-field Lorenzo variant (stream version 2).  all_cores: the
+    same stream computed over all host cores (Sec. 4.4's FZ-OMP)."""
+    assert not (whole and all_cores)
+    fn = (lib().fzo_compress_whole if whole else
+          lib().fzo_compress_mt if all_cores else lib().fzo_compress)
     x = np.ascontiguousarray(x, dtype=np.float32)
     dims = _dims3(x.shape[::-1][:ndim])
     cap = compress_bound(ndim, dims)
@@ -279,8 +291,9 @@ def compress_ranged(x: np.ndarray, ndim: int, eb: float, range_min: float,
     return st, out[: size.value].tobytes()
 
 
-def decompress(stream: bytes, n_elems: int | None = None):
-    """Returns (status, float32 array of the field's element count)."""
+def decompress(stream: bytes, n_elems: int | None = None, all_cores: bool = False):
+    """Returns (status, float32 array of the field's element count).
+    all_cores: the same reconstruction over all host cores."""
     buf = np.frombuffer(stream, dtype=np.uint8).copy()
     if n_elems is None:
         if len(stream) < 20:
@@ -288,8 +301,8 @@ def decompress(stream: bytes, n_elems: int | None = None):
         d = np.frombuffer(stream[8:20], dtype="<u4").astype(np.int64)
         n_elems = int(max(1, d[0]) * max(1, d[1]) * max(1, d[2]))
     out = np.empty(max(n_elems, 1), np.float32)
-    st = lib().fzo_decompress(_ptr(buf, _u8p), len(stream), _ptr(out, _f32p),
-                              n_elems)
+    fn = lib().fzo_decompress_mt if all_cores else lib().fzo_decompress
+    st = fn(_ptr(buf, _u8p), len(stream), _ptr(out, _f32p), n_elems)
     return st, (out[:n_elems] if st == OK else None)
 
 

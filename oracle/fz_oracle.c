@@ -713,3 +713,428 @@ void fzo_pwrel_inverse(const float *y, uint64_t n, const uint32_t *signs, float 
     x[i] = ((signs[i / 32] >> (i % 32)) & 1u) ? -a : a;
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* All host cores (the paper's multi-threaded CPU version, FZ-OMP, Sec.   */
+/* 4.4): the same steps as compress_common and fzo_decompress, with the   */
+/* loops whose iterations are independent (points, tiles, chunks) split   */
+/* into contiguous ranges over POSIX threads, and the compaction (prefix  */
+/* sum and copy) serial.  Every value is computed by the same per-point   */
+/* and per-tile functions, so the stream and the reconstruction are       */
+/* identical to the one-thread calls.  Chunk-local (version 1) streams.   */
+/* ------------------------------------------------------------------ */
+#include <pthread.h>
+#include <unistd.h>
+
+#define MT_MAX_THREADS 256
+
+int fzo_threads(void) {
+  long n = sysconf(_SC_NPROCESSORS_ONLN);
+  if (n < 1) n = 1;
+  if (n > MT_MAX_THREADS) n = MT_MAX_THREADS;
+  return (int)n;
+}
+
+typedef void (*mt_body)(void *ctx, int64_t lo, int64_t hi, int part);
+typedef struct { mt_body fn; void *ctx; int64_t lo, hi; int part; } mt_job;
+
+static void *mt_run(void *p) {
+  mt_job *j = (mt_job *)p;
+  j->fn(j->ctx, j->lo, j->hi, j->part);
+  return NULL;
+}
+
+/* fn over [0, n) in `parts` contiguous ranges, one per thread (the calling
+ * thread takes the first); parts <= MT_MAX_THREADS */
+static void mt_for(int64_t n, int parts, mt_body fn, void *ctx) {
+  mt_job jobs[MT_MAX_THREADS];
+  pthread_t th[MT_MAX_THREADS];
+  int started[MT_MAX_THREADS];
+  for (int k = 0; k < parts; k++) {
+    jobs[k].fn = fn; jobs[k].ctx = ctx; jobs[k].part = k;
+    jobs[k].lo = n * k / parts; jobs[k].hi = n * (k + 1) / parts;
+    started[k] = 0;
+  }
+  for (int k = 1; k < parts; k++)
+    started[k] = pthread_create(&th[k], NULL, mt_run, &jobs[k]) == 0;
+  mt_run(&jobs[0]);
+  for (int k = 1; k < parts; k++) {
+    if (started[k]) pthread_join(th[k], NULL);
+    else mt_run(&jobs[k]);                /* no thread: run it here */
+  }
+}
+
+/* codes of tile t (stream order) from the residual field; returns the
+ * number of escapes */
+static uint32_t tile_codes(const int32_t *delta, const uint32_t dims[3], int ndim,
+                           const uint64_t d[3], uint64_t t, uint16_t codes[FZO_TILE_CODES]) {
+  uint32_t n_out = 0;
+  for (uint32_t p = 0; p < FZO_TILE_CODES; p++) {
+    uint32_t c[3];
+    codes[p] = 0;
+    if (!fzo_tile_coord(ndim, dims, t, p, c)) continue;
+    codes[p] = fzo_encode(delta[c[0] + d[0] * (c[1] + d[1] * (uint64_t)c[2])]);
+    n_out += codes[p] == 0x8000;
+  }
+  return n_out;
+}
+
+typedef struct {
+  const float *x;
+  int32_t *q, *delta;
+  const uint32_t *dims;
+  const uint64_t *d;
+  int ndim;
+  float ebx2_r;
+  uint32_t *shuf, *flags;
+  uint64_t *tile_out;
+  uint8_t *po;
+  int bad[MT_MAX_THREADS];
+  float lo[MT_MAX_THREADS], hi[MT_MAX_THREADS];
+} mt_comp;
+
+static void mt_finite(void *c, int64_t lo, int64_t hi, int k) {
+  mt_comp *m = (mt_comp *)c;
+  int bad = 0;
+  for (int64_t i = lo; i < hi; i++) bad |= !isfinite(m->x[i]);
+  m->bad[k] = bad;
+}
+static void mt_minmax(void *c, int64_t lo, int64_t hi, int k) {
+  mt_comp *m = (mt_comp *)c;
+  float a = m->x[lo < hi ? lo : 0], b = a;
+  for (int64_t i = lo; i < hi; i++) {
+    if (m->x[i] < a) a = m->x[i];
+    if (m->x[i] > b) b = m->x[i];
+  }
+  m->lo[k] = a;
+  m->hi[k] = b;
+}
+static void mt_prequant(void *c, int64_t lo, int64_t hi, int k) {
+  mt_comp *m = (mt_comp *)c;
+  int bad = 0;
+  for (int64_t i = lo; i < hi; i++) bad |= fzo_prequant1(m->x[i], m->ebx2_r, &m->q[i]) != FZO_OK;
+  m->bad[k] = bad;
+}
+static void mt_lorenzo(void *c, int64_t lo, int64_t hi, int k) {
+  mt_comp *m = (mt_comp *)c;
+  const uint64_t *d = m->d;
+  (void)k;
+  for (int64_t i = lo; i < hi; i++) {
+    const uint64_t xx = (uint64_t)i % d[0], yy = ((uint64_t)i / d[0]) % d[1];
+    const uint64_t zz = (uint64_t)i / (d[0] * d[1]);
+    uint64_t o[3];
+    pred_origin(m->ndim, 0, xx, yy, zz, o);
+    m->delta[i] = (int32_t)((int64_t)m->q[i] -
+                            lorenzo_pred(m->q, d, o, m->ndim, (int64_t)xx, (int64_t)yy, (int64_t)zz));
+  }
+}
+static void mt_tiles(void *c, int64_t lo, int64_t hi, int k) {
+  mt_comp *m = (mt_comp *)c;
+  (void)k;
+  for (int64_t t = lo; t < hi; t++) {
+    uint16_t codes[FZO_TILE_CODES];
+    uint32_t words[1024];
+    m->tile_out[t + 1] = tile_codes(m->delta, m->dims, m->ndim, m->d, (uint64_t)t, codes);
+    for (int w = 0; w < 1024; w++)
+      words[w] = (uint32_t)codes[2 * w] | ((uint32_t)codes[2 * w + 1] << 16);
+    fzo_bitshuffle(words, m->shuf + t * 1024);
+    fzo_block_flags(m->shuf + t * 1024, m->flags + t * 8);
+  }
+}
+/* escapes in stream order: each tile writes its own slice of the list */
+static void mt_escapes(void *c, int64_t lo, int64_t hi, int k) {
+  mt_comp *m = (mt_comp *)c;
+  const uint64_t *d = m->d;
+  (void)k;
+  for (int64_t t = lo; t < hi; t++) {
+    if (m->tile_out[t + 1] == m->tile_out[t]) continue;
+    uint16_t codes[FZO_TILE_CODES];
+    tile_codes(m->delta, m->dims, m->ndim, d, (uint64_t)t, codes);
+    uint64_t j = m->tile_out[t];
+    for (uint32_t p = 0; p < FZO_TILE_CODES; p++) {
+      if (codes[p] != 0x8000) continue;
+      uint32_t c3[3];
+      fzo_tile_coord(m->ndim, m->dims, (uint64_t)t, p, c3);
+      put_u32(m->po + 8 * j, (uint32_t)((uint64_t)t * FZO_TILE_CODES + p));
+      put_u32(m->po + 8 * j + 4,
+              (uint32_t)m->delta[c3[0] + d[0] * (c3[1] + d[1] * (uint64_t)c3[2])]);
+      j++;
+    }
+  }
+}
+
+int fzo_compress_mt(const float *x, const uint32_t dims[3], int ndim, int mode,
+                    double eb, uint8_t *out, uint64_t cap, uint64_t *out_size) {
+  *out_size = 0;
+  if (!x || !out || !check_dims(ndim, dims)) return FZO_ERR_ARG;
+  if (mode != FZO_EB_ABS && mode != FZO_EB_REL) return FZO_ERR_ARG;
+  if (!(eb > 0.0) || !isfinite(eb)) return FZO_ERR_ARG;
+  if (fegetround() != FE_TONEAREST) return FZO_ERR_ARG;
+  uint64_t d[3];
+  norm_dims(ndim, dims, d);
+  const int64_t n = (int64_t)(d[0] * d[1] * d[2]);
+  const int T = fzo_threads();
+  mt_comp *m = (mt_comp *)calloc(1, sizeof(mt_comp));
+  if (!m) return FZO_ERR_ARG;
+  m->x = x; m->dims = dims; m->d = d; m->ndim = ndim;
+
+  mt_for(n, T, mt_finite, m);
+  int bad = 0;
+  for (int k = 0; k < T; k++) bad |= m->bad[k];
+  if (bad) { free(m); return FZO_ERR_NONFINITE; }
+
+  /* min and max are exact, so the order of the partial results is free */
+  float fmin = 0.0f, fmax = 0.0f;
+  if (mode == FZO_EB_REL) {
+    mt_for(n, T, mt_minmax, m);
+    fmin = m->lo[0]; fmax = m->hi[0];
+    for (int k = 1; k < T; k++) {
+      if (m->lo[k] < fmin) fmin = m->lo[k];
+      if (m->hi[k] > fmax) fmax = m->hi[k];
+    }
+    fmin = fmin + 0.0f;
+    fmax = fmax + 0.0f;
+  }
+  float eb_f, ebx2, ebx2_r;
+  int st = fzo_derive_eb(mode, eb, fmin, fmax, &eb_f, &ebx2, &ebx2_r);
+  if (st) { free(m); return st; }
+
+  m->q = (int32_t *)malloc(n * sizeof(int32_t));
+  m->delta = (int32_t *)malloc(n * sizeof(int32_t));
+  if (!m->q || !m->delta) { free(m->q); free(m->delta); free(m); return FZO_ERR_ARG; }
+  m->ebx2_r = ebx2_r;
+  mt_for(n, T, mt_prequant, m);
+  bad = 0;
+  for (int k = 0; k < T; k++) bad |= m->bad[k];
+  if (bad) { free(m->q); free(m->delta); free(m); return FZO_ERR_EB_RANGE; }
+  mt_for(n, T, mt_lorenzo, m);
+  free(m->q);
+  m->q = NULL;
+
+  const int64_t nt = (int64_t)fzo_num_tiles(ndim, dims);
+  m->shuf = (uint32_t *)malloc(nt * 1024 * sizeof(uint32_t));
+  m->flags = (uint32_t *)malloc(nt * 8 * sizeof(uint32_t));
+  m->tile_out = (uint64_t *)malloc((nt + 1) * sizeof(uint64_t));
+  mt_for(nt, T, mt_tiles, m);
+  m->tile_out[0] = 0;
+  for (int64_t t = 0; t < nt; t++) m->tile_out[t + 1] += m->tile_out[t];
+  const uint64_t n_out = m->tile_out[nt];
+  const uint32_t *flags = m->flags, *shuf = m->shuf;
+
+  /* compaction, serial: block k goes to PreSum[k] (Listing 2) */
+  const uint64_t nblk = (uint64_t)nt * 256;
+  uint64_t nnz = 0;
+  for (uint64_t k = 0; k < nblk; k++) nnz += (flags[k / 32] >> (k % 32)) & 1u;
+  const uint64_t size = FZO_HEADER_BYTES + 32 * (uint64_t)nt + 16 * nnz + 8 * n_out;
+  if (size > cap) {
+    *out_size = size;
+    free(m->shuf); free(m->flags); free(m->tile_out); free(m->delta); free(m);
+    return FZO_ERR_CAPACITY;
+  }
+  memset(out, 0, FZO_HEADER_BYTES);
+  out[0] = 'F'; out[1] = 'Z'; out[2] = 'G'; out[3] = '1';
+  out[4] = 1; out[5] = (uint8_t)ndim; out[6] = (uint8_t)mode; out[7] = 0;
+  put_u32(out + 8, (uint32_t)d[0]);
+  put_u32(out + 12, (uint32_t)d[1]);
+  put_u32(out + 16, (uint32_t)d[2]);
+  put_u32(out + 20, (uint32_t)nt);
+  put_f64(out + 24, eb);
+  put_f32(out + 32, eb_f);
+  put_f32(out + 36, ebx2);
+  put_f32(out + 40, ebx2_r);
+  put_u32(out + 44, (uint32_t)nnz);
+  put_u32(out + 48, (uint32_t)n_out);
+  put_f32(out + 52, fmin);
+  put_f32(out + 56, fmax);
+  uint8_t *pf = out + FZO_HEADER_BYTES;
+  for (uint64_t i = 0; i < (uint64_t)nt * 8; i++) put_u32(pf + 4 * i, flags[i]);
+  uint8_t *pp = pf + 32 * (uint64_t)nt;
+  uint64_t presum = 0;
+  for (uint64_t k = 0; k < nblk; k++) {
+    if ((flags[k / 32] >> (k % 32)) & 1u) {
+      for (int i = 0; i < 4; i++) put_u32(pp + 16 * presum + 4 * i, shuf[4 * k + i]);
+      presum++;
+    }
+  }
+  m->po = pp + 16 * nnz;
+  mt_for(nt, T, mt_escapes, m);
+  *out_size = size;
+  free(m->shuf); free(m->flags); free(m->tile_out); free(m->delta); free(m);
+  return FZO_OK;
+}
+
+typedef struct {
+  const uint8_t *pf, *pp, *po;
+  const uint32_t *dims;
+  const uint64_t *d;
+  int ndim;
+  uint64_t n_out;
+  const uint64_t *tile_pre;
+  int32_t *delta;
+  int64_t *q;
+  float *x;
+  float ebx2;
+  uint32_t ch[3];
+  uint64_t ncx, ncy;
+  int bad[MT_MAX_THREADS];
+  uint64_t matched[MT_MAX_THREADS];
+} mt_dec;
+
+static void mt_unshuffle(void *c, int64_t lo, int64_t hi, int k) {
+  mt_dec *m = (mt_dec *)c;
+  const uint64_t *d = m->d;
+  int bad = 0;
+  uint64_t matched = 0;
+  for (int64_t t = lo; t < hi && !bad; t++) {
+    uint32_t shuf[1024], words[1024];
+    uint64_t presum = m->tile_pre[t];
+    for (int b = 0; b < 256; b++) {
+      int f = (get_u32(m->pf + 32 * t + 4 * (b / 32)) >> (b % 32)) & 1u;
+      for (int i = 0; i < 4; i++) shuf[4 * b + i] = f ? get_u32(m->pp + 16 * presum + 4 * i) : 0;
+      presum += (uint64_t)f;
+    }
+    fzo_bitunshuffle(shuf, words);
+    /* this tile's first outlier record: the records are sorted by index */
+    uint64_t lo2 = 0, hi2 = m->n_out;
+    const uint32_t first = (uint32_t)((uint64_t)t * FZO_TILE_CODES);
+    while (lo2 < hi2) {
+      uint64_t mid = (lo2 + hi2) / 2;
+      if (get_u32(m->po + 8 * mid) < first) lo2 = mid + 1; else hi2 = mid;
+    }
+    uint64_t oi = lo2;
+    for (uint32_t p = 0; p < FZO_TILE_CODES; p++) {
+      uint16_t code = (uint16_t)(words[p / 2] >> (16 * (p % 2)));
+      uint32_t c3[3];
+      int in_field = fzo_tile_coord(m->ndim, m->dims, (uint64_t)t, p, c3);
+      uint32_t sidx = first + p;
+      int32_t dl;
+      if (code == 0x8000) {
+        if (oi >= m->n_out || get_u32(m->po + 8 * oi) != sidx) { bad = 1; break; }
+        dl = (int32_t)get_u32(m->po + 8 * oi + 4);
+        oi++;
+        matched++;
+      } else {
+        if (oi < m->n_out && get_u32(m->po + 8 * oi) == sidx) { bad = 1; break; }
+        dl = fzo_decode(code);
+      }
+      if (!in_field) {
+        if (code != 0) { bad = 1; break; }
+        continue;
+      }
+      m->delta[c3[0] + d[0] * (c3[1] + d[1] * (uint64_t)c3[2])] = dl;
+    }
+  }
+  m->bad[k] = bad;
+  m->matched[k] = matched;
+}
+/* the predictor recurrence chunk by chunk (chunks are independent) */
+static void mt_inverse(void *c, int64_t lo, int64_t hi, int k) {
+  mt_dec *m = (mt_dec *)c;
+  const uint64_t *d = m->d;
+  const int64_t *q = m->q;
+  (void)k;
+  for (int64_t ci = lo; ci < hi; ci++) {
+    const uint64_t o[3] = {((uint64_t)ci % m->ncx) * m->ch[0],
+                           (((uint64_t)ci / m->ncx) % m->ncy) * m->ch[1],
+                           ((uint64_t)ci / (m->ncx * m->ncy)) * m->ch[2]};
+    for (uint64_t z = o[2]; z < o[2] + m->ch[2] && z < d[2]; z++)
+      for (uint64_t y = o[1]; y < o[1] + m->ch[1] && y < d[1]; y++)
+        for (uint64_t xx = o[0]; xx < o[0] + m->ch[0] && xx < d[0]; xx++) {
+          int64_t X = (int64_t)xx, Y = (int64_t)y, Z = (int64_t)z;
+          int64_t pred;
+          if (m->ndim == 1)
+            pred = qt64(q, d, o, X - 1, Y, Z);
+          else if (m->ndim == 2)
+            pred = qt64(q, d, o, X - 1, Y, Z) + qt64(q, d, o, X, Y - 1, Z) -
+                   qt64(q, d, o, X - 1, Y - 1, Z);
+          else
+            pred = qt64(q, d, o, X - 1, Y, Z) + qt64(q, d, o, X, Y - 1, Z) +
+                   qt64(q, d, o, X, Y, Z - 1) - qt64(q, d, o, X - 1, Y - 1, Z) -
+                   qt64(q, d, o, X - 1, Y, Z - 1) - qt64(q, d, o, X, Y - 1, Z - 1) +
+                   qt64(q, d, o, X - 1, Y - 1, Z - 1);
+          const uint64_t i = xx + d[0] * (y + d[1] * z);
+          m->q[i] = (int64_t)m->delta[i] + pred;
+        }
+  }
+}
+static void mt_dequant(void *c, int64_t lo, int64_t hi, int k) {
+  mt_dec *m = (mt_dec *)c;
+  (void)k;
+  for (int64_t i = lo; i < hi; i++) {
+    volatile float qf = (float)m->q[i];
+    m->x[i] = qf * m->ebx2;
+  }
+}
+
+int fzo_decompress_mt(const uint8_t *in, uint64_t in_size, float *x, uint64_t cap_elems) {
+  if (!in || !x) return FZO_ERR_ARG;
+  if (in_size < FZO_HEADER_BYTES) return FZO_ERR_CORRUPT;
+  if (in[4] == 2) return fzo_decompress(in, in_size, x, cap_elems);   /* whole-field */
+  if (in[0] != 'F' || in[1] != 'Z' || in[2] != 'G' || in[3] != '1' || in[4] != 1 ||
+      in[7] != 0)
+    return FZO_ERR_CORRUPT;
+  int ndim = in[5], mode = in[6];
+  uint32_t dims[3] = {get_u32(in + 8), get_u32(in + 12), get_u32(in + 16)};
+  if (ndim < 1 || ndim > 3 || mode > 1) return FZO_ERR_CORRUPT;
+  for (int i = ndim; i < 3; i++)
+    if (dims[i] != 1) return FZO_ERR_CORRUPT;
+  if (!check_dims(ndim, dims)) return FZO_ERR_CORRUPT;
+  const int64_t nt = (int64_t)fzo_num_tiles(ndim, dims);
+  if (get_u32(in + 20) != (uint64_t)nt) return FZO_ERR_CORRUPT;
+  float ebx2 = get_f32(in + 36);
+  uint64_t nnz = get_u32(in + 44), n_out = get_u32(in + 48);
+  if (FZO_HEADER_BYTES + 32 * (uint64_t)nt + 16 * nnz + 8 * n_out != in_size)
+    return FZO_ERR_CORRUPT;
+  uint64_t d[3];
+  norm_dims(ndim, dims, d);
+  const int64_t n = (int64_t)(d[0] * d[1] * d[2]);
+  if (cap_elems < (uint64_t)n) return FZO_ERR_CAPACITY;
+  const int T = fzo_threads();
+  mt_dec *m = (mt_dec *)calloc(1, sizeof(mt_dec));
+  uint64_t *tile_pre = (uint64_t *)malloc((nt + 1) * sizeof(uint64_t));
+  if (!m || !tile_pre) { free(m); free(tile_pre); return FZO_ERR_ARG; }
+  m->pf = in + FZO_HEADER_BYTES;
+  m->pp = m->pf + 32 * (uint64_t)nt;
+  m->po = m->pp + 16 * nnz;
+  m->dims = dims; m->d = d; m->ndim = ndim; m->n_out = n_out; m->ebx2 = ebx2;
+
+  /* each tile's first payload block (serial prefix of the flag counts) */
+  tile_pre[0] = 0;
+  for (int64_t t = 0; t < nt; t++) {
+    uint64_t c = 0;
+    for (int j = 0; j < 8; j++) c += (uint64_t)__builtin_popcount(get_u32(m->pf + 32 * t + 4 * j));
+    tile_pre[t + 1] = tile_pre[t] + c;
+  }
+  int bad = tile_pre[nt] != nnz;
+  for (uint64_t i = 0; i < n_out && !bad; i++) {
+    uint32_t idx = get_u32(m->po + 8 * i);
+    int32_t v = (int32_t)get_u32(m->po + 8 * i + 4);
+    if (idx >= (uint64_t)nt * FZO_TILE_CODES) bad = 1;
+    if (i > 0 && idx <= get_u32(m->po + 8 * (i - 1))) bad = 1;
+    if (v >= -32767 && v <= 32767) bad = 1;
+  }
+  if (bad) { free(tile_pre); free(m); return FZO_ERR_CORRUPT; }
+  m->tile_pre = tile_pre;
+  m->delta = (int32_t *)calloc(n, sizeof(int32_t));
+  m->q = (int64_t *)malloc(n * sizeof(int64_t));
+  if (!m->delta || !m->q) {
+    free(m->delta); free(m->q); free(tile_pre); free(m);
+    return FZO_ERR_ARG;
+  }
+  mt_for(nt, T, mt_unshuffle, m);
+  uint64_t matched = 0;
+  for (int k = 0; k < T; k++) { bad |= m->bad[k]; matched += m->matched[k]; }
+  free(tile_pre);
+  if (!bad && matched != n_out) bad = 1;
+  if (bad) { free(m->delta); free(m->q); free(m); return FZO_ERR_CORRUPT; }
+
+  fzo_chunk_shape(ndim, m->ch);
+  m->ncx = ceil_div(d[0], m->ch[0]);
+  m->ncy = ceil_div(d[1], m->ch[1]);
+  const int64_t nc = (int64_t)(m->ncx * m->ncy * ceil_div(d[2], m->ch[2]));
+  mt_for(nc, T, mt_inverse, m);
+  m->x = x;
+  mt_for(n, T, mt_dequant, m);
+  free(m->delta); free(m->q); free(m);
+  return FZO_OK;
+}

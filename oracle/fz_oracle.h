@@ -154,6 +154,16 @@ int fzo_pwrel_forward(const float *x, uint64_t n, float *y, uint32_t *signs);
 /* x[i] = +-2^y[i] (0 below -154, +-FLT_MAX from 128 up) */
 void fzo_pwrel_inverse(const float *y, uint64_t n, const uint32_t *signs, float *x);
 
+/* --- all host cores (the paper's multi-threaded FZ-OMP, Sec. 4.4) -------
+ * The same steps with the loops over points, tiles and chunks split over
+ * POSIX threads, one per online core; the compaction stays serial.  Streams
+ * and reconstructions are identical to fzo_compress / fzo_decompress.
+ * fzo_threads: the threads these calls use. */
+int fzo_threads(void);
+int fzo_compress_mt(const float *x, const uint32_t dims[3], int ndim, int mode,
+                    double eb, uint8_t *out, uint64_t cap, uint64_t *out_size);
+int fzo_decompress_mt(const uint8_t *in, uint64_t in_size, float *x, uint64_t cap_elems);
+
 #ifdef __cplusplus
 }
 #endif
