@@ -44,9 +44,9 @@ WORKLOAD_DESC = ("512x512x512 float32 lognormal density exp(0.5 g), g a unit-std
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# each kernel on the 512^3 workload, from one ncu capture of this benchmark
-# (summarised in profiles/launches_cosmo3d_512.md).  A figure stands only while
-# the kernel's sources are the ones that were captured (SHA-256 over them).
+# each kernel on the 512^3 workload, from one ncu capture of this benchmark's
+# kernels.  A figure stands only while the kernel's sources are the ones that
+# were captured (SHA-256 over them); otherwise the line reports null.
 TRAFFIC = {
     "compress_kernel": (("fz_compress.cu", "fz_compress_impl.cuh", "fz_device.cuh", "fz_kernels.h"),
                         "ed8ff315521d5da5d8881d1990c8685a249c5370ba22054d09e2fab6529b70fe",
@@ -151,17 +151,29 @@ def make_field(slab=None, size=512):
     return x
 
 
-def cpu_oracle_round_trip(x, reps=1):
-    """Time the CPU oracle (as it stands, one thread) compress+decompress."""
+def cpu_oracle_round_trip(x, reps=1, all_cores=False):
+    """Time the CPU oracle (as it stands: one thread, or its all-cores
+    variant) compress+decompress."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
     for _ in range(reps):
-        st, s = oracle.compress(x, 3, oracle.EB_REL, 1e-3)
+        st, s = oracle.compress(x, 3, oracle.EB_REL, 1e-3, all_cores=all_cores)
         assert st == oracle.OK
-        st, _ = oracle.decompress(s)
+        st, _ = oracle.decompress(s, all_cores=all_cores)
         assert st == oracle.OK
     return time.perf_counter() - t0, len(s)
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def run_reference(args, rank):
@@ -169,26 +181,30 @@ def run_reference(args, rank):
     slab of the same workload per step (rank 0 only)."""
     if rank != 0:
         return
-    slab = 16
+    import oracle
+    slab = 32
     x = make_field(slab)
     n = x.size
     for _ in range(args.warmup):
-        cpu_oracle_round_trip(x)
+        cpu_oracle_round_trip(x, all_cores=True)
     times = []
     for _ in range(args.steps):
-        t, _ = cpu_oracle_round_trip(x)
+        t, _ = cpu_oracle_round_trip(x, all_cores=True)
         times.append(t)
     ms = 1e3 * sum(times) / len(times)
     value = 2 * 4 * n / (ms / 1e3) / 1e9
-    sample = f"512x512x{slab} slab of the 512^3 field, compress+decompress per step"
+    cores = oracle.threads()
+    sample = (f"512x512x{slab} slab of the 512^3 field, compress+decompress per step, "
+              f"the oracle's all-cores variant on {cores} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1,
-                         "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores,
+                         "kind": "oracle", "sample": sample, "cpu_model": cpu_model(),
+                         "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -214,23 +230,23 @@ def run_ours(args, rank, world, local_rank, dist):
     field_bytes = 4 * n
     x_d = torch.from_numpy(x_h).to(dev)
     codec = fz.Codec(local_rank)
-    codec.set_profiling(True)
     stream = torch.cuda.current_stream(dev)
     cap = fz.stream_min_bytes((S, S, S), 3) + 16 * 256 * (n // 2048 + 64)
     s_d = torch.empty(cap, dtype=torch.uint8, device=dev)
     y_d = torch.empty_like(x_d)
 
+    # One step: the whole fz_compress call, then the whole fz_decompress
+    # call, each bracketed by CUDA events on the stream (so a call's time
+    # includes its launches, its result read-back and its synchronisation).
     def step(rec):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         st, size = codec.compress_into(x_d, s_d, "rel", 1e-3, 3)
-        kc = codec.kernel_times_ms()
         e1.record(stream)
         codec.decompress_into(s_d, y_d, nbytes=size)
-        kd = codec.kernel_times_ms()
         e2.record(stream)
         if rec is not None:
-            rec.append((e0, e1, e2, kc, kd, size))
+            rec.append((e0, e1, e2, size))
         return size
 
     for _ in range(max(args.warmup, 3)):
@@ -276,27 +292,37 @@ def run_ours(args, rank, world, local_rank, dist):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_step = total_ms / args.steps
+    comp_ms = [a.elapsed_time(b) for a, b, _, _ in recs]
+    dec_ms = [b.elapsed_time(c) for _, b, c, _ in recs]
+    size = recs[-1][3]
 
-    comp_ms = [a.elapsed_time(b) for a, b, _, _, _, _ in recs]
-    dec_ms = [b.elapsed_time(c) for _, b, c, _, _, _ in recs]
-    k_range = [kc[0] for _, _, _, kc, _, _ in recs]
-    k_comp = [kc[1] for _, _, _, kc, _, _ in recs]
-    k_out = [kc[2] for _, _, _, kc, _, _ in recs]
-    k_dec = [kd[3] for _, _, _, _, kd, _ in recs]
-    k_doff = [kd[4] for _, _, _, _, kd, _ in recs]
-    size = recs[-1][5]
+    # A second timed pass of the same steps with the library's per-kernel
+    # CUDA events (recorded on the launching stream around every kernel):
+    # each kernel's duration, for the kernel-level roofline.
+    codec.set_profiling(True)
+    kc_all, kd_all = [], []
+    for _ in range(args.steps):
+        codec.compress_into(x_d, s_d, "rel", 1e-3, 3)
+        kc_all.append(codec.kernel_times_ms())
+        codec.decompress_into(s_d, y_d, nbytes=size)
+        kd_all.append(codec.kernel_times_ms())
+    codec.set_profiling(False)
+    k_range = [kc[0] for kc in kc_all]
+    k_comp = [kc[1] for kc in kc_all]
+    k_out = [kc[2] for kc in kc_all]
+    k_dec = [kd[3] for kd in kd_all]
+    k_doff = [kd[4] for kd in kd_all]
     # per step: range, compress, (outliers), offsets pass, decompress
-    launches = sum(4 + (1 if kc[2] > 0 else 0) for _, _, _, kc, _, _ in recs)
+    launches = args.steps * (4 + (1 if max(k_out) > 0 else 0))
 
-    # roofline of the dominant kernel (algorithmic bytes per launch)
     mean = lambda v: sum(v) / len(v)
+    peak, peak_kind = peaks()
     kern = {
         "compress_kernel": (mean(k_comp), field_bytes + size),
         "decompress_kernel": (mean(k_dec), size + field_bytes),
         "range_kernel": (mean(k_range), field_bytes),
     }
     dom = max(kern, key=lambda k: kern[k][0])
-    peak, peak_kind = peaks()
     achieved = kern[dom][1] / (kern[dom][0] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak,
@@ -324,6 +350,18 @@ def run_ours(args, rank, world, local_rank, dist):
             "GB/s": (size + field_bytes) / (dec_path_ms / 1e3) / 1e9,
             "frac": (size + field_bytes) / (dec_path_ms / 1e3) / 1e9 / peak},
     }
+    # The whole calls from the headline pass (p50): fz_compress with its
+    # range pass, launches, result read-back and synchronisation against
+    # 8 + 4/CR bytes per element; fz_decompress against 4/CR + 4.
+    c50, d50 = percentile(comp_ms, 0.5), percentile(dec_ms, 0.5)
+    roof["calls"] = {
+        "fz_compress": {"ms_p50": c50, "bytes": 2 * field_bytes + size,
+                        "GB/s": (2 * field_bytes + size) / (c50 / 1e3) / 1e9,
+                        "frac": (2 * field_bytes + size) / (c50 / 1e3) / 1e9 / peak},
+        "fz_decompress": {"ms_p50": d50, "bytes": size + field_bytes,
+                          "GB/s": (size + field_bytes) / (d50 / 1e3) / 1e9,
+                          "frac": (size + field_bytes) / (d50 / 1e3) / 1e9 / peak},
+    }
 
     # the same compression as the paper's separate kernels (codes and
     # shuffled words through HBM): what fusing them saves on this GPU
@@ -346,13 +384,20 @@ def run_ours(args, rank, world, local_rank, dist):
 
     cpu = None
     if rank == 0 and world >= 1 and not args.no_cpu_baseline:
+        import oracle
+        t_all, _ = cpu_oracle_round_trip(x_h, all_cores=True)
         slab = S // 2
-        t, _ = cpu_oracle_round_trip(x_h[:slab].copy())
-        cpu = {"value": 2 * 4 * x_h[:slab].size / t / 1e9, "unit": "GB/s",
-               "cores": 1, "kind": "oracle",
-               "sample": f"{S}x{S}x{slab} slab (half) of the same field, "
-                         "one compress+decompress, single-threaded C oracle",
-               "seconds": t}
+        t_one, _ = cpu_oracle_round_trip(x_h[:slab].copy())
+        cpu = {"value": 2 * field_bytes / t_all / 1e9, "unit": "GB/s",
+               "cores": oracle.threads(), "kind": "oracle",
+               "sample": f"the whole {S}^3 field, one compress+decompress, the oracle's "
+                         "all-cores variant (OpenMP over points, tiles and chunks; "
+                         "serial compaction)",
+               "seconds": t_all, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+               "one_thread": {"value": 2 * 4 * x_h[:slab].size / t_one / 1e9,
+                              "unit": "GB/s", "cores": 1, "seconds": t_one,
+                              "sample": f"{S}x{S}x{slab} slab (half) of the same field, "
+                                        "one compress+decompress, single-threaded"}}
     value = world * 2 * field_bytes / (ms_step / 1e3) / 1e9
     if rank == 0:
         line = {
@@ -368,8 +413,8 @@ def run_ours(args, rank, world, local_rank, dist):
                        "parallelism": f"{world} independent field(s), one per GPU"},
             "compress_gbs": field_bytes / (statistics.mean(comp_ms) / 1e3) / 1e9,
             "decompress_gbs": field_bytes / (statistics.mean(dec_ms) / 1e3) / 1e9,
-            "compress_ms": {"p50": percentile(comp_ms, 0.5), "p99": percentile(comp_ms, 0.99)},
-            "decompress_ms": {"p50": percentile(dec_ms, 0.5), "p99": percentile(dec_ms, 0.99)},
+            "compress_ms": {"p50": c50, "p99": percentile(comp_ms, 0.99)},
+            "decompress_ms": {"p50": d50, "p99": percentile(dec_ms, 0.99)},
             "kernel_ms": {"range": mean(k_range), "compress": mean(k_comp),
                           "outliers": mean(k_out), "decompress_offsets": mean(k_doff),
                           "decompress": mean(k_dec)},
@@ -379,8 +424,6 @@ def run_ours(args, rank, world, local_rank, dist):
         }
         print(json.dumps(line), flush=True)
     codec.close()
-
-
 
 
 def run_e2e(codec, x_h, cap, world, field_bytes, args, torch):

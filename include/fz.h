@@ -231,6 +231,17 @@ int fz_compress_staged(fz_ctx *ctx, const float *d_in, const uint64_t dims[3],
                        uint64_t out_capacity, uint64_t *out_size, double ms[5],
                        void *stream);
 
+/* The bitshuffle of fz_compress_staged (Sec. 3.3, Listing 1):
+ * FZ_SHUFFLE_REGISTER (default) transposes each lane's 32 code words in
+ * registers; FZ_SHUFFLE_BALLOT is Listing 1's form, 32 warp ballots per
+ * 32-word group, one word per lane (plane b of group g to word 32b + g).
+ * The stream is the same byte for byte; the choice only changes the time.
+ * The fused fz_compress always uses the register transpose.  FZ_OK or
+ * FZ_ERR_ARG. */
+#define FZ_SHUFFLE_REGISTER 0
+#define FZ_SHUFFLE_BALLOT 1
+int fz_set_staged_shuffle(fz_ctx *ctx, int kind);
+
 /* ---------------------------------------------------------------------
  * Many fields in one persistent launch.  A batch is planned once for a fixed
  * list of fields (their device buffers, dims and bounds); every run
@@ -291,8 +302,9 @@ int fz_batch_tuning(const fz_batch *batch, int *tma_on, double ms[2]);
  * for the request's input, output and scratch (a later request may pass
  * one that does not fit yet), copies their inputs in, and runs them:
  * every admitted compress request joins the next batched launch (as in
- * fz_batch_*; the next batch is formed and queued while one runs), and
- * decompressions run on a second stream beside the batches.  Results stay
+ * fz_batch_*; two batches alternate on two streams, so the next batch is
+ * formed, queued and started on the device while one runs), and
+ * decompressions run on a third stream beside the batches.  Results stay
  * in the pool until fetched.  Each result equals what fz_compress /
  * fz_decompress return for that input alone.  The paper has no counterpart. */
 
@@ -351,6 +363,26 @@ int fz_server_fetch(fz_server *server, uint64_t id, void *h_out, uint64_t capaci
 /* Counters and latency percentiles; reset != 0 starts a new window. */
 int fz_server_get_stats(fz_server *server, fz_server_stats *stats, int reset);
 
+/* Where a request's time went, for a request not yet fetched.  Host times
+ * are ms since the server's creation (steady clock); GPU times are ms since
+ * an event the server recorded at its creation, from CUDA events around the
+ * request's kernels (the whole batch's, for a compress request).  Fields not
+ * reached yet are negative. */
+typedef struct fz_request_info {
+  uint64_t batch;         /* compress: the batch it ran in, numbered from 1
+                             in launch order; decompress: 0                     */
+  uint64_t launch_seq;    /* the order in which its GPU work was launched,
+                             batches and decompressions counted together
+                             from 1                                             */
+  double submit_ms;       /* fz_server_submit                                   */
+  double admit_ms;        /* pool room found, input copy queued                 */
+  double launch_ms;       /* its kernels queued                                 */
+  double done_ms;         /* the worker saw them complete                       */
+  double gpu_start_ms;    /* its kernels (its batch) began on the device        */
+  double gpu_end_ms;      /* ... and ended                                      */
+} fz_request_info;
+int fz_server_request_info(fz_server *server, uint64_t id, fz_request_info *info);
+
 /* ---------------------------------------------------------------------
  * Compression without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
@@ -362,17 +394,22 @@ int fz_server_get_stats(fz_server *server, fz_server_stats *stats, int reset);
  *
  * Same arguments, stream format and statuses as fz_compress, but with no
  * context: the look-back and result scratch lives in one statically sized
- * device array inside the library (about 1.6 MB per device, kept until the
- * process exits).  Fields are limited to FZ_NOALLOC_MAX_CODES codes after
- * padding to whole chunks (a 512^3 field fits); larger fields return
- * FZ_ERR_ARG.  The call uses the calling thread's current device.  Its
- * first call on a device looks up the array's device address, so make that
- * first call before any stream capture.  Every call on a device shares the
- * one array and clears the parts that must start at zero; calls whose GPU
- * work overlaps (different streams or threads at the same time) race on it
- * and must be serialised by the caller.  No cudaMalloc, cudaFree or other
- * allocating routine is called. */
+ * device array inside the library, FZ_NOALLOC_SCRATCH_BYTES (at most
+ * 1.75 MiB) per device, kept until the process exits.  That array is not
+ * allocated by this call, but the CUDA driver reserves it in device memory
+ * when it loads the library's device code on a device, which under lazy
+ * module loading (the default) happens at the first call on that device.
+ * So make one call on each device at start-up, before a memory pool takes
+ * the free HBM, and before any stream capture (the first call also looks up
+ * the array's device address).  Fields are limited to FZ_NOALLOC_MAX_CODES
+ * codes after padding to whole chunks (a 512^3 field fits); larger fields
+ * return FZ_ERR_ARG.  The call uses the calling thread's current device.
+ * Every call on a device shares the one array and clears the parts that
+ * must start at zero; calls whose GPU work overlaps (different streams or
+ * threads at the same time) race on it and must be serialised by the
+ * caller.  No cudaMalloc, cudaFree or other allocating routine is called. */
 #define FZ_NOALLOC_MAX_CODES 134217728ull
+#define FZ_NOALLOC_SCRATCH_BYTES 1835008ull
 int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], int ndim,
                         int mode, double eb, void *d_out,
                         uint64_t out_capacity, uint64_t *out_size,

@@ -45,7 +45,8 @@ C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
          "fz_batch_compress", "fz_batch_set_graph", "fz_batch_autotune",
          "fz_batch_tuning", "fz_server_create", "fz_server_destroy",
          "fz_server_submit", "fz_server_poll", "fz_server_fetch",
-         "fz_server_get_stats", "fz_compress_staged", "fz_compress_noalloc",
+         "fz_server_get_stats", "fz_server_request_info", "fz_compress_staged", "fz_set_staged_shuffle",
+         "fz_compress_noalloc",
          "fz_pwrel_bound", "fz_pwrel_forward", "fz_pwrel_inverse"]
 
 _lib = None
@@ -82,6 +83,13 @@ class _Request(ctypes.Structure):
                 ("dims", _u64 * 3), ("mode", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("eb", ctypes.c_double),
                 ("h_in", _vp), ("in_bytes", _u64)]
+
+
+class _RequestInfo(ctypes.Structure):
+    _fields_ = [("batch", _u64), ("launch_seq", _u64), ("submit_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("launch_ms", ctypes.c_double),
+                ("done_ms", ctypes.c_double), ("gpu_start_ms", ctypes.c_double),
+                ("gpu_end_ms", ctypes.c_double)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -171,6 +179,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_server_fetch.argtypes = [_vp, _u64, _vp, _u64]
         L.fz_server_get_stats.argtypes = [_vp, ctypes.POINTER(_ServerStats),
                                           ctypes.c_int]
+        L.fz_server_request_info.argtypes = [_vp, _u64, ctypes.POINTER(_RequestInfo)]
+        L.fz_set_staged_shuffle.argtypes = [_vp, ctypes.c_int]
         L.fz_compress_staged.argtypes = [_vp, _vp, dims_t, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, _vp, _u64,
                                          ctypes.POINTER(_u64),
@@ -420,6 +430,15 @@ class Server:
         self._meta.pop(rid, None)
         self._L.fz_server_fetch(self._h, rid, None, 0)
 
+    def info(self, rid):
+        """Where the request's time went (see fz_server_request_info): a dict
+        of batch, launch_seq and host/GPU times in ms; call before fetch."""
+        i = _RequestInfo()
+        st = self._L.fz_server_request_info(self._h, rid, ctypes.byref(i))
+        if st != OK:
+            raise FZError(st, "fz_server_request_info")
+        return {k: getattr(i, k) for k, _ in _RequestInfo._fields_}
+
     def stats(self, reset: bool = False):
         s = _ServerStats()
         st = self._L.fz_server_get_stats(self._h, ctypes.byref(s), int(bool(reset)))
@@ -563,6 +582,14 @@ class Codec:
         if st != OK and raise_on_error:
             raise FZError(st, "fz_compress_staged")
         return st, int(size.value), list(ms)
+
+    def set_staged_shuffle(self, kind: str):
+        """The unfused path's bitshuffle: 'register' (default) or 'ballot'
+        (Listing 1's warp ballots); the stream is the same."""
+        k = {"register": 0, "ballot": 1}[kind]
+        st = self._L.fz_set_staged_shuffle(self._ctx, k)
+        if st != OK:
+            raise FZError(st, "fz_set_staged_shuffle")
 
     def value_range(self, x, stream=None):
         """(min, max, nonfinite) of a float32 CUDA tensor (the range pass)."""

@@ -45,6 +45,7 @@ struct fz_ctx {
   void *staged = nullptr;
   uint64_t staged_tiles = 0;
   cudaEvent_t staged_ev[6] = {};
+  int staged_shuffle = FZ_SHUFFLE_REGISTER;
   // profiling: events around each kernel of the last call
   bool profiling = false;
   cudaEvent_t ev[2 * fz::kProfSlots] = {};
@@ -318,6 +319,12 @@ int fz_get_kernel_times(fz_ctx *c, double ms[5]) {
   return FZ_OK;
 }
 
+int fz_set_staged_shuffle(fz_ctx *c, int kind) {
+  if (!c || (kind != FZ_SHUFFLE_REGISTER && kind != FZ_SHUFFLE_BALLOT)) return FZ_ERR_ARG;
+  c->staged_shuffle = kind;
+  return FZ_OK;
+}
+
 int fz_debug_skip_publish(fz_ctx *c, uint64_t chunk) {
   if (!c) return FZ_ERR_ARG;
   c->skip_publish = chunk;
@@ -382,7 +389,8 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
   const bool tma = fz::compress_uses_tma(sh.ndim, a) &&
                    fz::encode_field_tmap(sh.ndim, sh.d, d_in, &tm);
   prof_begin(c, 1, s);
-  if (fz::launch_compress(sh.ndim, a, tma ? &tm : nullptr, c->num_sms, s) != cudaSuccess) {
+  if (fz::launch_compress(sh.ndim, a, tma ? &tm : nullptr, c->num_sms, s,
+                          mode == FZ_EB_REL && !rng) != cudaSuccess) {
     mark_all_dirty(c);
     return FZ_ERR_CUDA;
   }
@@ -587,7 +595,8 @@ int fz_compress_staged(fz_ctx *c, const float *d_in, const uint64_t dims[3], int
   a.out_capacity = cap;
   a.wait_limit_ns = c->wait_limit_ns;
   a.skip_publish_chunk = ~0ull;
-  if (fz::launch_staged(sh.ndim, a, w, c->num_sms, ev, s) != cudaSuccess) {
+  if (fz::launch_staged(sh.ndim, a, w, c->num_sms, c->staged_shuffle == FZ_SHUFFLE_BALLOT, ev,
+                        s) != cudaSuccess) {
     mark_all_dirty(c);
     return FZ_ERR_CUDA;
   }
@@ -712,7 +721,7 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   const int grid = c->num_sms * c->dec_blocks_per_sm;
   prof_reset(c);
   prof_begin(c, 4, s);
-  if (fz::launch_dec_offsets(a, bound, s) != cudaSuccess) {
+  if (fz::launch_dec_offsets(a, bound, c->num_sms, s) != cudaSuccess) {
     mark_all_dirty(c);
     return FZ_ERR_CUDA;
   }

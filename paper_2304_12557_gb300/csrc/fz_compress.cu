@@ -29,6 +29,7 @@ namespace fz {
 __global__ void __launch_bounds__(256) range_kernel(const float *__restrict__ x,
                                                     uint64_t n, float2 *partial,
                                                     RangeResult *res) {
+  grid_launch_dependents();              // the compressor may be scheduled now
   float lo = INFINITY, hi = -INFINITY;
   uint32_t bad = 0;
   const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -120,11 +121,6 @@ __global__ void __launch_bounds__(256) range_kernel(const float *__restrict__ x,
   }
 }
 
-// number of look-back status words a compression of n_tiles tiles uses
-uint64_t compress_status_words(uint64_t n_tiles) {
-  return (n_tiles + kCompWarps - 1) / kCompWarps;
-}
-
 // ====================================================================
 // launchers
 // ====================================================================
@@ -143,7 +139,7 @@ static int vec_width(const CompressArgs &a) {
 }
 
 template <int NDIM, int V, bool CHECK, bool TMA>
-static cudaError_t launch_c3(const CompressArgs &a, const CUtensorMap &tm, int sms,
+static cudaError_t launch_c3(const CompressArgs &a, const CUtensorMap &tm, int sms, bool pdl,
                              cudaStream_t s) {
   auto k = compress_kernel<NDIM, V, CHECK, TMA, false>;
   const int smem = TMA ? kCompSmemTma : kCompSmemLdg;
@@ -156,36 +152,45 @@ static cudaError_t launch_c3(const CompressArgs &a, const CUtensorMap &tm, int s
     if (e != cudaSuccess) return e;
     per_sm = n > 0 ? n : 1;
   }
-  k<<<sms * per_sm, kCompThreads, smem, s>>>(a, tm, BatchArgs{});
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sms * per_sm);
+  cfg.blockDim = dim3(kCompThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, a, tm, BatchArgs{});
 }
 
 template <int NDIM, int V, bool CHECK>
-static cudaError_t launch_c2(const CompressArgs &a, const CUtensorMap *tm, int sms,
+static cudaError_t launch_c2(const CompressArgs &a, const CUtensorMap *tm, int sms, bool pdl,
                              cudaStream_t s) {
   if constexpr (NDIM >= 2 && V >= 4) {
-    if (tm) return launch_c3<NDIM, V, CHECK, true>(a, *tm, sms, s);
+    if (tm) return launch_c3<NDIM, V, CHECK, true>(a, *tm, sms, pdl, s);
   }
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
-  return launch_c3<NDIM, V, CHECK, false>(a, none, sms, s);
+  return launch_c3<NDIM, V, CHECK, false>(a, none, sms, pdl, s);
 }
 
 template <int NDIM, int V>
-static cudaError_t launch_c1(const CompressArgs &a, const CUtensorMap *tm, int sms,
+static cudaError_t launch_c1(const CompressArgs &a, const CUtensorMap *tm, int sms, bool pdl,
                              cudaStream_t s) {
   // every element is range-checked unless a range pass has bounded them all
-  return (a.mode == 0 || a.range_given) ? launch_c2<NDIM, V, true>(a, tm, sms, s)
-                                        : launch_c2<NDIM, V, false>(a, tm, sms, s);
+  return (a.mode == 0 || a.range_given) ? launch_c2<NDIM, V, true>(a, tm, sms, pdl, s)
+                                        : launch_c2<NDIM, V, false>(a, tm, sms, pdl, s);
 }
 
 template <int NDIM>
-static cudaError_t launch_c0(const CompressArgs &a, const CUtensorMap *tm, int sms,
+static cudaError_t launch_c0(const CompressArgs &a, const CUtensorMap *tm, int sms, bool pdl,
                              cudaStream_t s) {
   switch (vec_width(a)) {
-    case 8: return launch_c1<NDIM, 8>(a, tm, sms, s);
-    case 4: return launch_c1<NDIM, 4>(a, tm, sms, s);
-    default: return launch_c1<NDIM, 1>(a, nullptr, sms, s);
+    case 8: return launch_c1<NDIM, 8>(a, tm, sms, pdl, s);
+    case 4: return launch_c1<NDIM, 4>(a, tm, sms, pdl, s);
+    default: return launch_c1<NDIM, 1>(a, nullptr, sms, pdl, s);
   }
 }
 
@@ -227,10 +232,10 @@ bool compress_uses_tma(int ndim, const CompressArgs &a) {
 }
 
 cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *tm, int sms,
-                            cudaStream_t s) {
-  if (ndim == 3) return launch_c0<3>(a, tm, sms, s);
-  if (ndim == 2) return launch_c0<2>(a, tm, sms, s);
-  return launch_c0<1>(a, nullptr, sms, s);
+                            cudaStream_t s, bool after_range) {
+  if (ndim == 3) return launch_c0<3>(a, tm, sms, after_range, s);
+  if (ndim == 2) return launch_c0<2>(a, tm, sms, after_range, s);
+  return launch_c0<1>(a, nullptr, sms, after_range, s);
 }
 
 template <int NDIM>

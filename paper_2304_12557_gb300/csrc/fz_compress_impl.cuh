@@ -39,15 +39,18 @@ namespace fz {
 // and for 1-D fields, straight from global memory.
 
 constexpr int kCompWarps = 14;                  // compute warps per block
+static_assert(kCompWarps == kCompressUnitTiles, "a look-back unit is one tile per compute warp");
 constexpr int kCompThreads = 32 * (kCompWarps + 1);   // + the scan warp
 constexpr int kRing = 4;                        // rounds in flight per block
-// A warp stores a tile's compacted blocks defer_rounds() rounds after
-// computing it, so that the scan warp has that long to resolve the tile's
-// prefix.  The tile's bit planes wait in one of plane_bufs() plane buffers.
-// With no deferral the single buffer is drained (the previous tile's blocks
-// stored) right before the next tile's planes are written, so the prefix
-// still has most of a round's time.  A batch keeps each warp's field
-// arguments in shared memory as well and has room for one buffer only.
+// A warp stores a tile's compacted blocks after computing later tiles, so
+// that the scan warp has time to resolve the tile's prefix; the tile's bit
+// planes wait in one of plane_bufs() plane buffers.  Each buffer is drained
+// (the tile that last used it stored) right before the next tile's planes
+// are written into it: with defer_rounds() = 1 (two buffers) a tile of
+// round r is stored in round r + 2, before that round's planes, so its
+// prefix has one and a half rounds to arrive; with no deferral (one buffer)
+// about half a round.  A batch keeps each warp's field arguments in shared
+// memory as well and has room for one buffer only.
 template <bool BATCH>
 __host__ __device__ constexpr int defer_rounds() { return BATCH ? 0 : 1; }
 template <bool BATCH>
@@ -358,6 +361,158 @@ __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q
   }
 }
 
+// ---- the compute path's residuals in fp32 (2-D and 3-D) ----------------
+// The biased quantised values Q = fl(fl(x * r) + 1.5 * 2^23) are integers in
+// [2^23 + 1, 2^24 - 1] (|q| <= 2^22 - 1), exact as floats, and so are their
+// Lorenzo differences while a result stays within 2^24 in magnitude: a first
+// difference is below 2^23, a second below 2^24.  A third (3-D) may round
+// only beyond 2^24, where the residual is an escape either way (the escape
+// path recomputes such a tile in integers).  Pairs of x-neighbours go through
+// the packed f32x2 pipe: the multiply and the differences.  The rounding add
+// stays scalar: a paired multiply followed by a paired add is contracted into
+// one fused multiply-add by this toolchain, even with explicit .rn, which
+// rounds the exact product instead of fl(x * r) and changes q where fl(x * r)
+// falls on a tie.
+__device__ __forceinline__ float2 quant_pair(float x0, float x1, float r) {
+  float p0, p1;
+  asm("{\n .reg .b64 xa, ra, pa;\n mov.b64 xa, {%2, %3};\n mov.b64 ra, {%4, %4};\n"
+      " mul.rn.f32x2 pa, xa, ra;\n mov.b64 {%0, %1}, pa;\n}"
+      : "=f"(p0), "=f"(p1)
+      : "f"(x0), "f"(x1), "f"(r));
+  return make_float2(__fadd_rn(p0, kRoundMagic), __fadd_rn(p1, kRoundMagic));
+}
+__device__ __forceinline__ float2 sub_pair(float2 a, float2 b) {   // a - b, one rounding
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+template <bool CHECK>
+__device__ __forceinline__ void check_pair(float2 Q, uint32_t &qmax) {
+  if (CHECK)
+    qmax = max(qmax, max(__float_as_uint(Q.x) - kBiasBits, __float_as_uint(Q.y) - kBiasBits));
+}
+
+// Part 1 in fp32: pre-quantisation and the first difference (3-D: D_z
+// against the preloaded plane hf; 2-D: D_y, with the row above the brick
+// from the lane above or, for by == 0, from hf).  v[i] holds codes 2i, 2i+1.
+template <int NDIM, bool CHECK, class Src>
+__device__ __forceinline__ void residuals_first_f(const Src &src, const TileGeo &q, float r,
+                                                  const float (&hf)[32], float2 (&v)[32],
+                                                  uint32_t &qmax) {
+  const unsigned full = 0xffffffffu;
+  if constexpr (NDIM == 3) {
+#pragma unroll
+    for (int iy = 0; iy < 4; ++iy) {
+      float p0[8], p1[8];
+      src.row(0, iy, 0, p0);
+      src.row(1, iy, 0, p1);
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        const float2 q0 = quant_pair(p0[k], p0[k + 1], r);
+        const float2 q1 = quant_pair(p1[k], p1[k + 1], r);
+        const float2 qh = quant_pair(hf[8 * iy + k], hf[8 * iy + k + 1], r);  // hf = 0: q = 0
+        check_pair<CHECK>(q0, qmax);
+        check_pair<CHECK>(q1, qmax);
+        v[(8 * iy + k) / 2] = sub_pair(q0, qh);
+        v[(32 + 8 * iy + k) / 2] = sub_pair(q1, q0);
+      }
+    }
+  } else {
+    static_assert(NDIM == 2, "fp32 residuals: 2-D and 3-D");
+#pragma unroll
+    for (int row = 0; row < 8; ++row) {
+      float f8[8];
+      src.row(0, row, 0, f8);
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        v[(8 * row + k) / 2] = quant_pair(f8[k], f8[k + 1], r);
+        check_pair<CHECK>(v[(8 * row + k) / 2], qmax);
+      }
+    }
+#pragma unroll
+    for (int ix = 0; ix < 8; ix += 2) {            // D_y
+      float2 up;
+      up.x = __shfl_up_sync(full, v[(ix + 56) / 2].x, 8);
+      up.y = __shfl_up_sync(full, v[(ix + 56) / 2].y, 8);
+      if (q.by == 0) up = quant_pair(hf[ix], hf[ix + 1], r);   // hf = 0 when t == 0: q = 0
+#pragma unroll
+      for (int iy = 7; iy >= 1; --iy)
+        v[(ix + 8 * iy) / 2] = sub_pair(v[(ix + 8 * iy) / 2], v[(ix + 8 * (iy - 1)) / 2]);
+      v[ix / 2] = sub_pair(v[ix / 2], up);
+    }
+  }
+}
+
+// Part 2 in fp32: the remaining differences (3-D: D_y, then D_x; 2-D: D_x).
+template <int NDIM>
+__device__ __forceinline__ void residuals_rest_f(const TileGeo &q, float2 (&v)[32]) {
+  const unsigned full = 0xffffffffu;
+  if constexpr (NDIM == 3) {
+#pragma unroll
+    for (int iz = 0; iz < 2; ++iz) {               // D_y
+#pragma unroll
+      for (int ix = 0; ix < 8; ix += 2) {
+        float2 up;
+        up.x = __shfl_up_sync(full, v[(ix + 24 + 32 * iz) / 2].x, 4);
+        up.y = __shfl_up_sync(full, v[(ix + 24 + 32 * iz) / 2].y, 4);
+        if (q.by == 0) up = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int iy = 3; iy >= 1; --iy)
+          v[(ix + 8 * iy + 32 * iz) / 2] =
+              sub_pair(v[(ix + 8 * iy + 32 * iz) / 2], v[(ix + 8 * (iy - 1) + 32 * iz) / 2]);
+        v[(ix + 32 * iz) / 2] = sub_pair(v[(ix + 32 * iz) / 2], up);
+      }
+    }
+  }
+#pragma unroll
+  for (int row = 0; row < 8; ++row) {              // D_x: element 2j+1 - 2j, 2j - (2j-1)
+    float left = __shfl_up_sync(full, v[4 * row + 3].y, 1);
+    if (q.bx == 0) left = 0.f;
+#pragma unroll
+    for (int j = 3; j >= 1; --j) {
+      v[4 * row + j].y = __fsub_rn(v[4 * row + j].y, v[4 * row + j].x);
+      v[4 * row + j].x = __fsub_rn(v[4 * row + j].x, v[4 * row + j - 1].y);
+    }
+    v[4 * row].y = __fsub_rn(v[4 * row].y, v[4 * row].x);
+    v[4 * row].x = __fsub_rn(v[4 * row].x, left);
+  }
+}
+
+// Pairs of 16-bit sign-magnitude codes (Sec. 3.2) from exact float
+// residuals: the low 16 bits of |d| + 2^23 are |d| for |d| < 2^16, the sign
+// is the float's (a difference of equal values is +0, never -0).  Returns
+// the OR of the bits of |d| + 2^23: within 0x4B00007F when every |d| < 128,
+// within 0x4B007FFF when no residual escapes.
+__device__ __forceinline__ uint32_t pack_codes_f(const float2 (&v)[32], uint32_t (&w)[32]) {
+  uint32_t o = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const uint32_t m0 = __float_as_uint(__fadd_rn(fabsf(v[i].x), 8388608.0f));
+    const uint32_t m1 = __float_as_uint(__fadd_rn(fabsf(v[i].y), 8388608.0f));
+    o |= m0 | m1;
+    const uint32_t mag = byte_perm(m0, m1, 0x5410);
+    const uint32_t sgn = byte_perm(__float_as_uint(v[i].x), __float_as_uint(v[i].y), 0x7030);
+    w[i] = mag | (sgn & 0x80008000u);
+  }
+  return o;
+}
+
+// residual 0 (code 0) for the padding positions of a tile that reaches
+// past the field
+template <int NDIM>
+__device__ __forceinline__ void mask_padding(const CompressArgs &a, const TileGeo &q,
+                                             float2 (&v)[32]) {
+  using G = Geo<NDIM>;
+  const uint64_t lx = q.x0 < a.dims[0] ? a.dims[0] - q.x0 : 0;
+  const uint64_t ly = q.y0 < a.dims[1] ? a.dims[1] - q.y0 : 0;
+  const uint64_t lz = q.z0 < a.dims[2] ? a.dims[2] - q.z0 : 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int ix = (2 * i) % G::BX, iy = (2 * i / G::BX) % G::BY, iz = 2 * i / (G::BX * G::BY);
+    const bool row = (uint64_t)iy < ly && (uint64_t)iz < lz;
+    if (!(row && (uint64_t)ix < lx)) v[i].x = 0.f;
+    if (!(row && (uint64_t)ix + 1 < lx)) v[i].y = 0.f;
+  }
+}
+
 // Part 2: the remaining differences (no more input reads) and code 0 for
 // padding positions.
 template <int NDIM>
@@ -612,12 +767,6 @@ __device__ __forceinline__ void scan_warp(const CompressArgs &a0, const BatchArg
       if (g == 0) atomicOr(&cur->err, kErrTimeout);
       break;
     }
-    // The ticket for round r + 2 is taken once this block has finished
-    // round r: the later units are handed out, the closer their order is
-    // to the order in which blocks finish them, and the less a look-back
-    // waits for a predecessor's aggregate.  (Taken earlier, or by a compute
-    // warp at the start of a round, the compressor ran 1 to 6% slower.)
-    if (g == 0) post_ticket<BATCH>(a0, b, sh, r + 2, n_units);
     const uint64_t t_agg = g < kCompWarps ? sh->slot[s].agg[g] : 0;
     uint64_t inc = t_agg;
 #pragma unroll
@@ -628,6 +777,14 @@ __device__ __forceinline__ void scan_warp(const CompressArgs &a0, const BatchArg
     const uint64_t total = __shfl_sync(full, inc, 31);
     const bool publish = ul != skip_unit;
     publish_aggregate(a.status_cur, ul, total, publish);
+    // The ticket for round r + 2 is taken once this block has finished
+    // round r (and published the round's aggregate, which later units' look-
+    // backs wait for): the later units are handed out, the closer their
+    // order is to the order in which blocks finish them, and the less a
+    // look-back waits for a predecessor's aggregate.  (Taken earlier, or by
+    // a compute warp at the start of a round, the compressor ran 1 to 6%
+    // slower; taken before the publication, 1% slower.)
+    if (g == 0) post_ticket<BATCH>(a0, b, sh, r + 2, n_units);
     // 4 words per lane: a window of 128 units per round trip
     const uint64_t excl =
         resolve_prefix<4>(a.status_cur, ul, total, publish, &cur->err, a.wait_limit_ns);
@@ -650,6 +807,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const unsigned full = 0xffffffffu;
   const int g = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  grid_dependency_wait();                // a preceding range pass's result
   constexpr int kDef = defer_rounds<BATCH>(), kBufs = plane_bufs<BATCH>();
   // per compute warp: [TMA box 8 KB] (TMA only) [plane buffers]; then the
   // block's CompShared; then (batches) one WarpField per compute warp
@@ -785,7 +943,9 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       // a batch's TMA fields have 16-byte aligned rows: vector halo loads
       if (BATCH && V < 4 && tma_of(cw)) load_halo<NDIM, 4>(a, q, hf);
       else load_halo<NDIM, V>(a, q, hf);
-      int32_t v[64];
+      constexpr bool kF = NDIM >= 2;                // fp32 residuals
+      int32_t v[kF ? 1 : 64];
+      float2 vf[kF ? 32 : 1];
       uint32_t qmax = 0;
       // a single field's launch compiles one load path; a batch picks per field
       const bool use_box = BATCH ? tma_of(cw) : TMA;
@@ -793,34 +953,51 @@ __global__ void __launch_bounds__(kCompThreads, 1)
         if (!mbar_wait_bounded(bar, phase, a0.wait_limit_ns) && g == 0)
           atomicOr(&cur->err, kErrTimeout);
         phase ^= 1u;
-        residuals_first<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, g, rt.p.ebx2_r, hf, v,
-                                     qmax);
+        if constexpr (kF)
+          residuals_first_f<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, rt.p.ebx2_r, hf, vf,
+                                         qmax);
+        else
+          residuals_first<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, g, rt.p.ebx2_r, hf, v,
+                                       qmax);
         __syncwarp();                    // every lane is done with the box
       } else {
-        residuals_first<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, g, rt.p.ebx2_r, hf, v, qmax);
+        if constexpr (kF)
+          residuals_first_f<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, rt.p.ebx2_r, hf, vf, qmax);
+        else
+          residuals_first<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, g, rt.p.ebx2_r, hf, v, qmax);
       }
       // the box is free: fetch the next round's tile into it while this one
       // is finished
       next_unit();
       if (g == 0 && tma_of(nw)) issue(nw);
-      residuals_rest<NDIM>(a, q, g, rt.p.ebx2_r, v);
+      if constexpr (kF) residuals_rest_f<NDIM>(q, vf);
+      else residuals_rest<NDIM>(a, q, g, rt.p.ebx2_r, v);
       if (CHECK && __any_sync(full, qmax > kBiasedMax) && g == 0) atomicOr(&cur->err, kErrRange);
 
       uint32_t w[32];
-      const uint32_t orabs = pack_codes(v, w);       // v is dead from here on
-      // every code of the tile fits in 7 bits and the sign: the planes of
-      // magnitude bits 7..14 are zero and half the transpose is skipped
-      const bool narrow = !__any_sync(full, orabs > 127u);
-      if constexpr (kDef == 0) {
-        // drain the single plane buffer before anything below writes it
-        if (prev1.T != kNoTile) {
-          const CompressArgs &a1 = BATCH ? b.fields[prev1.field] : a0;
-          finish_tile<NDIM>(a1, sh, prev1, pb_of(prev1), rt_of(prev1.field), g, wid);
-          prev1.T = kNoTile;
-        }
+      // narrow: every code of the tile fits in 7 bits and the sign, so the
+      // planes of magnitude bits 7..14 are zero and half the transpose is
+      // skipped; escape: some |residual| needs more than 15 bits
+      bool narrow, escape;
+      if constexpr (kF) {
+        if (q.edge) mask_padding<NDIM>(a, q, vf);
+        const uint32_t o = pack_codes_f(vf, w);      // vf is dead from here on
+        narrow = !__any_sync(full, (o & ~0x4B00007Fu) != 0u);
+        escape = __any_sync(full, (o & ~0x4B007FFFu) != 0u);
+      } else {
+        const uint32_t orabs = pack_codes(v, w);     // v is dead from here on
+        narrow = !__any_sync(full, orabs > 127u);
+        escape = __any_sync(full, (orabs >> 15) != 0u);
+      }
+      // drain this round's plane buffer before anything below writes it
+      Pending &drain = kDef == 0 ? prev1 : prev2;
+      if (drain.T != kNoTile) {
+        const CompressArgs &a1 = BATCH ? b.fields[drain.field] : a0;
+        finish_tile<NDIM>(a1, sh, drain, pb_of(drain), rt_of(drain.field), g, wid);
+        drain.T = kNoTile;
       }
       uint32_t nout_lane = 0;
-      if (!narrow && __any_sync(full, (orabs >> 15) != 0)) {
+      if (!narrow && escape) {
         // rare: some |residual| needs more than 15 bits; recompute and repack
         // with escapes out of line (through this round's plane buffer)
         nout_lane = escape_repack<NDIM, V>(a, T, g, rt.p.ebx2_r, pb);
@@ -873,14 +1050,15 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       sh->slot[s].agg[wid] = agg;
       mbar_arrive(&sh->agg_bar[s]);
     }
-    // the oldest pending tile's prefix has had kDef tiles' time to settle
-    // (kDef = 0: prev1 is still pending only if this round ran no tile)
-    Pending &old = kDef == 2 ? prev2 : prev1;
+    // a round without a tile drained nothing: store the tile that would
+    // have been drained now, so that at most kDef tiles stay pending
+    Pending &old = kDef == 0 ? prev1 : prev2;
     if (old.T != kNoTile) {
       const CompressArgs &a = BATCH ? b.fields[old.field] : a0;
       finish_tile<NDIM>(a, sh, old, pb_of(old), rt_of(old.field), g, wid);
+      old.T = kNoTile;
     }
-    if constexpr (kDef == 2) prev2 = prev1;
+    if constexpr (kDef == 1) prev2 = prev1;
     prev1 = Pending{cw.run ? (uint32_t)T : kNoTile, BATCH ? cw.field : 0u, agg, F, P, r};
     cw = nw;
   }

@@ -589,16 +589,19 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
   if (__any_sync(full, oob || bad != 0) && g == 0) atomicOr(&cur->err, kErrCorrupt);
 }
 
-// Offsets pass: each block owns a unit of kOffChunks consecutive chunks
-// (ticketed in order), one chunk per thread: it counts the chunk's non-zero
-// blocks from its 128 flag bytes, scans the counts over the block and takes
-// the unit's offset by decoupled look-back, then writes every chunk's first
-// payload block and, with outliers, its first outlier record.  It also
-// validates the header and prepares the next call's scratch.
+// Offsets pass: blocks take units of kOffChunks consecutive chunks from a
+// ticket counter (in stream order, as many as the grid holds at once), one
+// chunk per thread: a block counts each chunk's non-zero blocks from its 128
+// flag bytes, scans the counts over the block and takes the unit's offset by
+// decoupled look-back, then writes every chunk's first payload block and,
+// with outliers, its first outlier record.  Block 0 also validates the
+// header and prepares the next call's scratch.  A unit's predecessors were
+// ticketed earlier to blocks that are running, so every look-back ends.
 __global__ void __launch_bounds__(kOffChunks) dec_offsets_kernel(const DecompressArgs a) {
   const unsigned full = 0xffffffffu;
   __shared__ uint32_t warp_tot[kOffChunks / 32];
   __shared__ uint64_t s_unit, s_excl;
+  grid_launch_dependents();              // the decompressor may be scheduled now
   SetScratch *cur = a.set_cur;
   const int g = threadIdx.x & 31, w = threadIdx.x >> 5;
   const Hdr h = read_header(a);
@@ -614,57 +617,58 @@ __global__ void __launch_bounds__(kOffChunks) dec_offsets_kernel(const Decompres
   }
   if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
   const uint64_t n_units = cdiv(h.n_chunks, kOffChunks);
-  if (threadIdx.x == 0) s_unit = atomicAdd(&cur->ticket, 1u);
-  __syncthreads();
-  const uint64_t u = s_unit;
-  if (u >= n_units) return;                          // the same in the whole block
-  const uint64_t c = u * kOffChunks + threadIdx.x;
-  uint32_t cnt = 0;
-  if (c < h.n_chunks) {
-    const uint4 *f = reinterpret_cast<const uint4 *>(a.in + 64 + 128 * c);
+  const uint2 *recs = reinterpret_cast<const uint2 *>(a.in + 64 + 32 * h.n_tiles + 16 * h.nnz);
+  while (true) {
+    if (threadIdx.x == 0) s_unit = atomicAdd(&cur->ticket, 1u);
+    __syncthreads();
+    const uint64_t u = s_unit;
+    if (u >= n_units) return;                        // the same in the whole block
+    const uint64_t c = u * kOffChunks + threadIdx.x;
+    uint32_t cnt = 0;
+    if (c < h.n_chunks) {
+      const uint4 *f = reinterpret_cast<const uint4 *>(a.in + 64 + 128 * c);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const uint4 v = __ldg(f + i);
-      cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+      for (int i = 0; i < 8; ++i) {
+        const uint4 v = __ldg(f + i);
+        cnt += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+      }
     }
-  }
-  uint32_t inc = cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(full, inc, o);
-    if (g >= o) inc += y;
-  }
-  if (g == 31) warp_tot[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    // the unit's total, its look-back, and the warps' exclusive offsets
-    const uint32_t t = g < kOffChunks / 32 ? warp_tot[g] : 0u;
-    uint32_t ti = t;
+    uint32_t inc = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(full, ti, o);
-      if (g >= o) ti += y;
+      const uint32_t y = __shfl_up_sync(full, inc, o);
+      if (g >= o) inc += y;
     }
-    const uint32_t total = __shfl_sync(full, ti, 31);
-    const bool publish = a.skip_publish_chunk >= h.n_chunks ||
-                         u != a.skip_publish_chunk / kOffChunks;
-    const uint64_t excl = lookback(a.status_cur, u, total, publish, &cur->err, a.wait_limit_ns);
-    if (g < kOffChunks / 32) warp_tot[g] = ti - t;
-    if (g == 0) {
-      s_excl = excl;
-      a.status_next[u * kStatusStride] = 0;            // for the next call
-      if (u == n_units - 1 && excl + total != h.nnz) atomicOr(&cur->err, kErrCorrupt);
+    if (g == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      // the unit's total, its look-back, and the warps' exclusive offsets
+      const uint32_t t = g < kOffChunks / 32 ? warp_tot[g] : 0u;
+      uint32_t ti = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(full, ti, o);
+        if (g >= o) ti += y;
+      }
+      const uint32_t total = __shfl_sync(full, ti, 31);
+      const bool publish = a.skip_publish_chunk >= h.n_chunks ||
+                           u != a.skip_publish_chunk / kOffChunks;
+      const uint64_t excl = lookback(a.status_cur, u, total, publish, &cur->err, a.wait_limit_ns);
+      if (g < kOffChunks / 32) warp_tot[g] = ti - t;
+      if (g == 0) {
+        s_excl = excl;
+        a.status_next[u * kStatusStride] = 0;          // for the next call
+        if (u == n_units - 1 && excl + total != h.nnz) atomicOr(&cur->err, kErrCorrupt);
+      }
     }
-  }
-  __syncthreads();
-  if (c < h.n_chunks) {
-    const uint64_t off = s_excl + warp_tot[w] + inc - cnt;
-    if (off + cnt > h.nnz) atomicOr(&cur->err, kErrCorrupt);
-    a.chunk_off[c] = (uint32_t)off;
-    if (h.nout) {
-      const uint2 *recs = reinterpret_cast<const uint2 *>(a.in + 64 + 32 * h.n_tiles + 16 * h.nnz);
-      a.chunk_olo[c] = (uint32_t)lower_bound_rec(recs, h.nout, (uint32_t)(c * kChunkCodes));
+    __syncthreads();
+    if (c < h.n_chunks) {
+      const uint64_t off = s_excl + warp_tot[w] + inc - cnt;
+      if (off + cnt > h.nnz) atomicOr(&cur->err, kErrCorrupt);
+      a.chunk_off[c] = (uint32_t)off;
+      if (h.nout) a.chunk_olo[c] = (uint32_t)lower_bound_rec(recs, h.nout, (uint32_t)(c * kChunkCodes));
     }
+    __syncthreads();                                 // s_unit, s_excl, warp_tot reused
   }
 }
 
@@ -675,23 +679,35 @@ __global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const Dec
   const Hdr h = read_header(a);
   if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
   uint32_t *pbuf = dsmem + w * (kDecWarpSmem / 4);
+  grid_dependency_wait();                // the offsets pass's chunk offsets
   if (h.ndim == 3) decompress_chunks<3>(a, h, pbuf, cur);
   else if (h.ndim == 2) decompress_chunks<2>(a, h, pbuf, cur);
   else decompress_chunks<1>(a, h, pbuf, cur);
 }
 
-cudaError_t launch_dec_offsets(const DecompressArgs &a, uint64_t max_chunks, cudaStream_t s) {
-  const uint64_t blocks = (max_chunks + kOffChunks - 1) / kOffChunks;
+// The grid: enough blocks for max_chunks chunks, at most two per SM (the
+// blocks loop over their tickets).
+cudaError_t launch_dec_offsets(const DecompressArgs &a, uint64_t max_chunks, int sms,
+                               cudaStream_t s) {
+  if (sms < 1) sms = 1;
+  uint64_t blocks = (max_chunks + kOffChunks - 1) / kOffChunks;
+  if (blocks > (uint64_t)sms * 2) blocks = (uint64_t)sms * 2;
   dec_offsets_kernel<<<(unsigned)(blocks ? blocks : 1), kOffChunks, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s) {
-  const cudaError_t e = cudaFuncSetAttribute(
-      decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecSmemBytes);
-  if (e != cudaSuccess) return e;
-  decompress_kernel<<<grid, kDecWarps * 32, kDecSmemBytes, s>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kDecWarps * 32);
+  cfg.dynamicSmemBytes = kDecSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, decompress_kernel, a);
 }
 
 int decompress_blocks_per_sm() {

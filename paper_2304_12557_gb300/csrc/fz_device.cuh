@@ -231,6 +231,18 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Programmatic dependent launch: a kernel that another kernel follows on
+// its stream lets that grid be scheduled as soon as every one of its own
+// blocks has started; the following kernel waits for this grid's completion
+// (and its memory) before it reads what this grid wrote.  Without a
+// programmatic dependency both are no-ops.
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // 128-byte swizzle of a box row of 32 floats: 16-byte chunk c of row r sits
 // at chunk position c ^ (r % 8) (the TMA SWIZZLE_128B layout for a
 // 1024-byte aligned box).

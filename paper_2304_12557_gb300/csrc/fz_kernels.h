@@ -63,16 +63,29 @@ void launch_range(const float *x, uint64_t n, float2 *partial, int nblocks,
 // passes a tensor map from encode_field_tmap.
 bool compress_uses_tma(int ndim, const CompressArgs &a);
 bool encode_field_tmap(int ndim, const uint64_t dims[3], const float *x, CUtensorMap *tm);
+// Tiles per look-back unit of a single-field compression (the compression
+// kernel's compute warps per block; fz_compress_impl.cuh checks the two agree).
+constexpr uint64_t kCompressUnitTiles = 14;
 // look-back status words (one per unit of consecutive tiles) a compression
 // of n_tiles tiles uses and clears in the other set
-uint64_t compress_status_words(uint64_t n_tiles);
+constexpr uint64_t compress_status_words(uint64_t n_tiles) {
+  return (n_tiles + kCompressUnitTiles - 1) / kCompressUnitTiles;
+}
+// after_range: the launch directly follows launch_range on stream s; the
+// compressor is then scheduled while the range pass finishes and waits for
+// its result on the device (programmatic dependent launch)
 cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *tm, int sms,
-                            cudaStream_t s);
+                            cudaStream_t s, bool after_range = false);
 cudaError_t launch_outliers(int ndim, const CompressArgs &a, uint64_t out_section,
                             cudaStream_t s);
 // offsets pass (header check, per-chunk payload and outlier offsets) over
-// at most max_chunks chunks, then the decompression proper
-cudaError_t launch_dec_offsets(const DecompressArgs &a, uint64_t max_chunks, cudaStream_t s);
+// at most max_chunks chunks on a grid of at most 2 * sms blocks, then the
+// decompression proper, which may be scheduled while the offsets pass
+// finishes (it waits for the pass's results on the device).  The kernel's
+// shared-memory attribute is set by decompress_blocks_per_sm(), which a
+// context or server calls on its device before its first launch.
+cudaError_t launch_dec_offsets(const DecompressArgs &a, uint64_t max_chunks, int sms,
+                               cudaStream_t s);
 cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s);
 // look-back status words the offsets pass uses and clears in the other set
 uint64_t decompress_status_words(uint64_t n_chunks);
@@ -85,9 +98,11 @@ struct StagedScratch {
   uint64_t *tile_excl;         // per tile: exclusive (blocks << 32 | escapes)
   uint64_t *status;            // look-back words of the scan (zero at launch)
 };
-// ev (may be NULL): 5 events recorded before, between and after the 4 kernels
+// ballot: the bitshuffle step by warp ballots (Listing 1) instead of the
+// register transpose; ev (may be NULL): 5 events recorded before, between
+// and after the 4 kernels
 cudaError_t launch_staged(int ndim, const CompressArgs &a, const StagedScratch &w, int sms,
-                          cudaEvent_t *ev, cudaStream_t s);
+                          bool ballot, cudaEvent_t *ev, cudaStream_t s);
 uint64_t staged_status_words(uint64_t n_tiles);
 
 // concatenation of slab streams (fz_shard.cu)

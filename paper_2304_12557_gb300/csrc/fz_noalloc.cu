@@ -27,6 +27,8 @@
 namespace {
 
 constexpr uint64_t kMaxTiles = FZ_NOALLOC_MAX_CODES / fz::kTileCodes;
+// look-back words per set: one per unit of consecutive tiles
+constexpr uint64_t kMaxUnits = fz::compress_status_words(kMaxTiles);
 constexpr int kRangeBlocks = 1216;
 constexpr int kMaxDevices = 64;
 
@@ -36,13 +38,15 @@ struct NoAllocScratch {
   fz::RangeResult range;                  // min/max/non-finite + counter
   uint32_t pad[12];
   float2 partial[kRangeBlocks];           // per-block range partials
-  uint64_t status[2][kMaxTiles * fz::kStatusStride];  // look-back words (set 1 is only
+  uint64_t status[2][kMaxUnits * fz::kStatusStride];  // look-back words (set 1 is only
                                           // ever written with zeros)
   uint32_t out_prefix[kMaxTiles];
   uint32_t out_count[kMaxTiles];
 };
 static_assert(offsetof(NoAllocScratch, partial) % 64 == 0, "alignment");
 static_assert(offsetof(NoAllocScratch, status) % 64 == 0, "alignment");
+// the size the public header states (FZ_NOALLOC_SCRATCH_BYTES)
+static_assert(sizeof(NoAllocScratch) <= FZ_NOALLOC_SCRATCH_BYTES, "scratch size as documented");
 
 }  // namespace
 
@@ -125,8 +129,9 @@ extern "C" int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], in
 
   // the array keeps the previous call's contents: clear what must start at 0
   // (both result blocks, the range counter, this field's look-back words)
+  const uint64_t units = fz::compress_status_words(n_tiles);
   if (cudaMemsetAsync(sc, 0, offsetof(NoAllocScratch, partial), s) != cudaSuccess ||
-      cudaMemsetAsync(sc->status[0], 0, n_tiles * fz::kStatusStride * sizeof(uint64_t), s) !=
+      cudaMemsetAsync(sc->status[0], 0, units * fz::kStatusStride * sizeof(uint64_t), s) !=
           cudaSuccess)
     return FZ_ERR_CUDA;
   if (mode == FZ_EB_REL) {
@@ -159,7 +164,8 @@ extern "C" int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], in
   CUtensorMap tm;
   std::memset(&tm, 0, sizeof(tm));
   const bool tma = fz::compress_uses_tma(ndim, a) && fz::encode_field_tmap(ndim, d, d_in, &tm);
-  if (fz::launch_compress(ndim, a, tma ? &tm : nullptr, sms, s) != cudaSuccess)
+  if (fz::launch_compress(ndim, a, tma ? &tm : nullptr, sms, s, mode == FZ_EB_REL) !=
+      cudaSuccess)
     return FZ_ERR_CUDA;
   fz::SetScratch r;
   int st = read_result(&sc->sets[0], &r, s);

@@ -9,10 +9,13 @@
 //                for the request's input, output and scratch;
 //   uploads      host -> pool copies of the admitted inputs (upload stream);
 //   compression  every admitted compress request joins the next batched
-//                launch (fz_batch_ws.h); two workspaces alternate, so the
-//                next batch is formed and queued while the previous one runs;
-//   decompression admitted streams, each with its own scratch, on a second
+//                launch (fz_batch_ws.h); two workspaces alternate, each on
+//                its own stream, so the next batch is formed, queued and
+//                started on the device while the previous one runs;
+//   decompression admitted streams, each with its own scratch, on a third
 //                stream: its kernels fill the device beside the batches.
+// CUDA events around every batch and decompression, against one recorded
+// at start-up, give each request's device interval (fz_server_request_info).
 // Every request's result is computed exactly as the single calls compute it
 // (the batch keeps one look-back domain per field; a decompression has its
 // own scratch), so it does not depend on what else is in flight.
@@ -116,11 +119,14 @@ struct Req {
   // decompress
   uint64_t n_elems = 0, n_chunks = 0, max_chunks = 0;
   int slot = -1;                   // pinned result slot
-  cudaEvent_t ev_done = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_done = nullptr;
   // result
   int status = FZ_OK;
   uint64_t size = 0;
   Clock::time_point t_submit, t_done;
+  // where the time went (fz_server_request_info)
+  uint64_t batch = 0, launch_seq = 0;
+  double admit_ms = -1.0, launch_ms = -1.0, gpu_start_ms = -1.0, gpu_end_ms = -1.0;
 };
 
 }  // namespace
@@ -129,12 +135,17 @@ struct fz_server {
   int device = 0;
   fz_ctx *ctx = nullptr;
   int max_batch = 256, max_dec = 8;
-  int dec_grid = 1;
+  int dec_grid = 1, num_sms = 1;
   Pool pool;
-  cudaStream_t s_up = nullptr, s_comp = nullptr, s_dec = nullptr, s_down = nullptr;
+  cudaStream_t s_up = nullptr, s_comp[2] = {nullptr, nullptr}, s_dec = nullptr, s_down = nullptr;
   fz::BatchWs ws[2];
   bool ws_busy[2] = {false, false};
-  cudaEvent_t ws_ev[2] = {nullptr, nullptr};
+  cudaEvent_t ws_ev[2] = {nullptr, nullptr};       // batch done (also its end time)
+  cudaEvent_t ws_start[2] = {nullptr, nullptr};    // batch start time
+  uint64_t ws_batch[2] = {0, 0};
+  cudaEvent_t ev_epoch = nullptr;                  // device time zero
+  Clock::time_point t_epoch = Clock::now();        // host time zero
+  uint64_t n_batches = 0, n_launches = 0;
   std::vector<uint64_t> ws_ids[2];
   int ws_next = 0;
   cudaEvent_t ev_uploads = nullptr;
@@ -160,6 +171,15 @@ uint64_t compress_out_cap(const Req &r, uint64_t tiles) {
   // rare: 64 KiB for them first, every code when that was not enough
   if (r.full_bound) return 64 + 32 * tiles + 4096 * tiles + 8ull * fz::kTileCodes * tiles;
   return 64 + 32 * tiles + 4096 * tiles + 65536;
+}
+
+double host_ms(const fz_server *S, Clock::time_point t) {
+  return std::chrono::duration<double, std::milli>(t - S->t_epoch).count();
+}
+double gpu_ms(const fz_server *S, cudaEvent_t e) {
+  float ms = -1.f;
+  if (!e || cudaEventElapsedTime(&ms, S->ev_epoch, e) != cudaSuccess) return -1.0;
+  return ms;
 }
 
 // pool memory a request needs; false when it can never fit
@@ -202,6 +222,7 @@ void admit(fz_server *S, std::vector<uint64_t> &uploads) {
     r.out_off = out;
     r.scratch_off = r.scratch_bytes ? scr : kNone;
     r.state = kAdmitted;
+    r.admit_ms = host_ms(S, Clock::now());
     (r.op == FZ_OP_COMPRESS ? S->adm_comp : S->adm_dec).push_back(r.id);
     uploads.push_back(r.id);
     it = S->queued.erase(it);
@@ -235,10 +256,13 @@ bool step(fz_server *S) {
     const uint32_t n = (uint32_t)S->ws_ids[w].size();
     std::vector<uint64_t> sizes(n);
     std::vector<int> sts(n);
-    S->ws[w].collect(S->ctx, sizes.data(), sts.data(), S->s_comp);
+    S->ws[w].collect(S->ctx, sizes.data(), sts.data(), S->s_comp[w]);
+    const double g0 = gpu_ms(S, S->ws_start[w]), g1 = gpu_ms(S, S->ws_ev[w]);
     std::lock_guard<std::mutex> lk(S->mu);
     for (uint32_t i = 0; i < n; ++i) {
       Req &r = S->reqs[S->ws_ids[w][i]];
+      r.gpu_start_ms = g0;
+      r.gpu_end_ms = g1;
       if (sts[i] == FZ_ERR_CAPACITY && !r.full_bound) {
         // escapes overflowed the first output: again with room for all of them
         S->pool.release(r.out_off, r.out_cap);
@@ -270,6 +294,8 @@ bool step(fz_server *S) {
       continue;
     }
     const fz::SetScratch res = S->h_slots[r.slot];
+    r.gpu_start_ms = gpu_ms(S, r.ev_start);
+    r.gpu_end_ms = gpu_ms(S, r.ev_done);
     int st = FZ_OK;
     if (res.err & fz::kErrTimeout) st = FZ_ERR_TIMEOUT;
     else if (res.err & fz::kErrCorrupt) st = FZ_ERR_CORRUPT;
@@ -311,8 +337,10 @@ bool step(fz_server *S) {
       S->adm_comp.erase(S->adm_comp.begin(), S->adm_comp.begin() + take);
     }
     std::vector<fz_field> fields(ids.size());
+    const uint64_t batch = ++S->n_batches, seq = ++S->n_launches;
     {
       std::lock_guard<std::mutex> lk(S->mu);
+      const double now = host_ms(S, Clock::now());
       for (size_t i = 0; i < ids.size(); ++i) {
         Req &r = S->reqs[ids[i]];
         fz_field &f = fields[i];
@@ -324,18 +352,24 @@ bool step(fz_server *S) {
         f.d_out = S->pool.ptr(r.out_off);
         f.out_capacity = r.out_cap;
         r.state = kRunning;
+        r.batch = batch;
+        r.launch_seq = seq;
+        r.launch_ms = now;
       }
     }
-    cudaStreamWaitEvent(S->s_comp, S->ev_uploads, 0);
-    int st = S->ws[w].set(S->device, fields.data(), (int)fields.size(), S->s_comp);
-    if (st == FZ_OK) st = S->ws[w].enqueue(S->s_comp);
-    if (st == FZ_OK) cudaEventRecord(S->ws_ev[w], S->s_comp);
+    cudaStream_t sc = S->s_comp[w];
+    cudaStreamWaitEvent(sc, S->ev_uploads, 0);
+    int st = S->ws[w].set(S->device, fields.data(), (int)fields.size(), sc);
+    if (st == FZ_OK) st = cudaEventRecord(S->ws_start[w], sc) == cudaSuccess ? FZ_OK : FZ_ERR_CUDA;
+    if (st == FZ_OK) st = S->ws[w].enqueue(sc);
+    if (st == FZ_OK) cudaEventRecord(S->ws_ev[w], sc);
     if (st != FZ_OK) {
       std::lock_guard<std::mutex> lk(S->mu);
       for (uint64_t id : ids) finish(S, S->reqs[id], st, 0);
       continue;
     }
     S->ws_ids[w] = ids;
+    S->ws_batch[w] = batch;
     S->ws_busy[w] = true;
     S->ws_next = 1 - w;
     did = true;
@@ -353,6 +387,8 @@ bool step(fz_server *S) {
       S->free_slots.pop_back();
       rp->state = kRunning;
       rp->slot = slot;
+      rp->launch_seq = ++S->n_launches;
+      rp->launch_ms = host_ms(S, Clock::now());
     }
     Req &r = *rp;
     uint8_t *scr = S->pool.ptr(r.scratch_off);
@@ -373,8 +409,9 @@ bool step(fz_server *S) {
     a.wait_limit_ns = 2000000000ull;
     a.skip_publish_chunk = ~0ull;
     cudaStreamWaitEvent(S->s_dec, S->ev_uploads, 0);
+    cudaEventRecord(r.ev_start, S->s_dec);
     cudaMemsetAsync(scr, 0, 2 * sizeof(fz::SetScratch) + units * fz::kStatusStride * 8, S->s_dec);
-    fz::launch_dec_offsets(a, r.max_chunks, S->s_dec);
+    fz::launch_dec_offsets(a, r.max_chunks, S->num_sms, S->s_dec);
     fz::launch_decompress(a, S->dec_grid, S->s_dec);
     cudaMemcpyAsync(&S->h_slots[slot], a.set_cur, sizeof(fz::SetScratch), cudaMemcpyDeviceToHost,
                     S->s_dec);
@@ -427,19 +464,27 @@ int fz_server_create(int device, uint64_t pool_bytes, int max_batch, fz_server *
   bool ok = fz_create(&S->ctx, device) == FZ_OK && cudaSetDevice(device) == cudaSuccess &&
             S->pool.init(pool_bytes) &&
             cudaStreamCreateWithFlags(&S->s_up, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaStreamCreateWithFlags(&S->s_comp, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&S->s_comp[0], cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&S->s_comp[1], cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&S->s_dec, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&S->s_down, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&S->ev_uploads, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&S->ws_ev[0], cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&S->ws_ev[1], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreate(&S->ws_ev[0]) == cudaSuccess &&
+            cudaEventCreate(&S->ws_ev[1]) == cudaSuccess &&
+            cudaEventCreate(&S->ws_start[0]) == cudaSuccess &&
+            cudaEventCreate(&S->ws_start[1]) == cudaSuccess &&
+            cudaEventCreate(&S->ev_epoch) == cudaSuccess &&
             cudaMallocHost(&S->h_slots, S->max_dec * sizeof(fz::SetScratch)) == cudaSuccess;
   if (ok) {
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    S->num_sms = sms;
     S->dec_grid = sms * fz::decompress_blocks_per_sm();
     for (int i = 0; i < S->max_dec; ++i) S->free_slots.push_back(i);
     cudaEventRecord(S->ev_uploads, S->s_up);
+    cudaEventRecord(S->ev_epoch, S->s_up);
+    cudaEventSynchronize(S->ev_epoch);
+    S->t_epoch = Clock::now();
   }
   if (prev >= 0) cudaSetDevice(prev);
   if (!ok) {
@@ -462,15 +507,18 @@ void fz_server_destroy(fz_server *S) {
   int prev = -1;
   cudaGetDevice(&prev);
   cudaSetDevice(S->device);
-  for (cudaStream_t s : {S->s_up, S->s_comp, S->s_dec, S->s_down})
+  for (cudaStream_t s : {S->s_up, S->s_comp[0], S->s_comp[1], S->s_dec, S->s_down})
     if (s) cudaStreamSynchronize(s);
-  for (auto &kv : S->reqs)
+  for (auto &kv : S->reqs) {
     if (kv.second.ev_done) cudaEventDestroy(kv.second.ev_done);
+    if (kv.second.ev_start) cudaEventDestroy(kv.second.ev_start);
+  }
   S->ws[0].release();
   S->ws[1].release();
-  for (cudaStream_t s : {S->s_up, S->s_comp, S->s_dec, S->s_down})
+  for (cudaStream_t s : {S->s_up, S->s_comp[0], S->s_comp[1], S->s_dec, S->s_down})
     if (s) cudaStreamDestroy(s);
-  for (cudaEvent_t e : {S->ev_uploads, S->ws_ev[0], S->ws_ev[1]})
+  for (cudaEvent_t e : {S->ev_uploads, S->ws_ev[0], S->ws_ev[1], S->ws_start[0], S->ws_start[1],
+                        S->ev_epoch})
     if (e) cudaEventDestroy(e);
   if (S->h_slots) cudaFreeHost(S->h_slots);
   S->pool.destroy();
@@ -513,8 +561,10 @@ int fz_server_submit(fz_server *S, const fz_request *q, uint64_t *id) {
   std::lock_guard<std::mutex> lk(S->mu);
   if (!sizes_of(S, r)) return FZ_ERR_CAPACITY;     // larger than the whole pool
   if (r.op == FZ_OP_DECOMPRESS &&
-      cudaEventCreateWithFlags(&r.ev_done, cudaEventDisableTiming) != cudaSuccess)
+      (cudaEventCreate(&r.ev_done) != cudaSuccess || cudaEventCreate(&r.ev_start) != cudaSuccess)) {
+    if (r.ev_done) cudaEventDestroy(r.ev_done);
     return FZ_ERR_CUDA;
+  }
   r.id = S->next_id++;
   r.t_submit = Clock::now();
   S->reqs.emplace(r.id, r);
@@ -546,6 +596,7 @@ int fz_server_fetch(fz_server *S, uint64_t id, void *h_out, uint64_t capacity) {
     if (r.state != kDone) return FZ_PENDING;
     if (r.status != FZ_OK) {
       if (r.ev_done) cudaEventDestroy(r.ev_done);
+      if (r.ev_start) cudaEventDestroy(r.ev_start);
       S->reqs.erase(it);
       return FZ_ERR_ARG;
     }
@@ -568,9 +619,27 @@ int fz_server_fetch(fz_server *S, uint64_t id, void *h_out, uint64_t capacity) {
   Req &r = S->reqs[id];
   S->pool.release(r.out_off, r.out_cap);
   if (r.ev_done) cudaEventDestroy(r.ev_done);
+  if (r.ev_start) cudaEventDestroy(r.ev_start);
   S->reqs.erase(id);
   S->cv.notify_all();
   return st;
+}
+
+int fz_server_request_info(fz_server *S, uint64_t id, fz_request_info *info) {
+  if (!S || !info) return FZ_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end() || it->second.state == kFetched) return FZ_ERR_ARG;
+  const Req &r = it->second;
+  info->batch = r.batch;
+  info->launch_seq = r.launch_seq;
+  info->submit_ms = host_ms(S, r.t_submit);
+  info->admit_ms = r.admit_ms;
+  info->launch_ms = r.launch_ms;
+  info->done_ms = r.state == kDone ? host_ms(S, r.t_done) : -1.0;
+  info->gpu_start_ms = r.gpu_start_ms;
+  info->gpu_end_ms = r.gpu_end_ms;
+  return FZ_OK;
 }
 
 int fz_server_get_stats(fz_server *S, fz_server_stats *out, int reset) {

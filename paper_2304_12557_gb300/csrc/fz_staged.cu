@@ -7,7 +7,9 @@
 //                         (Sec. 3.2), written to HBM (4 KiB per tile)
 //  staged_shuffle_kernel  reads the codes, bitshuffles (Sec. 3.3) and marks
 //                         (Sec. 3.4, Listing 1): shuffled words to HBM, the
-//                         stream's flag bytes, each tile's block count
+//                         stream's flag bytes, each tile's block count; the
+//                         transpose is either the in-register one or, as in
+//                         Listing 1, 32 warp ballots per 32-word group
 //  staged_scan_kernel     exclusive scan of the tiles' (blocks, escapes)
 //                         counts (the paper's prefix sum)
 //  staged_encode_kernel   copies every tile's non-zero blocks to their place
@@ -95,6 +97,46 @@ __global__ void __launch_bounds__(kStagedWarps * 32)
     out[64 + T * 32 + g] = (uint8_t)F;   // Listing 1's flags
     const uint32_t cnt = __reduce_add_sync(full, (uint32_t)__popc(F));
     if (g == 0) tile_nnz[T] = cnt;
+  }
+}
+
+// The same step with Listing 1's bitshuffle.  A warp takes a tile's 32
+// groups one at a time, lane t holding word t of the group (one coalesced
+// 128-byte load); the ballot of bit b over the lanes is the group's plane-b
+// word, and lane b keeps it (plane b of group g is word 32b + g, the
+// columns-written reading of Listing 1).  After the 32 groups lane b holds
+// plane b's 32 words: it stores them (128 contiguous bytes) and takes its
+// flag byte from them (block j of the plane: words 4j..4j+3).  That is 32
+// ballots per group, about one warp instruction per code for the transpose
+// alone, against about four per 32 codes for transpose32.
+__global__ void __launch_bounds__(kStagedWarps * 32)
+    staged_shuffle_ballot_kernel(const uint32_t *codes, uint32_t *shuf, uint8_t *out,
+                                 uint32_t *tile_nnz, uint64_t n_tiles) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const uint64_t n_warps = (uint64_t)gridDim.x * kStagedWarps;
+  for (uint64_t T = blockIdx.x * (uint64_t)kStagedWarps + (threadIdx.x >> 5); T < n_tiles;
+       T += n_warps) {
+    uint32_t row[32];                    // lane b: plane b's word of every group
+#pragma unroll
+    for (int g = 0; g < 32; ++g) {
+      const uint32_t wd = __ldcg(codes + T * 1024 + 32 * g + lane);
+#pragma unroll
+      for (int b = 0; b < 32; ++b) {
+        const uint32_t m = __ballot_sync(full, (wd >> b) & 1u);
+        if (lane == b) row[g] = m;
+      }
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(shuf + T * 1024 + 32 * lane);
+    uint32_t F = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      __stcg(dst + j, make_uint4(row[4 * j], row[4 * j + 1], row[4 * j + 2], row[4 * j + 3]));
+      F |= ((row[4 * j] | row[4 * j + 1] | row[4 * j + 2] | row[4 * j + 3]) != 0u ? 1u : 0u) << j;
+    }
+    out[64 + T * 32 + lane] = (uint8_t)F;   // Listing 1's flags
+    const uint32_t cnt = __reduce_add_sync(full, (uint32_t)__popc(F));
+    if (lane == 0) tile_nnz[T] = cnt;
   }
 }
 
@@ -233,7 +275,7 @@ cudaError_t launch_quant_v(const CompressArgs &a, uint32_t *codes, int blocks, i
 }  // namespace
 
 cudaError_t launch_staged(int ndim, const CompressArgs &a, const StagedScratch &w, int sms,
-                          cudaEvent_t *ev, cudaStream_t s) {
+                          bool ballot, cudaEvent_t *ev, cudaStream_t s) {
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
   const uintptr_t p = reinterpret_cast<uintptr_t>(a.x);
   const int v = (a.dims[0] % 8 == 0 && p % 32 == 0) ? 8 : (a.dims[0] % 4 == 0 && p % 16 == 0) ? 4 : 1;
@@ -245,8 +287,12 @@ cudaError_t launch_staged(int ndim, const CompressArgs &a, const StagedScratch &
                   : launch_quant_v<1>(a, w.codes, blocks, v, s);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
-  staged_shuffle_kernel<<<blocks, kStagedWarps * 32, 0, s>>>(w.codes, w.shuf, a.out, w.tile_nnz,
-                                                              n_tiles);
+  if (ballot)
+    staged_shuffle_ballot_kernel<<<blocks, kStagedWarps * 32, 0, s>>>(w.codes, w.shuf, a.out,
+                                                                       w.tile_nnz, n_tiles);
+  else
+    staged_shuffle_kernel<<<blocks, kStagedWarps * 32, 0, s>>>(w.codes, w.shuf, a.out,
+                                                                w.tile_nnz, n_tiles);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
   const uint64_t units = (n_tiles + kScanTiles - 1) / kScanTiles;

@@ -1,9 +1,11 @@
 """GPU: the unfused kernel sequence (codes and shuffled words in HBM) gives
-byte for byte the fused kernel's stream, including escapes, unaligned
-inputs, ragged shapes and errors."""
+byte for byte the oracle's stream and the fused kernel's, with either
+bitshuffle (the register transpose or Listing 1's warp ballots), including
+escapes, unaligned inputs, ragged shapes and errors."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2304_12557_gb300 as fz
 from paper_2304_12557_gb300 import fields
 
@@ -49,7 +51,8 @@ CASES = [
 
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("offset", [0, 1])
-def test_staged_equals_fused(codec, torch, case, offset):
+@pytest.mark.parametrize("shuffle", ["register", "ballot"])
+def test_staged_equals_oracle_and_fused(codec, torch, case, offset, shuffle):
     make, mode, eb = CASES[case]
     x = np.ascontiguousarray(make(), dtype=np.float32)
     xt = torch.from_numpy(x).cuda()
@@ -60,8 +63,16 @@ def test_staged_equals_fused(codec, torch, case, offset):
     fused = codec.compress(xt, mode=mode, eb=eb, ndim=x.ndim).cpu().numpy().tobytes()
     out = torch.zeros(fz.compress_bound(list(x.shape[::-1]), x.ndim), dtype=torch.uint8,
                       device="cuda")
-    st, size, ms = codec.compress_staged_into(xt, out, mode, eb, x.ndim)
-    assert st == fz.OK and out[:size].cpu().numpy().tobytes() == fused
+    codec.set_staged_shuffle(shuffle)
+    try:
+        st, size, ms = codec.compress_staged_into(xt, out, mode, eb, x.ndim)
+    finally:
+        codec.set_staged_shuffle("register")
+    got = out[:size].cpu().numpy().tobytes()
+    ost, want = oracle.compress(x, x.ndim, oracle.EB_ABS if mode == "abs" else oracle.EB_REL, eb)
+    assert ost == oracle.OK
+    assert st == fz.OK and got == want
+    assert got == fused
     assert all(t >= 0 for t in ms) and ms[1] > 0
 
 
