@@ -1,10 +1,15 @@
 """GPU: the request server.  Compress and decompress requests of mixed sizes
 submitted all at once (so that later ones join batches while earlier ones
-run) and one at a time must give the same results, and the same as the
-single-field calls; admission waits for pool room; errors are per request."""
+run) and one at a time must give the same results, equal to the oracle's;
+requests that arrive while a batch runs join a later batch and are in
+flight on the device beside it; admission waits for pool room; errors are
+per request."""
+import time
+
 import numpy as np
 import pytest
 
+import oracle
 import paper_2304_12557_gb300 as fz
 from paper_2304_12557_gb300 import fields
 
@@ -55,12 +60,23 @@ def _workload():
     return comp, dec_src
 
 
+def _oracle_stream(x, mode, eb):
+    st, s = oracle.compress(x, x.ndim, oracle.EB_ABS if mode == "abs" else oracle.EB_REL, eb,
+                            all_cores=True)
+    assert st == oracle.OK
+    return np.frombuffer(s, np.uint8)
+
+
 def _expected(codec, torch, comp, dec_src):
-    want_c = [codec.compress(torch.from_numpy(x).cuda(), mode=m, eb=e, ndim=x.ndim)
-              .cpu().numpy() for x, m, e in comp]
-    streams = [codec.compress(torch.from_numpy(x).cuda(), mode=m, eb=e, ndim=x.ndim)
-               .cpu().numpy() for x, m, e in dec_src]
-    want_d = [codec.decompress(torch.from_numpy(s).cuda()).cpu().numpy() for s in streams]
+    """Every expected result from the oracle: the compress requests' streams,
+    the decompress requests' input streams and their reconstructions."""
+    want_c = [_oracle_stream(x, m, e) for x, m, e in comp]
+    streams = [_oracle_stream(x, m, e) for x, m, e in dec_src]
+    want_d = []
+    for s in streams:
+        st, r = oracle.decompress(s.tobytes(), all_cores=True)
+        assert st == oracle.OK
+        want_d.append(r)
     return want_c, streams, want_d
 
 
@@ -103,10 +119,76 @@ def test_server_same_results_alone_and_in_the_mix(codec, torch):
         srv.close()
 
 
+def _smooth_on_device(torch, shape, seed):
+    """A smooth synthetic field made on the GPU (running sums of noise along
+    x and y), copied to pinned host memory."""
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    x = torch.randn(shape, generator=g, device="cuda").cumsum(-1).cumsum(-2)
+    x = (x / x.abs().max()).float()
+    h = torch.empty(shape, dtype=torch.float32).pin_memory()
+    h.copy_(x)
+    return h
+
+
+def test_late_requests_join_a_later_batch_in_flight_beside_the_first(codec, torch):
+    """Wave 1 (2 GiB of fields) forms one batch; as soon as the server has
+    launched it, wave 2 (small compress and decompress requests) arrives.
+    Wave 2 must run in later batches, be launched before wave 1 is done, and
+    be in flight on the device while wave 1's batch is (its GPU interval,
+    from CUDA events on its stream, starts before the batch's ends); every
+    result must equal the single calls' (and, for wave 2, the oracle's)."""
+    wave1 = [_smooth_on_device(torch, (32, 1024, 1024), 500 + i) for i in range(16)]
+    small = [fields.bumps3d(64), fields.climate2d(300, 500),
+             fields.grf((33, 70, 41), -3.0, 47).astype(np.float32)]
+    want_small = [_oracle_stream(x, "rel", 1e-3) for x in small]
+    dec_want = []
+    for s in want_small:
+        st, r = oracle.decompress(s.tobytes())
+        assert st == oracle.OK
+        dec_want.append(r)
+    srv = fz.Server(0, pool_bytes=8 << 30, max_batch=64)
+    try:
+        ids1 = [srv.submit_compress(x, "rel", 1e-3) for x in wave1]
+        t0 = time.monotonic()
+        while srv.info(ids1[-1])["launch_ms"] < 0:        # wave 1's batch launched
+            assert time.monotonic() - t0 < 30
+            time.sleep(20e-6)
+        ids2c = [srv.submit_compress(x, "rel", 1e-3) for x in small]
+        ids2d = [srv.submit_decompress(s) for s in want_small]
+        for rid in ids1 + ids2c + ids2d:
+            srv.wait(rid)
+        inf1 = [srv.info(r) for r in ids1]
+        inf2c = [srv.info(r) for r in ids2c]
+        inf2d = [srv.info(r) for r in ids2d]
+        got1 = [srv.fetch(r) for r in ids1]
+        got2c = [srv.fetch(r) for r in ids2c]
+        got2d = [srv.fetch(r) for r in ids2d]
+    finally:
+        srv.close()
+    # wave 1 may have been split over batches while it was being submitted;
+    # wave 2 came after all of them had been launched
+    b1 = max(i["batch"] for i in inf1)
+    assert min(i["batch"] for i in inf1) >= 1
+    assert all(i["batch"] > b1 for i in inf2c)
+    wave1_done = max(i["done_ms"] for i in inf1)
+    wave1_gpu_end = max(i["gpu_end_ms"] for i in inf1)
+    wave2 = inf2c + inf2d
+    assert all(i["submit_ms"] >= 0 and i["gpu_end_ms"] >= i["gpu_start_ms"] >= 0 for i in wave2)
+    assert min(i["launch_ms"] for i in wave2) < wave1_done
+    assert min(i["gpu_start_ms"] for i in wave2) < wave1_gpu_end
+    assert min(i["launch_seq"] for i in wave2) > max(i["launch_seq"] for i in inf1)
+    for x, g in zip(wave1[:3], got1[:3]):
+        want = codec.compress(x.cuda(), mode="rel", eb=1e-3).cpu().numpy()
+        assert g.tobytes() == want.tobytes()
+    for g, w in zip(got2c, want_small):
+        assert g.tobytes() == w.tobytes()
+    for g, w in zip(got2d, dec_want):
+        assert np.array_equal(g.reshape(-1).view(np.uint32), w.view(np.uint32))
+
+
 def test_server_admission_waits_for_pool_room(codec, torch):
     xs = [fields.grf((64, 128, 128), -3.0, 60 + i).astype(np.float32) for i in range(10)]
-    want = [codec.compress(torch.from_numpy(x).cuda(), mode="rel", eb=1e-3).cpu().numpy()
-            for x in xs]
+    want = [_oracle_stream(x, "rel", 1e-3) for x in xs]
     # each request holds ~4 MiB in and up to ~6.5 MiB out: a few at a time fit
     srv = fz.Server(0, pool_bytes=24 << 20, max_batch=8)
     try:
@@ -126,7 +208,7 @@ def test_server_errors_are_per_request(codec, torch):
     good = fields.bumps3d(64)
     bad = good.copy()
     bad[1, 2, 3] = np.inf
-    s = codec.compress(torch.from_numpy(good).cuda(), mode="rel", eb=1e-3).cpu().numpy()
+    s = _oracle_stream(good, "rel", 1e-3)
     corrupt = s.copy()
     corrupt[64] ^= 0x01                                          # a flag bit: counts mismatch
     srv = fz.Server(0, pool_bytes=256 << 20)
