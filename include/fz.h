@@ -155,6 +155,17 @@ int fz_debug_skip_publish(fz_ctx *ctx, uint64_t chunk);
 int fz_set_profiling(fz_ctx *ctx, int on);
 int fz_get_kernel_times(fz_ctx *ctx, double ms[5]);
 
+/* Whole-call timing (off by default).  When on, fz_compress and
+ * fz_decompress record one CUDA event on their stream when they are
+ * entered and one after their last operation on it (the result read-back
+ * they wait for), and fz_get_call_times fills ms[0] / ms[1] with the last
+ * fz_compress / fz_decompress call's time between the two, in milliseconds
+ * (0 before the first such call): the launches, kernels, gaps and read-back
+ * of the call, without the caller's own overhead.  Independent of
+ * fz_set_profiling.  Returns FZ_OK, FZ_ERR_ARG or FZ_ERR_CUDA. */
+int fz_set_call_timing(fz_ctx *ctx, int on);
+int fz_get_call_times(fz_ctx *ctx, double ms[2]);
+
 /* ---------------------------------------------------------------------
  * One field split across ranks.  Chunks are independent (Sec. 2.3: the
  * Lorenzo residual never reaches across a chunk), so a field can be cut

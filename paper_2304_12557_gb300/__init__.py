@@ -39,7 +39,8 @@ C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
          "fz_compress", "fz_decompress", "fz_compress_host",
          "fz_decompress_host", "fz_inspect", "fz_strerror",
          "fz_set_wait_limit_ns", "fz_debug_skip_publish",
-         "fz_set_profiling", "fz_get_kernel_times", "fz_range",
+         "fz_set_profiling", "fz_get_kernel_times", "fz_set_call_timing",
+         "fz_get_call_times", "fz_range",
          "fz_compress_ranged", "fz_shard_extent", "fz_concat_streams",
          "fz_concat_streams_host", "fz_batch_create", "fz_batch_destroy",
          "fz_batch_compress", "fz_batch_set_graph", "fz_batch_autotune",
@@ -136,6 +137,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_debug_skip_publish.argtypes = [_vp, _u64]
         L.fz_set_profiling.argtypes = [_vp, ctypes.c_int]
         L.fz_get_kernel_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+        L.fz_set_call_timing.argtypes = [_vp, ctypes.c_int]
+        L.fz_get_call_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
         L.fz_compress_noalloc.argtypes = [_vp, dims_t, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, _vp, _u64,
                                           ctypes.POINTER(_u64), _vp]
@@ -524,6 +527,20 @@ class Codec:
         st = self._L.fz_get_kernel_times(self._ctx, ms)
         if st != OK:
             raise FZError(st, "fz_get_kernel_times")
+        return list(ms)
+
+    def set_call_timing(self, on: bool):
+        st = self._L.fz_set_call_timing(self._ctx, int(bool(on)))
+        if st != OK:
+            raise FZError(st, "fz_set_call_timing")
+
+    def call_times_ms(self):
+        """[last fz_compress, last fz_decompress] call time (ms), from the
+        library's own events at the call's entry and after its read-back."""
+        ms = (ctypes.c_double * 2)()
+        st = self._L.fz_get_call_times(self._ctx, ms)
+        if st != OK:
+            raise FZError(st, "fz_get_call_times")
         return list(ms)
 
     # ------------------------------------------------------------ device

@@ -50,6 +50,10 @@ struct fz_ctx {
   bool profiling = false;
   cudaEvent_t ev[2 * fz::kProfSlots] = {};
   bool ev_used[fz::kProfSlots] = {};
+  // whole-call timing: [0] compress, [1] decompress (start, end)
+  bool call_timing = false;
+  cudaEvent_t call_ev[4] = {};
+  bool call_used[2] = {};
 };
 
 namespace fz {
@@ -173,9 +177,12 @@ int range_pass(fz_ctx *c, const float *x, uint64_t n, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? FZ_OK : FZ_ERR_CUDA;
 }
 
-int read_set(fz_ctx *c, int set, cudaStream_t s) {
+// the result block of `set` to the host; `done` (may be NULL) is recorded
+// after the copy, before the wait
+int read_set(fz_ctx *c, int set, cudaStream_t s, cudaEvent_t done = nullptr) {
   if (cudaMemcpyAsync(c->h_res, c->sets + set, sizeof(SetScratch), cudaMemcpyDeviceToHost, s) !=
           cudaSuccess ||
+      (done && cudaEventRecord(done, s) != cudaSuccess) ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return FZ_ERR_CUDA;
   return FZ_OK;
@@ -257,6 +264,12 @@ int fz_create(fz_ctx **out, int device) {
       return FZ_ERR_CUDA;
     }
   }
+  for (cudaEvent_t &e : c->call_ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      fz_destroy(c);
+      return FZ_ERR_CUDA;
+    }
+  }
   *out = c;
   return FZ_OK;
 }
@@ -275,6 +288,8 @@ void fz_destroy(fz_ctx *c) {
   if (c->h_res) cudaFreeHost(c->h_res);
   if (c->h_range) cudaFreeHost(c->h_range);
   for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->call_ev)
     if (e) cudaEventDestroy(e);
   delete c;
 }
@@ -325,6 +340,28 @@ int fz_set_staged_shuffle(fz_ctx *c, int kind) {
   return FZ_OK;
 }
 
+int fz_set_call_timing(fz_ctx *c, int on) {
+  if (!c) return FZ_ERR_ARG;
+  c->call_timing = on != 0;
+  c->call_used[0] = c->call_used[1] = false;
+  return FZ_OK;
+}
+
+int fz_get_call_times(fz_ctx *c, double ms[2]) {
+  if (!c || !ms) return FZ_ERR_ARG;
+  DeviceGuard guard(c->device);
+  for (int k = 0; k < 2; ++k) {
+    ms[k] = 0.0;
+    if (!c->call_used[k]) continue;
+    float t = 0.f;
+    if (cudaEventSynchronize(c->call_ev[2 * k + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, c->call_ev[2 * k], c->call_ev[2 * k + 1]) != cudaSuccess)
+      return FZ_ERR_CUDA;
+    ms[k] = t;
+  }
+  return FZ_OK;
+}
+
 int fz_debug_skip_publish(fz_ctx *c, uint64_t chunk) {
   if (!c) return FZ_ERR_ARG;
   c->skip_publish = chunk;
@@ -351,6 +388,8 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
   DeviceGuard guard(c->device);
   if (!guard.ok) return FZ_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool timed = c->call_timing;
+  if (timed) cudaEventRecord(c->call_ev[0], s);
   int st = ensure_cap(c, sh.n_tiles);             // at least one look-back word per unit
   if (st) return st;
   if ((st = prepare_set(c, s))) return st;
@@ -397,10 +436,11 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
   prof_end(c, 1, s);
   const uint64_t words = fz::compress_status_words(sh.n_tiles);
   retire_set(c, words, words);
-  if ((st = read_set(c, A, s))) {
+  if ((st = read_set(c, A, s, timed ? c->call_ev[1] : nullptr))) {
     mark_all_dirty(c);
     return st;
   }
+  c->call_used[0] = timed;
   const SetScratch r = *c->h_res;
   if (r.err & (fz::kErrNonFinite | fz::kErrEbParam | fz::kErrRange | fz::kErrTimeout)) {
     // the kernel may have stopped before zeroing the next call's look-back
@@ -431,7 +471,7 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
     prof_end(c, 2, s);
     const int B = c->cur;
     c->hdr_dirty[B] = true;
-    if ((st = read_set(c, B, s))) return st;
+    if ((st = read_set(c, B, s, timed ? c->call_ev[1] : nullptr))) return st;
     if (c->h_res->err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
     if (c->h_res->err & fz::kErrCapacity) {
       *out_size = total;
@@ -696,6 +736,8 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   DeviceGuard guard(c->device);
   if (!guard.ok) return FZ_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool timed = c->call_timing;
+  if (timed) cudaEventRecord(c->call_ev[2], s);
   // every chunk carries 128 bytes of flags, which bounds the chunk count
   uint64_t bound = (in_size - 64) / 128;
   const uint64_t max_chunks = kMaxCodes / fz::kChunkCodes + 1;
@@ -732,10 +774,11 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
     return FZ_ERR_CUDA;
   }
   prof_end(c, 3, s);
-  if ((st = read_set(c, A, s))) {
+  if ((st = read_set(c, A, s, timed ? c->call_ev[3] : nullptr))) {
     mark_all_dirty(c);
     return st;
   }
+  c->call_used[1] = timed;
   const SetScratch r = *c->h_res;
   const uint64_t words = fz::decompress_status_words(r.n_chunks);
   retire_set(c, r.n_chunks ? words : c->cap, words);
