@@ -384,11 +384,22 @@ def run_ours(args, rank, world, local_rank, dist):
         st_ms.append(ms)
     assert ssize == size
     med = [statistics.median(m[k] for m in st_ms[1:]) for k in range(5)]
+    # the same step with Listing 1's warp-ballot bitshuffle instead of the
+    # register transpose (same stream)
+    codec.set_staged_shuffle("ballot")
+    bal_ms = []
+    for _ in range(6):
+        _, bsize, ms = codec.compress_staged_into(x_d, s_d, "rel", 1e-3, 3)
+        bal_ms.append(ms[2])
+    codec.set_staged_shuffle("register")
+    assert bsize == size
     ablation = {"staged_kernel_ms": {"quantise": med[1], "shuffle_mark": med[2],
                                      "scan": med[3], "encode": med[4]},
                 "staged_compress_ms": sum(med[1:]),
                 "fused_compress_ms": mean(k_comp),
-                "fusion_speedup": sum(med[1:]) / mean(k_comp)}
+                "fusion_speedup": sum(med[1:]) / mean(k_comp),
+                "shuffle_mark_ballot_ms": statistics.median(bal_ms[1:]),
+                "shuffle_mark_register_ms": med[2]}
 
     # end to end through the host-buffer calls (pinned host memory)
     e2e = None

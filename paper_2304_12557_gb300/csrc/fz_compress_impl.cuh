@@ -361,7 +361,7 @@ __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q
   }
 }
 
-// ---- the compute path's residuals in fp32 (2-D and 3-D) ----------------
+// ---- the compute path's residuals in fp32 ------------------------------
 // The biased quantised values Q = fl(fl(x * r) + 1.5 * 2^23) are integers in
 // [2^23 + 1, 2^24 - 1] (|q| <= 2^22 - 1), exact as floats, and so are their
 // Lorenzo differences while a result stays within 2^24 in magnitude: a first
@@ -392,7 +392,8 @@ __device__ __forceinline__ void check_pair(float2 Q, uint32_t &qmax) {
 
 // Part 1 in fp32: pre-quantisation and the first difference (3-D: D_z
 // against the preloaded plane hf; 2-D: D_y, with the row above the brick
-// from the lane above or, for by == 0, from hf).  v[i] holds codes 2i, 2i+1.
+// from the lane above or, for by == 0, from hf; 1-D: none).  v[i] holds
+// codes 2i, 2i+1.
 template <int NDIM, bool CHECK, class Src>
 __device__ __forceinline__ void residuals_first_f(const Src &src, const TileGeo &q, float r,
                                                   const float (&hf)[32], float2 (&v)[32],
@@ -415,8 +416,18 @@ __device__ __forceinline__ void residuals_first_f(const Src &src, const TileGeo 
         v[(32 + 8 * iy + k) / 2] = sub_pair(q1, q0);
       }
     }
+  } else if constexpr (NDIM == 1) {
+#pragma unroll
+    for (int row = 0; row < 8; ++row) {
+      float f8[8];
+      src.row(0, 0, 8 * row, f8);
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        v[(8 * row + k) / 2] = quant_pair(f8[k], f8[k + 1], r);
+        check_pair<CHECK>(v[(8 * row + k) / 2], qmax);
+      }
+    }
   } else {
-    static_assert(NDIM == 2, "fp32 residuals: 2-D and 3-D");
 #pragma unroll
     for (int row = 0; row < 8; ++row) {
       float f8[8];
@@ -441,10 +452,28 @@ __device__ __forceinline__ void residuals_first_f(const Src &src, const TileGeo 
   }
 }
 
-// Part 2 in fp32: the remaining differences (3-D: D_y, then D_x; 2-D: D_x).
+// Part 2 in fp32: the remaining differences (3-D: D_y, then D_x; 2-D: D_x;
+// 1-D: D_x along the lane's 64 elements, whose left neighbour is the
+// previous lane's last, or for lane 0 the element before the tile).
 template <int NDIM>
-__device__ __forceinline__ void residuals_rest_f(const TileGeo &q, float2 (&v)[32]) {
+__device__ __forceinline__ void residuals_rest_f(const CompressArgs &a, const TileGeo &q, int g,
+                                                 float r, float2 (&v)[32]) {
   const unsigned full = 0xffffffffu;
+  if constexpr (NDIM == 1) {
+    float hq = kRoundMagic;                          // q = 0 before a chunk's first element
+    if (q.t > 0 && g == 0)
+      hq = quant_pair((q.x0 - 1 < a.dims[0]) ? __ldcs(a.x + q.x0 - 1) : 0.0f, 0.0f, r).x;
+    float left = __shfl_up_sync(full, v[31].y, 1);
+    if (g == 0) left = hq;
+#pragma unroll
+    for (int j = 31; j >= 1; --j) {
+      v[j].y = __fsub_rn(v[j].y, v[j].x);
+      v[j].x = __fsub_rn(v[j].x, v[j - 1].y);
+    }
+    v[0].y = __fsub_rn(v[0].y, v[0].x);
+    v[0].x = __fsub_rn(v[0].x, left);
+    return;
+  }
   if constexpr (NDIM == 3) {
 #pragma unroll
     for (int iz = 0; iz < 2; ++iz) {               // D_y
@@ -943,9 +972,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       // a batch's TMA fields have 16-byte aligned rows: vector halo loads
       if (BATCH && V < 4 && tma_of(cw)) load_halo<NDIM, 4>(a, q, hf);
       else load_halo<NDIM, V>(a, q, hf);
-      constexpr bool kF = NDIM >= 2;                // fp32 residuals
-      int32_t v[kF ? 1 : 64];
-      float2 vf[kF ? 32 : 1];
+      float2 vf[32];                                // fp32 residuals, codes 2i, 2i+1 in vf[i]
       uint32_t qmax = 0;
       // a single field's launch compiles one load path; a batch picks per field
       const bool use_box = BATCH ? tma_of(cw) : TMA;
@@ -953,42 +980,27 @@ __global__ void __launch_bounds__(kCompThreads, 1)
         if (!mbar_wait_bounded(bar, phase, a0.wait_limit_ns) && g == 0)
           atomicOr(&cur->err, kErrTimeout);
         phase ^= 1u;
-        if constexpr (kF)
-          residuals_first_f<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, rt.p.ebx2_r, hf, vf,
-                                         qmax);
-        else
-          residuals_first<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, g, rt.p.ebx2_r, hf, v,
+        residuals_first_f<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, rt.p.ebx2_r, hf, vf,
                                        qmax);
         __syncwarp();                    // every lane is done with the box
       } else {
-        if constexpr (kF)
-          residuals_first_f<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, rt.p.ebx2_r, hf, vf, qmax);
-        else
-          residuals_first<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, g, rt.p.ebx2_r, hf, v, qmax);
+        residuals_first_f<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, rt.p.ebx2_r, hf, vf, qmax);
       }
       // the box is free: fetch the next round's tile into it while this one
       // is finished
       next_unit();
       if (g == 0 && tma_of(nw)) issue(nw);
-      if constexpr (kF) residuals_rest_f<NDIM>(q, vf);
-      else residuals_rest<NDIM>(a, q, g, rt.p.ebx2_r, v);
+      residuals_rest_f<NDIM>(a, q, g, rt.p.ebx2_r, vf);
       if (CHECK && __any_sync(full, qmax > kBiasedMax) && g == 0) atomicOr(&cur->err, kErrRange);
 
       uint32_t w[32];
       // narrow: every code of the tile fits in 7 bits and the sign, so the
       // planes of magnitude bits 7..14 are zero and half the transpose is
       // skipped; escape: some |residual| needs more than 15 bits
-      bool narrow, escape;
-      if constexpr (kF) {
-        if (q.edge) mask_padding<NDIM>(a, q, vf);
-        const uint32_t o = pack_codes_f(vf, w);      // vf is dead from here on
-        narrow = !__any_sync(full, (o & ~0x4B00007Fu) != 0u);
-        escape = __any_sync(full, (o & ~0x4B007FFFu) != 0u);
-      } else {
-        const uint32_t orabs = pack_codes(v, w);     // v is dead from here on
-        narrow = !__any_sync(full, orabs > 127u);
-        escape = __any_sync(full, (orabs >> 15) != 0u);
-      }
+      if (q.edge) mask_padding<NDIM>(a, q, vf);
+      const uint32_t o = pack_codes_f(vf, w);        // vf is dead from here on
+      const bool narrow = !__any_sync(full, (o & ~0x4B00007Fu) != 0u);
+      const bool escape = __any_sync(full, (o & ~0x4B007FFFu) != 0u);
       // drain this round's plane buffer before anything below writes it
       Pending &drain = kDef == 0 ? prev1 : prev2;
       if (drain.T != kNoTile) {

@@ -58,8 +58,10 @@ def gpu_decompress(codec, torch, s):
     return y.cpu().numpy().ravel()
 
 
-def check_parity(codec, torch, x, ndim, mode, eb, offset=0):
-    ost, ostream = oracle.compress(x, ndim, mode, eb)
+def check_parity(codec, torch, x, ndim, mode, eb, offset=0, all_cores=False):
+    """all_cores: the oracle's all-cores variant (bit-identical to the
+    one-thread oracle, checked on the CPU) for the full-size fields"""
+    ost, ostream = oracle.compress(x, ndim, mode, eb, all_cores=all_cores)
     assert ost == oracle.OK
     g = gpu_compress(codec, torch, x, ndim, mode, eb, offset)
     assert len(g) == len(ostream)
@@ -69,7 +71,7 @@ def check_parity(codec, torch, x, ndim, mode, eb, offset=0):
         bad = np.flatnonzero(a != b)
         raise AssertionError(f"stream differs at {bad.size} bytes, first {bad[:8]}")
     xr_gpu = gpu_decompress(codec, torch, g)
-    st, xr_or = oracle.decompress(ostream)
+    st, xr_or = oracle.decompress(ostream, all_cores=all_cores)
     assert st == oracle.OK
     np.testing.assert_array_equal(xr_gpu.view(np.uint32), xr_or.view(np.uint32))
     return g, xr_gpu
@@ -109,9 +111,13 @@ def test_bumps3d_64(codec, torch, eb):
     check_parity(codec, torch, fields.bumps3d(), 3, fz.EB_REL, eb)
 
 
-@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
+# the paper's five relative bounds (Sec. 4.1)
+PAPER_EBS = [1e-2, 5e-3, 1e-3, 5e-4, 1e-4]
+
+
+@pytest.mark.parametrize("eb", PAPER_EBS)
 def test_climate2d_1800x3600(codec, torch, eb):
-    check_parity(codec, torch, fields.climate2d(), 2, fz.EB_REL, eb)
+    check_parity(codec, torch, fields.climate2d(), 2, fz.EB_REL, eb, all_cores=True)
 
 
 @pytest.fixture(scope="module")
@@ -119,14 +125,30 @@ def cosmo512():
     return fields.cosmo3d(512)
 
 
-@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
+@pytest.mark.parametrize("eb", PAPER_EBS)
 def test_cosmo3d_512(codec, torch, cosmo512, eb):
-    g, xr = check_parity(codec, torch, cosmo512, 3, fz.EB_REL, eb)
+    g, xr = check_parity(codec, torch, cosmo512, 3, fz.EB_REL, eb, all_cores=True)
     info = fz.inspect(g[:64])
     x = cosmo512.ravel().astype(np.float64)
     err = np.abs(x - xr.astype(np.float64))
     slack = 2.0 ** -22 * np.maximum(np.abs(x), np.abs(xr.astype(np.float64)))
     assert np.all(err <= info["eb"] + slack)
+
+
+@pytest.mark.parametrize("rel", [1e-3, 1e-5])
+def test_cosmo3d_512_absolute_bound(codec, torch, cosmo512, rel):
+    """An absolute bound on the full field (every element range-checked on
+    the device); 1e-5 of the range gives codes beyond 7 bits in most tiles."""
+    eb = float(rel * (cosmo512.max() - cosmo512.min()))
+    check_parity(codec, torch, cosmo512, 3, fz.EB_ABS, eb, all_cores=True)
+
+
+def test_1d_64m_values(codec, torch):
+    """A 1-D field of 2^26 values (256 MiB): 8192 chunks of 4 tiles."""
+    rng = np.random.default_rng(26)
+    x = np.cumsum(rng.standard_normal(1 << 26, dtype=np.float32), dtype=np.float64)
+    x = (x / np.abs(x).max()).astype(np.float32)
+    check_parity(codec, torch, x, 1, fz.EB_REL, 1e-4, all_cores=True)
 
 
 # ------------------------------------------------------------ edge cases
