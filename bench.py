@@ -401,6 +401,23 @@ def run_ours(args, rank, world, local_rank, dist):
                 "shuffle_mark_ballot_ms": statistics.median(bal_ms[1:]),
                 "shuffle_mark_register_ms": med[2]}
 
+    # the whole-field Lorenzo variant (stream version 2) through the same
+    # calls, timed by the library's call events: its stream size, and the
+    # cost of its decompression (faces pass, cross-chunk scans, field pass)
+    codec.set_call_timing(True)
+    wc, wd = [], []
+    for _ in range(6):
+        _, wsize = codec.compress_into(x_d, s_d, "rel", 1e-3, 3, whole=True)
+        wc.append(codec.call_times_ms()[0])
+        codec.decompress_into(s_d, y_d, nbytes=wsize)
+        wd.append(codec.call_times_ms()[1])
+    codec.set_call_timing(False)
+    ablation["whole_field_lorenzo"] = {
+        "stream_bytes": wsize, "stream_bytes_chunked": size,
+        "fz_compress_whole_ms_p50": statistics.median(wc[1:]),
+        "fz_decompress_v2_ms_p50": statistics.median(wd[1:]),
+        "fz_compress_ms_p50": c50, "fz_decompress_ms_p50": d50}
+
     # end to end through the host-buffer calls (pinned host memory)
     e2e = None
     if not args.no_e2e:

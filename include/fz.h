@@ -50,6 +50,8 @@ extern "C" {
 #define FZ_ERR_CORRUPT     -6  /* stream fails a structural check          */
 #define FZ_ERR_TIMEOUT     -7  /* a bounded device wait gave up            */
 #define FZ_ERR_CUDA        -8  /* a CUDA runtime call failed               */
+#define FZ_ERR_VERSION     -9  /* a version-2 stream (whole-field Lorenzo)
+                                  where the call reads version 1 only      */
 
 /* error-bound modes (Sec. 4.1) */
 #define FZ_EB_ABS 0   /* eb is the absolute bound                          */
@@ -74,6 +76,9 @@ typedef struct fz_info {
   uint64_t nnz_blocks;    /* non-zero 16-byte blocks in the payload        */
   uint64_t n_outliers;    /* escaped residuals                             */
   uint64_t stream_bytes;  /* 64 + 32*n_tiles + 16*nnz_blocks + 8*n_outliers*/
+  uint32_t version;       /* 1: chunk-local Lorenzo (fz_compress), 2:
+                             whole-field Lorenzo (fz_compress_whole)       */
+  uint32_t reserved;      /* 0                                             */
 } fz_info;
 
 /* Create a context on CUDA device `device`: allocates the scratch used by
@@ -107,11 +112,25 @@ int fz_compress(fz_ctx *ctx, const float *d_in, const uint64_t dims[3],
                 int ndim, int mode, double eb, void *d_out,
                 uint64_t out_capacity, uint64_t *out_size, void *stream);
 
-/* Decompress a stream made by fz_compress (Sec. 4.4).
+/* The whole-field Lorenzo variant of fz_compress: the same quantisation,
+ * encoding and stream layout, but the residual of every element takes its
+ * Lorenzo neighbours anywhere in the field (Eq. 1 with q = 0 only outside
+ * the field) instead of inside its chunk (Sec. 2.3), so chunk faces see
+ * full-order predictors.  The stream's version byte is 2; fz_decompress
+ * reads it (three passes instead of one: the chunks are no longer
+ * independent).  The reconstruction equals fz_compress's, element for
+ * element.  Same arguments and errors as fz_compress. */
+int fz_compress_whole(fz_ctx *ctx, const float *d_in, const uint64_t dims[3],
+                      int ndim, int mode, double eb, void *d_out,
+                      uint64_t out_capacity, uint64_t *out_size, void *stream);
+
+/* Decompress a stream made by fz_compress or fz_compress_whole (Sec. 4.4).
  *   d_in       device pointer to the stream, 16-byte aligned, in_size bytes
  *   d_out      device pointer to out_capacity_elems floats
  * Writes every element of the field; the reconstruction x' satisfies
- * x' = fl(q * 2eb) with q the pre-quantised value of the original x.
+ * x' = fl(q * 2eb) with q the pre-quantised value of the original x.  A
+ * version-2 stream takes context scratch of 3/2 (3-D), 3/16 (2-D) or
+ * 1/1024 (1-D) bytes per element, allocated on first use and kept.
  * Errors: FZ_ERR_ARG, FZ_ERR_CORRUPT (header, sizes, flags or outlier list
  * inconsistent), FZ_ERR_CAPACITY, FZ_ERR_TIMEOUT, FZ_ERR_CUDA. */
 int fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_size,
@@ -215,7 +234,7 @@ int fz_shard_extent(const uint64_t dims[3], int ndim, int n_shards, int shard,
  *                FZ_ERR_CAPACITY: the size needed)
  * Synchronises `stream`.  FZ_OK, FZ_ERR_ARG, FZ_ERR_CORRUPT (a part's
  * header or size is inconsistent, or the parts do not fit together),
- * FZ_ERR_CAPACITY or FZ_ERR_CUDA. */
+ * FZ_ERR_VERSION (a version-2 part), FZ_ERR_CAPACITY or FZ_ERR_CUDA. */
 int fz_concat_streams(fz_ctx *ctx, const void *const *d_parts,
                       const uint64_t *part_sizes, int n_parts, void *d_out,
                       uint64_t out_capacity, uint64_t *out_size, void *stream);
@@ -356,7 +375,8 @@ int fz_server_create(int device, uint64_t pool_bytes, int max_batch, fz_server *
 void fz_server_destroy(fz_server *server);
 
 /* Queue a request; *id names it.  FZ_ERR_ARG (bad request), FZ_ERR_CORRUPT
- * (a decompress input whose header or size is inconsistent) or
+ * (a decompress input whose header or size is inconsistent), FZ_ERR_VERSION
+ * (a version-2 stream: fz_decompress reads those) or
  * FZ_ERR_CAPACITY (the request needs more than the whole pool). */
 int fz_server_submit(fz_server *server, const fz_request *request, uint64_t *id);
 

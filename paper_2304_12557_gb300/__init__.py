@@ -15,7 +15,7 @@ import threading
 
 __all__ = ["Codec", "FZError", "load_library", "library_path", "EB_ABS",
            "EB_REL", "OK", "ERR_ARG", "ERR_CAPACITY", "ERR_NONFINITE",
-           "ERR_EB_RANGE", "ERR_CORRUPT", "ERR_TIMEOUT", "ERR_CUDA",
+           "ERR_EB_RANGE", "ERR_CORRUPT", "ERR_TIMEOUT", "ERR_CUDA", "ERR_VERSION",
            "compress_bound", "stream_min_bytes", "inspect", "shard_extent",
            "concat_streams_host", "Batch", "Server", "PENDING", "C_API"]
 
@@ -30,13 +30,14 @@ ERR_EB_RANGE = -4
 ERR_CORRUPT = -6
 ERR_TIMEOUT = -7
 ERR_CUDA = -8
+ERR_VERSION = -9
 PENDING = 1
 EB_ABS = 0
 EB_REL = 1
 
 # every entry point declared in include/fz.h
 C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
-         "fz_compress", "fz_decompress", "fz_compress_host",
+         "fz_compress", "fz_compress_whole", "fz_decompress", "fz_compress_host",
          "fz_decompress_host", "fz_inspect", "fz_strerror",
          "fz_set_wait_limit_ns", "fz_debug_skip_publish",
          "fz_set_profiling", "fz_get_kernel_times", "fz_set_call_timing",
@@ -70,7 +71,8 @@ class _Info(ctypes.Structure):
                 ("ebx2_r", ctypes.c_float), ("range_min", ctypes.c_float),
                 ("range_max", ctypes.c_float), ("n_tiles", _u64),
                 ("nnz_blocks", _u64), ("n_outliers", _u64),
-                ("stream_bytes", _u64)]
+                ("stream_bytes", _u64), ("version", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class _Field(ctypes.Structure):
@@ -127,6 +129,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_compress.argtypes = [_vp, _vp, dims_t, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_double, _vp, _u64,
                                   ctypes.POINTER(_u64), _vp]
+        L.fz_compress_whole.argtypes = L.fz_compress.argtypes
         L.fz_decompress.argtypes = [_vp, _vp, _u64, _vp, _u64, _vp]
         L.fz_compress_host.argtypes = L.fz_compress.argtypes
         L.fz_decompress_host.argtypes = L.fz_decompress.argtypes
@@ -219,7 +222,8 @@ def inspect(header: bytes) -> dict:
             "ebx2": info.ebx2, "ebx2_r": info.ebx2_r,
             "range_min": info.range_min, "range_max": info.range_max,
             "n_tiles": info.n_tiles, "nnz_blocks": info.nnz_blocks,
-            "n_outliers": info.n_outliers, "stream_bytes": info.stream_bytes}
+            "n_outliers": info.n_outliers, "stream_bytes": info.stream_bytes,
+            "version": info.version}
 
 
 def pwrel_bound(eps: float) -> float:
@@ -551,22 +555,24 @@ class Codec:
         return _vp(s.cuda_stream)
 
     def compress_into(self, x, out, mode="rel", eb=1e-3, ndim=None,
-                      stream=None, raise_on_error=True):
+                      stream=None, raise_on_error=True, whole=False):
         """Compress device tensor x into the uint8 device tensor out.
-        Returns (status, size)."""
+        Returns (status, size).  whole: the whole-field Lorenzo variant
+        (fz_compress_whole, stream version 2)."""
         ndim = ndim or x.dim()
         dims = list(x.shape[::-1])[:ndim]
         assert x.is_cuda and x.is_contiguous(), "x must be a contiguous CUDA tensor"
         size = _u64(0)
-        st = self._L.fz_compress(self._ctx, _vp(x.data_ptr()), _dims(dims), ndim,
-                                 _mode(mode), float(eb), _vp(out.data_ptr()),
-                                 out.numel() * out.element_size(),
-                                 ctypes.byref(size), self._stream(stream))
+        fn = self._L.fz_compress_whole if whole else self._L.fz_compress
+        st = fn(self._ctx, _vp(x.data_ptr()), _dims(dims), ndim,
+                _mode(mode), float(eb), _vp(out.data_ptr()),
+                out.numel() * out.element_size(),
+                ctypes.byref(size), self._stream(stream))
         if st != OK and raise_on_error:
-            raise FZError(st, "fz_compress")
+            raise FZError(st, "fz_compress_whole" if whole else "fz_compress")
         return st, int(size.value)
 
-    def compress(self, x, mode="rel", eb=1e-3, ndim=None, stream=None):
+    def compress(self, x, mode="rel", eb=1e-3, ndim=None, stream=None, whole=False):
         """Compress a float32 CUDA tensor; returns the stream as a uint8 CUDA
         tensor (a view of a buffer sized for the worst case)."""
         import torch
@@ -574,12 +580,12 @@ class Codec:
         dims = list(x.shape[::-1])[:ndim]
         cap = stream_min_bytes(dims, ndim) + 16 * 256 * (x.numel() // 2048 + 4)
         out = torch.empty(cap, dtype=torch.uint8, device=x.device)
-        st, size = self.compress_into(x, out, mode, eb, ndim, stream, False)
+        st, size = self.compress_into(x, out, mode, eb, ndim, stream, False, whole)
         if st == ERR_CAPACITY:
             out = torch.empty(size, dtype=torch.uint8, device=x.device)
-            st, size = self.compress_into(x, out, mode, eb, ndim, stream, False)
+            st, size = self.compress_into(x, out, mode, eb, ndim, stream, False, whole)
         if st != OK:
-            raise FZError(st, "fz_compress")
+            raise FZError(st, "fz_compress_whole" if whole else "fz_compress")
         return out[:size]
 
     def compress_staged_into(self, x, out, mode="rel", eb=1e-3, ndim=None,

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfz_gb300.so")
-SOURCES = ["fz_api.cu", "fz_compress.cu", "fz_decompress.cu", "fz_noalloc.cu", "fz_shard.cu",
+SOURCES = ["fz_api.cu", "fz_compress.cu", "fz_decompress.cu", "fz_whole.cu", "fz_noalloc.cu",
+           "fz_shard.cu",
            "fz_pwrel.cu",
            "fz_batch.cu", "fz_server.cu", "fz_staged.cu"]
 HEADERS = ["fz_device.cuh", "fz_kernels.h", "fz_compress_impl.cuh", "fz_batch_ws.h", "fz_pwrel.h"]

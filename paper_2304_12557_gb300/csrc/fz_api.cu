@@ -41,6 +41,9 @@ struct fz_ctx {
   uint64_t stage_in_cap = 0;
   void *stage_out = nullptr;
   uint64_t stage_out_cap = 0;
+  // version-2 decompression: faces and scan work space, grown on demand
+  void *whole = nullptr;
+  uint64_t whole_bytes = 0;
   // the unfused path's scratch (fz_compress_staged), grown on demand
   void *staged = nullptr;
   uint64_t staged_tiles = 0;
@@ -231,6 +234,7 @@ const char *fz_strerror(int st) {
     case FZ_ERR_CORRUPT: return "corrupt or inconsistent stream";
     case FZ_ERR_TIMEOUT: return "a bounded device wait timed out";
     case FZ_ERR_CUDA: return "CUDA runtime error";
+    case FZ_ERR_VERSION: return "stream version not read by this call";
     default: return "unknown status";
   }
 }
@@ -278,6 +282,7 @@ void fz_destroy(fz_ctx *c) {
   if (!c) return;
   DeviceGuard guard(c->device);
   free_scratch(c);
+  cudaFree(c->whole);
   cudaFree(c->staged);
   for (cudaEvent_t e : c->staged_ev)
     if (e) cudaEventDestroy(e);
@@ -372,7 +377,7 @@ int fz_debug_skip_publish(fz_ctx *c, uint64_t chunk) {
 // range from a range pass over d_in, else rng[0..1] is the range
 static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim,
                          int mode, double eb, const float *rng, void *d_out, uint64_t cap,
-                         uint64_t *out_size, void *stream) {
+                         uint64_t *out_size, void *stream, bool whole = false) {
   if (out_size) *out_size = 0;
   Shape sh;
   if (!c || !d_in || !d_out || !out_size || !make_shape(dims, ndim, &sh)) return FZ_ERR_ARG;
@@ -423,9 +428,10 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
   a.out_capacity = cap;
   a.wait_limit_ns = c->wait_limit_ns;
   a.skip_publish_chunk = c->skip_publish;
+  a.whole = whole;
   CUtensorMap tm;
   std::memset(&tm, 0, sizeof(tm));
-  const bool tma = fz::compress_uses_tma(sh.ndim, a) &&
+  const bool tma = !whole && fz::compress_uses_tma(sh.ndim, a) &&
                    fz::encode_field_tmap(sh.ndim, sh.d, d_in, &tm);
   prof_begin(c, 1, s);
   if (fz::launch_compress(sh.ndim, a, tma ? &tm : nullptr, c->num_sms, s,
@@ -485,6 +491,12 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
 int fz_compress(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, int mode,
                 double eb, void *d_out, uint64_t cap, uint64_t *out_size, void *stream) {
   return compress_impl(c, d_in, dims, ndim, mode, eb, nullptr, d_out, cap, out_size, stream);
+}
+
+int fz_compress_whole(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim, int mode,
+                      double eb, void *d_out, uint64_t cap, uint64_t *out_size, void *stream) {
+  return compress_impl(c, d_in, dims, ndim, mode, eb, nullptr, d_out, cap, out_size, stream,
+                       true);
 }
 
 int fz_compress_ranged(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim,
@@ -727,6 +739,71 @@ int fz_concat_streams(fz_ctx *c, const void *const *d_parts, const uint64_t *par
   return st;
 }
 
+// A version-2 stream (whole-field Lorenzo), after the offsets pass: phase 1
+// (chunk-local prefix sums on the chunks' faces), the cross-chunk scans of
+// the faces, phase 2 (the field).  Both phases count the matched outliers.
+static int decompress_whole(fz_ctx *c, fz::DecompressArgs a, const SetScratch &r, int grid,
+                            cudaStream_t s, bool timed) {
+  // the chunk grid and dimensionality of the header the offsets pass checked
+  const uint64_t nch = r.n_chunks;
+  const int nd = (int)r.ndim;
+  if (nd < 1 || nd > 3 || r.ncx == 0 || r.ncy == 0) return FZ_ERR_CORRUPT;
+  const uint32_t nc[3] = {r.ncx, r.ncy, (uint32_t)(nch / ((uint64_t)r.ncx * r.ncy))};
+  uint64_t words[3], total = 0;
+  for (int k = 0; k < 3; ++k) {
+    words[k] = nch * (uint64_t)fz::whole_face_elems(nd, k);
+    total += 2 * words[k];
+  }
+  const uint64_t bytes = 4 * total;
+  if (bytes > c->whole_bytes) {
+    cudaFree(c->whole);
+    c->whole = nullptr;
+    c->whole_bytes = 0;
+    if (cudaMalloc(&c->whole, bytes) != cudaSuccess) return FZ_ERR_CUDA;
+    c->whole_bytes = bytes;
+  }
+  int32_t *p = static_cast<int32_t *>(c->whole);
+  int32_t *face[3], *work[3];
+  for (int k = 0; k < 3; ++k) {
+    face[k] = p;
+    p += words[k];
+    work[k] = p;
+    p += words[k];
+  }
+  int st = prepare_set(c, s);
+  if (st) return st;
+  const int B = c->cur;
+  a.set_cur = c->sets + B;
+  for (int k = 0; k < 3; ++k) a.face[k] = face[k];
+  a.phase = 1;
+  prof_begin(c, 3, s);
+  if (fz::launch_decompress(a, grid, s) != cudaSuccess) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  const int32_t *corr[3];
+  if (fz::launch_whole_scans(nd, nc, face, work, corr, s) != cudaSuccess) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  a.phase = 2;
+  for (int k = 0; k < 3; ++k) a.corr[k] = corr[k];
+  if (fz::launch_decompress(a, grid, s) != cudaSuccess) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  prof_end(c, 3, s);
+  c->hdr_dirty[B] = true;
+  if ((st = read_set(c, B, s, timed ? c->call_ev[3] : nullptr))) {
+    mark_all_dirty(c);
+    return st;
+  }
+  const SetScratch q = *c->h_res;
+  if (q.err & fz::kErrCorrupt) return FZ_ERR_CORRUPT;
+  if (q.nout != 2ull * r.hdr_nout) return FZ_ERR_CORRUPT;
+  return FZ_OK;
+}
+
 int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
                   uint64_t cap_elems, void *stream) {
   if (!c || !d_in || !d_out) return FZ_ERR_ARG;
@@ -760,6 +837,7 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   a.chunk_olo = c->out_count;
   a.wait_limit_ns = c->wait_limit_ns;
   a.skip_publish_chunk = c->skip_publish;
+  a.accept_whole = 1;
   const int grid = c->num_sms * c->dec_blocks_per_sm;
   prof_reset(c);
   prof_begin(c, 4, s);
@@ -787,6 +865,7 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   if (r.err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
   if (r.err & fz::kErrCorrupt) return FZ_ERR_CORRUPT;
   if (r.err & fz::kErrCapacity) return FZ_ERR_CAPACITY;
+  if (r.version == 2) return decompress_whole(c, a, r, grid, s, timed);
   if (r.nout != r.hdr_nout) return FZ_ERR_CORRUPT;
   return FZ_OK;
 }
@@ -856,7 +935,8 @@ int fz_inspect(const void *hdr, uint64_t n, fz_info *out) {
   if (!hdr || !out) return FZ_ERR_ARG;
   if (n < 64) return FZ_ERR_CORRUPT;
   const uint8_t *p = static_cast<const uint8_t *>(hdr);
-  if (p[0] != 'F' || p[1] != 'Z' || p[2] != 'G' || p[3] != '1' || p[4] != 1 || p[7] != 0)
+  if (p[0] != 'F' || p[1] != 'Z' || p[2] != 'G' || p[3] != '1' || p[4] < 1 || p[4] > 2 ||
+      p[7] != 0)
     return FZ_ERR_CORRUPT;
   const int ndim = p[5], mode = p[6];
   if (ndim < 1 || ndim > 3 || mode > 1) return FZ_ERR_CORRUPT;
@@ -879,6 +959,8 @@ int fz_inspect(const void *hdr, uint64_t n, fz_info *out) {
   std::memcpy(&out->range_max, p + 56, 4);
   out->n_tiles = sh.n_tiles;
   out->stream_bytes = 64 + 32 * sh.n_tiles + 16 * out->nnz_blocks + 8 * out->n_outliers;
+  out->version = p[4];
+  out->reserved = 0;
   return FZ_OK;
 }
 

@@ -138,10 +138,10 @@ static int vec_width(const CompressArgs &a) {
   return 1;
 }
 
-template <int NDIM, int V, bool CHECK, bool TMA>
+template <int NDIM, int V, bool CHECK, bool TMA, bool WHOLE = false>
 static cudaError_t launch_c3(const CompressArgs &a, const CUtensorMap &tm, int sms, bool pdl,
                              cudaStream_t s) {
-  auto k = compress_kernel<NDIM, V, CHECK, TMA, false>;
+  auto k = compress_kernel<NDIM, V, CHECK, TMA, false, WHOLE>;
   const int smem = TMA ? kCompSmemTma : kCompSmemLdg;
   static int per_sm = 0;                    // resident blocks per SM, once
   if (per_sm == 0) {
@@ -231,8 +231,23 @@ bool compress_uses_tma(int ndim, const CompressArgs &a) {
   return !ldg_only && ndim >= 2 && vec_width(a) >= 4;
 }
 
+// The whole-field variant (stream version 2) reads its tiles with scalar
+// loads; a range-checked and an unchecked kernel per dimensionality.
+template <int NDIM>
+static cudaError_t launch_whole(const CompressArgs &a, int sms, bool pdl, cudaStream_t s) {
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  return (a.mode == 0 || a.range_given) ? launch_c3<NDIM, 1, true, false, true>(a, none, sms, pdl, s)
+                                        : launch_c3<NDIM, 1, false, false, true>(a, none, sms, pdl, s);
+}
+
 cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *tm, int sms,
                             cudaStream_t s, bool after_range) {
+  if (a.whole) {
+    if (ndim == 3) return launch_whole<3>(a, sms, after_range, s);
+    if (ndim == 2) return launch_whole<2>(a, sms, after_range, s);
+    return launch_whole<1>(a, sms, after_range, s);
+  }
   if (ndim == 3) return launch_c0<3>(a, tm, sms, after_range, s);
   if (ndim == 2) return launch_c0<2>(a, tm, sms, after_range, s);
   return launch_c0<1>(a, nullptr, sms, after_range, s);
@@ -242,6 +257,10 @@ template <int NDIM>
 static cudaError_t launch_o(const CompressArgs &a, uint64_t out_section, cudaStream_t s) {
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
   const unsigned blocks = (unsigned)((n_tiles + kOutWarps - 1) / kOutWarps);
+  if (a.whole) {
+    outlier_kernel<NDIM, 1, true><<<blocks, kOutWarps * 32, 0, s>>>(a, out_section);
+    return cudaGetLastError();
+  }
   switch (vec_width(a)) {
     case 8: outlier_kernel<NDIM, 8><<<blocks, kOutWarps * 32, 0, s>>>(a, out_section); break;
     case 4: outlier_kernel<NDIM, 4><<<blocks, kOutWarps * 32, 0, s>>>(a, out_section); break;

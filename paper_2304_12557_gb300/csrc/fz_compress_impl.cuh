@@ -230,6 +230,50 @@ __device__ __forceinline__ TileGeo tile_geo(const CompressArgs &a, const ChunkGr
   return q;
 }
 
+// ---- whole-field Lorenzo (stream version 2) ----------------------------
+// The variant takes every neighbour inside the field (zero only outside it)
+// instead of every neighbour inside the chunk, so a brick on a chunk's lower
+// face needs values of the neighbouring chunk; they come from global memory.
+// q_at: the biased quantised value Q = fl(fl(x * r) + 1.5 * 2^23) of the
+// element at (x, y, z), or the biased zero outside the field (a coordinate
+// of -1 wraps around and is outside too).
+__device__ __forceinline__ float q_at(const CompressArgs &a, uint64_t x, uint64_t y, uint64_t z,
+                                      float r) {
+  const bool in = x < a.dims[0] && y < a.dims[1] && z < a.dims[2];
+  const float v = in ? __ldg(a.x + x + a.dims[0] * (y + a.dims[1] * z)) : 0.0f;
+  return __fadd_rn(__fmul_rn(v, r), kRoundMagic);
+}
+// whether a brick's neighbours one step back along the march axis (3-D:
+// the plane below, 2-D: the row above, 1-D: the element before) count:
+// inside the chunk (the chunk's first tile has none) or inside the field
+template <int NDIM, bool WHOLE>
+__device__ __forceinline__ bool march_halo(const TileGeo &q) {
+  if constexpr (WHOLE) return NDIM == 3 ? q.z0 > 0 : NDIM == 2 ? q.y0 > 0 : q.x0 > 0;
+  else return q.t > 0;
+}
+// 3-D, a brick with by == 0: D_z Q of the row above the brick (y0 - 1) at
+// x0 + ix, z0 + iz (whole-field; chunked residuals take 0 there)
+__device__ __forceinline__ float face_up3(const CompressArgs &a, const TileGeo &q, int ix, int iz,
+                                          float r) {
+  const uint64_t x = q.x0 + ix, y = q.y0 - 1, z = q.z0 + iz;
+  return __fsub_rn(q_at(a, x, y, z, r), q_at(a, x, y, z - 1, r));
+}
+// 3-D, a brick with bx == 0: D_y D_z Q of the column before the brick
+// (x0 - 1) at y0 + iy, z0 + iz
+__device__ __forceinline__ float face_left3(const CompressArgs &a, const TileGeo &q, int iy,
+                                            int iz, float r) {
+  const uint64_t x = q.x0 - 1, y = q.y0 + iy, z = q.z0 + iz;
+  const float d1 = __fsub_rn(q_at(a, x, y, z, r), q_at(a, x, y - 1, z, r));
+  const float d0 = __fsub_rn(q_at(a, x, y, z - 1, r), q_at(a, x, y - 1, z - 1, r));
+  return __fsub_rn(d1, d0);
+}
+// 2-D, a brick with bx == 0: D_y Q of the column before the brick at y0 + iy
+__device__ __forceinline__ float face_left2(const CompressArgs &a, const TileGeo &q, int iy,
+                                            float r) {
+  const uint64_t x = q.x0 - 1, y = q.y0 + iy;
+  return __fsub_rn(q_at(a, x, y, 0, r), q_at(a, x, y - 1, 0, r));
+}
+
 // Rows of 8 floats of a lane's brick, read from global memory.  Row
 // selectors: 3-D (p, iy) with p = -1 the previous plane, 0/1 the brick's
 // planes; 2-D (0, iy) with iy = -1 the previous row; 1-D (0, 0, xo).
@@ -276,14 +320,14 @@ struct BoxRows {
 // of the chunk (3-D: the previous plane under the brick, 2-D: the row
 // before the brick for by == 0 lanes), read from global memory before the
 // tile's own data is waited for.  A chunk's first tile has none.
-template <int NDIM, int V>
+template <int NDIM, int V, bool WHOLE = false>
 __device__ __forceinline__ void load_halo(const CompressArgs &a, const TileGeo &q,
                                           float (&hf)[32]) {
 #pragma unroll
   for (int k = 0; k < 32; ++k) hf[k] = 0.0f;
   const GlobalRows<NDIM, V> src{a, q};
   if constexpr (NDIM == 3) {
-    if (q.t > 0) {
+    if (march_halo<NDIM, WHOLE>(q)) {
 #pragma unroll
       for (int iy = 0; iy < 4; ++iy) {
         float h8[8];
@@ -293,7 +337,7 @@ __device__ __forceinline__ void load_halo(const CompressArgs &a, const TileGeo &
       }
     }
   } else if constexpr (NDIM == 2) {
-    if (q.t > 0 && q.by == 0) {
+    if (march_halo<NDIM, WHOLE>(q) && q.by == 0) {
       float h8[8];
       src.row(0, -1, 0, h8);
 #pragma unroll
@@ -455,13 +499,13 @@ __device__ __forceinline__ void residuals_first_f(const Src &src, const TileGeo 
 // Part 2 in fp32: the remaining differences (3-D: D_y, then D_x; 2-D: D_x;
 // 1-D: D_x along the lane's 64 elements, whose left neighbour is the
 // previous lane's last, or for lane 0 the element before the tile).
-template <int NDIM>
+template <int NDIM, bool WHOLE = false>
 __device__ __forceinline__ void residuals_rest_f(const CompressArgs &a, const TileGeo &q, int g,
                                                  float r, float2 (&v)[32]) {
   const unsigned full = 0xffffffffu;
   if constexpr (NDIM == 1) {
     float hq = kRoundMagic;                          // q = 0 before a chunk's first element
-    if (q.t > 0 && g == 0)
+    if (march_halo<NDIM, WHOLE>(q) && g == 0)
       hq = quant_pair((q.x0 - 1 < a.dims[0]) ? __ldcs(a.x + q.x0 - 1) : 0.0f, 0.0f, r).x;
     float left = __shfl_up_sync(full, v[31].y, 1);
     if (g == 0) left = hq;
@@ -482,7 +526,9 @@ __device__ __forceinline__ void residuals_rest_f(const CompressArgs &a, const Ti
         float2 up;
         up.x = __shfl_up_sync(full, v[(ix + 24 + 32 * iz) / 2].x, 4);
         up.y = __shfl_up_sync(full, v[(ix + 24 + 32 * iz) / 2].y, 4);
-        if (q.by == 0) up = make_float2(0.f, 0.f);
+        if (q.by == 0)
+          up = WHOLE && q.y0 > 0 ? make_float2(face_up3(a, q, ix, iz, r), face_up3(a, q, ix + 1, iz, r))
+                                   : make_float2(0.f, 0.f);
 #pragma unroll
         for (int iy = 3; iy >= 1; --iy)
           v[(ix + 8 * iy + 32 * iz) / 2] =
@@ -494,7 +540,10 @@ __device__ __forceinline__ void residuals_rest_f(const CompressArgs &a, const Ti
 #pragma unroll
   for (int row = 0; row < 8; ++row) {              // D_x: element 2j+1 - 2j, 2j - (2j-1)
     float left = __shfl_up_sync(full, v[4 * row + 3].y, 1);
-    if (q.bx == 0) left = 0.f;
+    if (q.bx == 0)
+      left = !(WHOLE && q.x0 > 0) ? 0.f
+             : NDIM == 3            ? face_left3(a, q, row % 4, row / 4, r)
+                                    : face_left2(a, q, row, r);
 #pragma unroll
     for (int j = 3; j >= 1; --j) {
       v[4 * row + j].y = __fsub_rn(v[4 * row + j].y, v[4 * row + j].x);
@@ -544,7 +593,7 @@ __device__ __forceinline__ void mask_padding(const CompressArgs &a, const TileGe
 
 // Part 2: the remaining differences (no more input reads) and code 0 for
 // padding positions.
-template <int NDIM>
+template <int NDIM, bool WHOLE = false>
 __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const TileGeo &q, int g,
                                                float r, int32_t (&v)[64]) {
   using G = Geo<NDIM>;
@@ -555,7 +604,10 @@ __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const Tile
 #pragma unroll
       for (int ix = 0; ix < 8; ++ix) {
         int32_t up = __shfl_up_sync(full, v[ix + 24 + 32 * iz], 4);
-        if (q.by == 0) up = 0;
+        if (q.by == 0)
+          up = WHOLE && q.y0 > 0 ? __float_as_int(q_at(a, q.x0 + ix, q.y0 - 1, q.z0 + iz, r)) -
+                                         __float_as_int(q_at(a, q.x0 + ix, q.y0 - 1, q.z0 + iz - 1, r))
+                                   : 0;
 #pragma unroll
         for (int iy = 3; iy >= 1; --iy) v[ix + 8 * iy + 32 * iz] -= v[ix + 8 * (iy - 1) + 32 * iz];
         v[ix + 32 * iz] -= up;
@@ -566,14 +618,26 @@ __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const Tile
 #pragma unroll
     for (int row = 0; row < 8; ++row) {              // D_x
       int32_t left = __shfl_up_sync(full, v[7 + 8 * row], 1);
-      if (q.bx == 0) left = 0;
+      if (q.bx == 0) {
+        left = 0;
+        if (WHOLE && q.x0 > 0) {
+          // the column before the brick, differenced like the brick's rows
+          const uint64_t x = q.x0 - 1;
+          const int iy = NDIM == 3 ? row % 4 : row, iz = NDIM == 3 ? row / 4 : 0;
+          const uint64_t y = q.y0 + iy, z = q.z0 + iz;
+          left = __float_as_int(q_at(a, x, y, z, r)) - __float_as_int(q_at(a, x, y - 1, z, r));
+          if (NDIM == 3)
+            left -= __float_as_int(q_at(a, x, y, z - 1, r)) -
+                    __float_as_int(q_at(a, x, y - 1, z - 1, r));
+        }
+      }
 #pragma unroll
       for (int ix = 7; ix >= 1; --ix) v[ix + 8 * row] -= v[ix - 1 + 8 * row];
       v[8 * row] -= left;
     }
   } else {
     int32_t hq = (int32_t)kMagicBits;
-    if (q.t > 0 && g == 0)
+    if (march_halo<NDIM, WHOLE>(q) && g == 0)
       hq = quant_bits((q.x0 - 1 < a.dims[0]) ? __ldcs(a.x + q.x0 - 1) : 0.0f, r);
     int32_t left = __shfl_up_sync(full, v[63], 1);
     if (g == 0) left = hq;
@@ -596,15 +660,15 @@ __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const Tile
 
 // all residuals from global memory (the rare escape repack and the outlier
 // pass, when the TMA box no longer holds the tile)
-template <int NDIM, int V>
+template <int NDIM, int V, bool WHOLE = false>
 __device__ __forceinline__ void residuals_global(const CompressArgs &a, uint64_t T, int g,
                                                  float r, int32_t (&v)[64]) {
   const TileGeo q = tile_geo<NDIM>(a, ChunkGrid(a), T, g);
   uint32_t unused = 0;
   float hf[32];
-  load_halo<NDIM, V>(a, q, hf);
+  load_halo<NDIM, V, WHOLE>(a, q, hf);
   residuals_first<NDIM, false>(GlobalRows<NDIM, V>{a, q}, q, g, r, hf, v, unused);
-  residuals_rest<NDIM>(a, q, g, r, v);
+  residuals_rest<NDIM, WHOLE>(a, q, g, r, v);
 }
 
 // residuals -> pairs of 16-bit sign-magnitude codes (Sec. 3.2), even code in
@@ -643,11 +707,11 @@ __device__ __forceinline__ uint32_t pack_codes_escaped(const int32_t (&v)[64], u
 // The rare escape path, kept out of the hot loop: recompute the lane's
 // residuals from global memory, pack them with escapes into pb[32g..32g+31]
 // and return the lane's escape count.
-template <int NDIM, int V>
+template <int NDIM, int V, bool WHOLE = false>
 __device__ __forceinline__ uint32_t escape_repack(const CompressArgs &a, uint64_t T, int g, float r,
                                                uint32_t *pb) {
   int32_t v[64];
-  residuals_global<NDIM, V>(a, T, g, r, v);
+  residuals_global<NDIM, V, WHOLE>(a, T, g, r, v);
   uint32_t w[32];
   const uint32_t n = pack_codes_escaped(v, w);
 #pragma unroll
@@ -711,7 +775,8 @@ __device__ __forceinline__ void finish_tile(const CompressArgs &a, CompShared *s
       const uint64_t inc = excl + d.agg;
       StreamHeader *h = reinterpret_cast<StreamHeader *>(a.out);
       h->magic[0] = 'F'; h->magic[1] = 'Z'; h->magic[2] = 'G'; h->magic[3] = '1';
-      h->version = 1; h->ndim = (uint8_t)NDIM; h->mode = (uint8_t)a.mode;
+      h->version = a.whole ? 2 : 1;         // 2: whole-field residuals
+      h->ndim = (uint8_t)NDIM; h->mode = (uint8_t)a.mode;
       h->reserved0 = 0;
       h->dims[0] = (uint32_t)a.dims[0]; h->dims[1] = (uint32_t)a.dims[1];
       h->dims[2] = (uint32_t)a.dims[2];
@@ -827,7 +892,7 @@ __device__ __forceinline__ void scan_warp(const CompressArgs &a0, const BatchArg
 // One block per SM.  A single field's launch (BATCH = false) reads its field
 // from the kernel parameters; a batched launch reads each unit's field from
 // the batch's descriptors.
-template <int NDIM, int V, bool CHECK, bool TMA, bool BATCH>
+template <int NDIM, int V, bool CHECK, bool TMA, bool BATCH, bool WHOLE = false>
 __global__ void __launch_bounds__(kCompThreads, 1)
     compress_kernel(const CompressArgs a0, const __grid_constant__ CUtensorMap tmap0,
                     const BatchArgs b) {
@@ -971,7 +1036,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       float hf[32];
       // a batch's TMA fields have 16-byte aligned rows: vector halo loads
       if (BATCH && V < 4 && tma_of(cw)) load_halo<NDIM, 4>(a, q, hf);
-      else load_halo<NDIM, V>(a, q, hf);
+      else load_halo<NDIM, V, WHOLE>(a, q, hf);
       float2 vf[32];                                // fp32 residuals, codes 2i, 2i+1 in vf[i]
       uint32_t qmax = 0;
       // a single field's launch compiles one load path; a batch picks per field
@@ -990,7 +1055,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       // is finished
       next_unit();
       if (g == 0 && tma_of(nw)) issue(nw);
-      residuals_rest_f<NDIM>(a, q, g, rt.p.ebx2_r, vf);
+      residuals_rest_f<NDIM, WHOLE>(a, q, g, rt.p.ebx2_r, vf);
       if (CHECK && __any_sync(full, qmax > kBiasedMax) && g == 0) atomicOr(&cur->err, kErrRange);
 
       uint32_t w[32];
@@ -1012,7 +1077,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       if (!narrow && escape) {
         // rare: some |residual| needs more than 15 bits; recompute and repack
         // with escapes out of line (through this round's plane buffer)
-        nout_lane = escape_repack<NDIM, V>(a, T, g, rt.p.ebx2_r, pb);
+        nout_lane = escape_repack<NDIM, V, WHOLE>(a, T, g, rt.p.ebx2_r, pb);
 #pragma unroll
         for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
         __syncwarp();
@@ -1087,7 +1152,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
 // ====================================================================
 constexpr int kOutWarps = 4;                    // outlier pass: warps per block, one tile each
 
-template <int NDIM, int V>
+template <int NDIM, int V, bool WHOLE = false>
 __global__ void __launch_bounds__(kOutWarps * 32)
     outlier_kernel(const CompressArgs a, uint64_t out_section) {
   const int g = threadIdx.x & 31;
@@ -1099,7 +1164,7 @@ __global__ void __launch_bounds__(kOutWarps * 32)
   field_range(a, fmin, fmax, nonfinite);
   const EbParams p = derive_eb(a.mode, a.eb_req, fmin, fmax);
   int32_t v[64];
-  residuals_global<NDIM, V>(a, T, g, p.ebx2_r, v);
+  residuals_global<NDIM, V, WHOLE>(a, T, g, p.ebx2_r, v);
   uint32_t cnt = 0;
 #pragma unroll
   for (int e = 0; e < 64; ++e) cnt += (uint32_t)abs(v[e]) > 32767u;

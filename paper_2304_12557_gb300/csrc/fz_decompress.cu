@@ -27,7 +27,7 @@ constexpr int kDecWarpSmem = kTilesPerChunk * 4096 + 1024;
 constexpr int kDecSmemBytes = kDecWarps * kDecWarpSmem;
 
 struct Hdr {
-  int ndim, mode;
+  int version, ndim, mode;
   uint32_t dims[3];
   uint64_t n_tiles, nnz, nout, n_chunks, ncx, ncy, n_elems;
   float ebx2;
@@ -43,7 +43,10 @@ __device__ Hdr read_header(const DecompressArgs &a) {
   const StreamHeader *s = reinterpret_cast<const StreamHeader *>(a.in);
   if (s->magic[0] != 'F' || s->magic[1] != 'Z' || s->magic[2] != 'G' || s->magic[3] != '1')
     return h;
-  if (s->version != 1 || s->reserved0 != 0 || s->mode > 1) return h;
+  if (!(s->version == 1 || (s->version == 2 && a.accept_whole)) || s->reserved0 != 0 ||
+      s->mode > 1)
+    return h;
+  h.version = s->version;
   h.ndim = s->ndim;
   h.mode = s->mode;
   if (h.ndim < 1 || h.ndim > 3) return h;
@@ -356,7 +359,90 @@ __device__ __forceinline__ uint64_t tile_rank(const ChunkPlan &p, int t) {
   }
 }
 
+// phase 1: L on the chunk's upper faces, from the lanes that hold them
+// (layouts at decompress_chunks)
 template <int NDIM>
+__device__ __forceinline__ void write_faces(const DecompressArgs &a, uint64_t c, int t, int bx,
+                                            int by, int g, const int32_t (&v)[64]) {
+  if constexpr (NDIM == 3) {
+    if (bx == 3) {                                   // x = 31: rows 4by..4by+3, planes 2t, 2t+1
+#pragma unroll
+      for (int iz = 0; iz < 2; ++iz)
+        *reinterpret_cast<int4 *>(a.face[0] + c * 256 + 32 * (2 * t + iz) + 4 * by) =
+            make_int4(v[7 + 32 * iz], v[15 + 32 * iz], v[23 + 32 * iz], v[31 + 32 * iz]);
+    }
+    if (by == 7) {                                   // y = 31
+#pragma unroll
+      for (int iz = 0; iz < 2; ++iz) {
+        int4 *d = reinterpret_cast<int4 *>(a.face[1] + c * 256 + 32 * (2 * t + iz) + 8 * bx);
+        d[0] = make_int4(v[24 + 32 * iz], v[25 + 32 * iz], v[26 + 32 * iz], v[27 + 32 * iz]);
+        d[1] = make_int4(v[28 + 32 * iz], v[29 + 32 * iz], v[30 + 32 * iz], v[31 + 32 * iz]);
+      }
+    }
+    if (t == kTilesPerChunk - 1) {                   // z = 7: the tile's second plane
+#pragma unroll
+      for (int iy = 0; iy < 4; ++iy) {
+        int4 *d = reinterpret_cast<int4 *>(a.face[2] + c * 1024 + 32 * (4 * by + iy) + 8 * bx);
+        d[0] = make_int4(v[32 + 8 * iy], v[33 + 8 * iy], v[34 + 8 * iy], v[35 + 8 * iy]);
+        d[1] = make_int4(v[36 + 8 * iy], v[37 + 8 * iy], v[38 + 8 * iy], v[39 + 8 * iy]);
+      }
+    }
+  } else if constexpr (NDIM == 2) {
+    if (bx == 7) {                                   // x = 63: rows 32t + 8by .. +7
+      int4 *d = reinterpret_cast<int4 *>(a.face[0] + c * 128 + 32 * t + 8 * by);
+      d[0] = make_int4(v[7], v[15], v[23], v[31]);
+      d[1] = make_int4(v[39], v[47], v[55], v[63]);
+    }
+    if (t == kTilesPerChunk - 1 && by == 3) {        // y = 127
+      int4 *d = reinterpret_cast<int4 *>(a.face[1] + c * 64 + 8 * bx);
+      d[0] = make_int4(v[56], v[57], v[58], v[59]);
+      d[1] = make_int4(v[60], v[61], v[62], v[63]);
+    }
+  } else {
+    if (t == kTilesPerChunk - 1 && g == 31) a.face[0][c] = v[63];
+  }
+}
+
+// phase 2: the corrections that change along the chunk's last axis (3-D:
+// A'(y, z) + B'(x, z), 2-D: A'(y)); the others came in with the carry
+template <int NDIM>
+__device__ __forceinline__ void add_corrections(const DecompressArgs &a, uint64_t c, int t,
+                                                int bx, int by, int32_t (&v)[64]) {
+  if constexpr (NDIM == 3) {
+#pragma unroll
+    for (int iz = 0; iz < 2; ++iz) {
+      const uint64_t o = c * 256 + 32 * (2 * t + iz);
+      const int4 ay = __ldg(reinterpret_cast<const int4 *>(a.corr[0] + o + 4 * by));
+      const int4 b0 = __ldg(reinterpret_cast<const int4 *>(a.corr[1] + o + 8 * bx));
+      const int4 b1 = __ldg(reinterpret_cast<const int4 *>(a.corr[1] + o + 8 * bx) + 1);
+      const int32_t A[4] = {ay.x, ay.y, ay.z, ay.w};
+      const int32_t B[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int iy = 0; iy < 4; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < 8; ++ix) v[ix + 8 * iy + 32 * iz] += A[iy] + B[ix];
+    }
+  } else if constexpr (NDIM == 2) {
+    const int4 *p = reinterpret_cast<const int4 *>(a.corr[0] + c * 128 + 32 * t + 8 * by);
+    const int4 a0 = __ldg(p), a1 = __ldg(p + 1);
+    const int32_t A[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+    for (int row = 0; row < 8; ++row)
+#pragma unroll
+      for (int ix = 0; ix < 8; ++ix) v[ix + 8 * row] += A[row];
+  }
+}
+
+// PHASE 0: a version-1 stream written out; 1 and 2: the two passes over a
+// version-2 stream (whole-field Lorenzo).  Phase 1 writes each chunk's
+// chunk-local prefix sums L on its upper faces and nothing else; phase 2
+// adds the cross-chunk corrections to L and writes the field.  Face and
+// correction layouts per chunk c (coordinates inside the chunk):
+//   3-D: [0] (y, z) at c*256 + 32z + y, [1] (x, z) at c*256 + 32z + x,
+//        [2] (x, y) at c*1024 + 32y + x;
+//   2-D: [0] y at c*128 + y, [1] x at c*64 + x;   1-D: [0] at c.
+// Faces hold L at the chunk's last x ([0]), last y ([1]), last z ([2]).
+template <int NDIM, int PHASE>
 __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_t *pbuf,
                                   SetScratch *cur) {
   using G = Geo<NDIM>;
@@ -414,7 +500,7 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
     const uint64_t cx = (uint32_t)c - cr * dx.d, cz = dy.div(cr), cy = cr - (uint32_t)cz * dy.d;
     const bool edge = (cx + 1) * G::CX > h.dims[0] || (cy + 1) * G::CY > h.dims[1] ||
                       (cz + 1) * G::CZ > h.dims[2];
-    // origin of lane g's brick in tile 0, and per-tile / per-row strides
+    // origin of lane g's brick in tile 0
     const int bx = g % G::NBX, by = g / G::NBX;
     uint64_t x0, y0, z0;
     if constexpr (NDIM == 3) {
@@ -429,6 +515,29 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
     int32_t carry[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) carry[e] = 0;
+    if constexpr (PHASE == 2) {
+      // the corrections that do not change along the chunk's last axis
+      // (3-D: C'(x, y), 2-D: B'(x), 1-D: A') and the float bias enter as the
+      // carried plane / row / element, so the prefix sums add them to all
+      if constexpr (NDIM == 3) {
+        const int4 *cc = reinterpret_cast<const int4 *>(a.corr[2] + c * 1024 + 32 * (4 * by) + 8 * bx);
+#pragma unroll
+        for (int iy = 0; iy < 4; ++iy) {
+          const int4 p = __ldg(cc + 8 * iy), q = __ldg(cc + 8 * iy + 1);
+          const int32_t r8[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int ix = 0; ix < 8; ++ix) carry[ix + 8 * iy] = r8[ix] + (int32_t)kMagicBits;
+        }
+      } else if constexpr (NDIM == 2) {
+        const int4 *cb = reinterpret_cast<const int4 *>(a.corr[1] + c * 64 + 8 * bx);
+        const int4 p = __ldg(cb), q = __ldg(cb + 1);
+        const int32_t r8[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int ix = 0; ix < 8; ++ix) carry[ix] = r8[ix] + (int32_t)kMagicBits;
+      } else {
+        carry[0] = __ldg(a.corr[0] + c) + (int32_t)kMagicBits;
+      }
+    }
 #pragma unroll 1
     for (int t = 0; t < kTilesPerChunk; ++t) {
       cp_async_wait<3>();                // this tile's group (3 newer ones may pend)
@@ -510,8 +619,13 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
         }
       }
       // the chunk origin carries the float bias of 1.5*2^23 into every q
-      if (t == 0 && g == 0) v[0] += (int32_t)kMagicBits;
+      if (PHASE == 0 && t == 0 && g == 0) v[0] += (int32_t)kMagicBits;
       inverse_lorenzo<NDIM>(v, carry, g);
+      if constexpr (PHASE == 1) {
+        write_faces<NDIM>(a, c, t, bx, by, g, v);
+        continue;
+      }
+      if constexpr (PHASE == 2) add_corrections<NDIM>(a, c, t, bx, by, v);
       // q -> fl(float(q) * 2eb), 8-float rows
       auto row_floats = [&](int row, float (&f)[8]) {
 #pragma unroll
@@ -608,9 +722,14 @@ __global__ void __launch_bounds__(kOffChunks) dec_offsets_kernel(const Decompres
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     SetScratch *nx = a.set_next;
     nx->ticket = 0; nx->err = 0; nx->nnz = 0; nx->nout = 0; nx->n_chunks = 0; nx->hdr_nout = 0;
+    nx->version = 0;
     if (!h.ok) atomicOr(&cur->err, kErrCorrupt);
     else if (a.out_cap_elems < h.n_elems) atomicOr(&cur->err, kErrCapacity);
     else if (h.n_chunks > a.status_cap) atomicOr(&cur->err, kErrCorrupt);
+    cur->version = h.ok ? (uint32_t)h.version : 0;
+    cur->ndim = h.ok ? (uint32_t)h.ndim : 0;
+    cur->ncx = h.ok ? (uint32_t)h.ncx : 0;
+    cur->ncy = h.ok ? (uint32_t)h.ncy : 0;
     cur->n_chunks = h.ok ? h.n_chunks : 0;
     cur->nnz = h.ok ? h.nnz : 0;
     cur->hdr_nout = h.ok ? (uint32_t)h.nout : 0;
@@ -678,11 +797,27 @@ __global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const Dec
   const int w = threadIdx.x >> 5;
   const Hdr h = read_header(a);
   if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
+  if (h.version != 1) return;            // version 2: phases 1 and 2 follow
   uint32_t *pbuf = dsmem + w * (kDecWarpSmem / 4);
   grid_dependency_wait();                // the offsets pass's chunk offsets
-  if (h.ndim == 3) decompress_chunks<3>(a, h, pbuf, cur);
-  else if (h.ndim == 2) decompress_chunks<2>(a, h, pbuf, cur);
-  else decompress_chunks<1>(a, h, pbuf, cur);
+  if (h.ndim == 3) decompress_chunks<3, 0>(a, h, pbuf, cur);
+  else if (h.ndim == 2) decompress_chunks<2, 0>(a, h, pbuf, cur);
+  else decompress_chunks<1, 0>(a, h, pbuf, cur);
+}
+
+// phases 1 and 2 of a version-2 stream (after the offsets pass and phase 0)
+template <int PHASE>
+__global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_whole_kernel(const DecompressArgs a) {
+  extern __shared__ __align__(16) uint32_t dsmem[];
+  SetScratch *cur = a.set_cur;
+  const int w = threadIdx.x >> 5;
+  const Hdr h = read_header(a);
+  if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
+  if (h.version != 2) return;
+  uint32_t *pbuf = dsmem + w * (kDecWarpSmem / 4);
+  if (h.ndim == 3) decompress_chunks<3, PHASE>(a, h, pbuf, cur);
+  else if (h.ndim == 2) decompress_chunks<2, PHASE>(a, h, pbuf, cur);
+  else decompress_chunks<1, PHASE>(a, h, pbuf, cur);
 }
 
 // The grid: enough blocks for max_chunks chunks, at most two per SM (the
@@ -706,12 +841,19 @@ cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s)
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  // phases 1 and 2 wait for everything before them (no dependency wait inside)
+  cfg.numAttrs = a.phase == 0 ? 1 : 0;
+  if (a.phase == 1) return cudaLaunchKernelEx(&cfg, decompress_whole_kernel<1>, a);
+  if (a.phase == 2) return cudaLaunchKernelEx(&cfg, decompress_whole_kernel<2>, a);
   return cudaLaunchKernelEx(&cfg, decompress_kernel, a);
 }
 
 int decompress_blocks_per_sm() {
   int n = 0;
+  cudaFuncSetAttribute(decompress_whole_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kDecSmemBytes);
+  cudaFuncSetAttribute(decompress_whole_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kDecSmemBytes);
   cudaFuncSetAttribute(decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kDecSmemBytes);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decompress_kernel, kDecWarps * 32,

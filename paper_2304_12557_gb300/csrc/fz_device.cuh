@@ -108,7 +108,10 @@ struct SetScratch {
   uint64_t nout;        // compressor: total outliers; decompressor: matched
   uint64_t n_chunks;    // decompressor: chunks found in the stream header
   uint32_t hdr_nout;    // decompressor: the header's outlier count
-  uint32_t pad[7];
+  uint32_t version;     // decompressor: the header's stream version (0: invalid)
+  uint32_t ndim;        // decompressor: the header's dimensionality
+  uint32_t ncx, ncy;    // decompressor: the chunk grid's x and y extents
+  uint32_t pad[3];
 };
 static_assert(sizeof(SetScratch) == 64, "scratch block is 64 bytes");
 

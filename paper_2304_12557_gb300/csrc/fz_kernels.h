@@ -32,6 +32,8 @@ struct CompressArgs {
   float range_lo, range_hi;
   int use_tma;                 // batches: this field's tiles come by TMA
   int ndim;                    // batches: the field's dimensionality
+  int whole;                   // whole-field Lorenzo (stream version 2): residuals
+                               // across chunk faces
   SetScratch *set_cur, *set_next;
   uint64_t *status_cur, *status_next;
   uint32_t *tile_out_prefix;   // per tile: exclusive outlier prefix
@@ -54,7 +56,25 @@ struct DecompressArgs {
   uint32_t *chunk_olo;         // per chunk: first outlier record (offsets pass)
   uint64_t wait_limit_ns;
   uint64_t skip_publish_chunk;
+  // Stream version 2 (whole-field Lorenzo).  accept_whole: the offsets pass
+  // takes version-2 headers (else they fail the header check).  phase 0:
+  // version 1 written out, a version-2 stream left alone (the caller runs
+  // phases 1 and 2); phase 1: each chunk's chunk-local prefix sums L on its
+  // three upper faces to face[0..2]; phase 2: L plus the cross-chunk
+  // corrections corr[0..2], written out.  Face layouts in fz_whole.cu.
+  int accept_whole;
+  int phase;
+  int32_t *face[3];
+  const int32_t *corr[3];
 };
+
+// Version-2 decompression, between phases 1 and 2: the cross-chunk sums of
+// the faces (fz_whole.cu).  face[k] and work[k] hold face_elems(ndim, k)
+// words per chunk; the corrections end up in corr[k], which points into
+// face or work.  n_chunk[3]: the chunk grid.
+int whole_face_elems(int ndim, int k);
+cudaError_t launch_whole_scans(int ndim, const uint32_t n_chunk[3], int32_t *const face[3],
+                               int32_t *const work[3], const int32_t *corr[3], cudaStream_t s);
 
 void launch_range(const float *x, uint64_t n, float2 *partial, int nblocks,
                   RangeResult *res, cudaStream_t s);

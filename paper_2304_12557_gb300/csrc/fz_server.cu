@@ -551,6 +551,7 @@ int fz_server_submit(fz_server *S, const fz_request *q, uint64_t *id) {
     fz_info info;
     if (fz_inspect(q->h_in, q->in_bytes, &info) != FZ_OK) return FZ_ERR_CORRUPT;
     if (info.stream_bytes != q->in_bytes) return FZ_ERR_CORRUPT;
+    if (info.version != 1) return FZ_ERR_VERSION;
     r.in_bytes = q->in_bytes;
     r.n_elems = info.dims[0] * info.dims[1] * info.dims[2];
     r.n_chunks = info.n_tiles / fz::kTilesPerChunk;

@@ -42,6 +42,8 @@ int concat_plan(const uint8_t (*hdrs)[64], const uint64_t *sizes, int n, ConcatP
     fz_info f{};
     if (sizes[i] < 64 || fz_inspect(hdrs[i], 64, &f) != FZ_OK) return FZ_ERR_CORRUPT;
     if (f.stream_bytes != sizes[i]) return FZ_ERR_CORRUPT;
+    // whole-field residuals cross slab faces: such slabs do not concatenate
+    if (f.version != 1) return FZ_ERR_VERSION;
     const int ax = f.ndim - 1;
     if (i == 0) {
       first = f;

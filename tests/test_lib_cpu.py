@@ -64,6 +64,22 @@ def test_inspect_golden(lib, name):
     assert info["stream_bytes"] == rec["size"]
     assert info["nnz_blocks"] == int(rec["header"]["nnz"])
     assert info["eb"] == float(rec["header"]["eb_f"])
+    assert info["version"] == 1
+
+
+def test_inspect_reads_version_2(lib):
+    import oracle
+    from paper_2304_12557_gb300 import fields
+    x = fields.bumps3d(32)
+    st, s = oracle.compress(x, 3, oracle.EB_REL, 1e-3, whole=True)
+    assert st == oracle.OK
+    info = fz.inspect(s[:64])
+    assert info["version"] == 2 and info["stream_bytes"] == len(s)
+    bad = bytearray(s[:64])
+    bad[4] = 3                                           # no version 3
+    with pytest.raises(fz.FZError) as e:
+        fz.inspect(bytes(bad))
+    assert e.value.status == fz.ERR_CORRUPT
 
 
 def test_inspect_rejects_corrupt(lib):

@@ -131,6 +131,12 @@ def test_concat_rejects_inconsistent_parts():
     with pytest.raises(fz.FZError) as e:                # another mode
         fz.concat_streams_host([p[0], rel])
     assert e.value.status == fz.ERR_CORRUPT
+    # whole-field residuals cross slab faces: version-2 parts are refused
+    _, w0 = oracle.compress(np.ascontiguousarray(x[:32]), 3, fz.EB_ABS, 1e-3, whole=True)
+    _, w1 = oracle.compress(np.ascontiguousarray(x[32:]), 3, fz.EB_ABS, 1e-3, whole=True)
+    with pytest.raises(fz.FZError) as e:
+        fz.concat_streams_host([w0, w1])
+    assert e.value.status == fz.ERR_VERSION
 
 
 def test_oracle_ranged_reduces_to_rel_and_abs():
