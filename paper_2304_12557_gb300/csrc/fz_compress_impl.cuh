@@ -412,18 +412,20 @@ __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q
 // difference is below 2^23, a second below 2^24.  A third (3-D) may round
 // only beyond 2^24, where the residual is an escape either way (the escape
 // path recomputes such a tile in integers).  Pairs of x-neighbours go through
-// the packed f32x2 pipe: the multiply and the differences.  The rounding add
-// stays scalar: a paired multiply followed by a paired add is contracted into
-// one fused multiply-add by this toolchain, even with explicit .rn, which
-// rounds the exact product instead of fl(x * r) and changes q where fl(x * r)
-// falls on a tie.
+// the packed f32x2 pipe: the multiply, the rounding add and the differences.
+// The rounding add fl(p + 1.5 * 2^23) is a paired FMA with the exact factor
+// 1: a paired multiply followed by a paired add is contracted into one fused
+// multiply-add by this toolchain, even with explicit .rn, which rounds the
+// exact product instead of fl(x * r) and changes q where fl(x * r) falls on a
+// tie; an FMA whose product is already an FMA operand is left alone.
 __device__ __forceinline__ float2 quant_pair(float x0, float x1, float r) {
   float p0, p1;
   asm("{\n .reg .b64 xa, ra, pa;\n mov.b64 xa, {%2, %3};\n mov.b64 ra, {%4, %4};\n"
       " mul.rn.f32x2 pa, xa, ra;\n mov.b64 {%0, %1}, pa;\n}"
       : "=f"(p0), "=f"(p1)
       : "f"(x0), "f"(x1), "f"(r));
-  return make_float2(__fadd_rn(p0, kRoundMagic), __fadd_rn(p1, kRoundMagic));
+  return __ffma2_rn(make_float2(p0, p1), make_float2(1.0f, 1.0f),
+                    make_float2(kRoundMagic, kRoundMagic));
 }
 __device__ __forceinline__ float2 sub_pair(float2 a, float2 b) {   // a - b, one rounding
   return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
