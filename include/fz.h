@@ -300,8 +300,10 @@ typedef struct fz_batch fz_batch;
 
 /* Plan a batch of n fields on ctx's device: validates every field (FZ_ERR_ARG;
  * FZ_ERR_CAPACITY when an output cannot hold the header and flags) and
- * allocates the batch's descriptors and scratch (FZ_ERR_CUDA).  The batch
- * keeps ctx for later calls; destroy the batch before the context. */
+ * allocates the batch's descriptors and scratch (FZ_ERR_CUDA).  Fields
+ * whose rows are 16-byte aligned take TMA tile loads, the others direct
+ * loads (load path [1] of fz_batch_autotune).  The batch keeps ctx for later
+ * calls; destroy the batch before the context. */
 int fz_batch_create(fz_ctx *ctx, const fz_field *fields, int n, fz_batch **batch);
 
 /* Release a batch.  NULL is allowed. */
@@ -316,14 +318,22 @@ int fz_batch_compress(fz_batch *batch, uint64_t *out_sizes, int *statuses, void 
 /* Capture runs in a CUDA graph (default on) or launch them directly. */
 int fz_batch_set_graph(fz_batch *batch, int on);
 
-/* Autotune the batch's load path: time `reps` runs with TMA tile loads for
- * the fields whose rows allow them (2-D/3-D, rows 16-byte aligned) and
- * `reps` runs with direct loads for every field, and keep the faster.  The
- * outputs are overwritten by the trial runs.  fz_batch_tuning reports the
- * choice (1: TMA) and the median run times in ms ([0] direct, [1] TMA; 0
- * before tuning). */
+/* Autotune the batch's load path over three choices, `reps` timed runs
+ * each: [0] direct loads for every field; [1] TMA tile loads for the
+ * fields whose rows allow them (2-D/3-D, rows 16-byte aligned), direct
+ * loads for the others (the default); [2] TMA tile loads for every 2-D/3-D
+ * field, the others through staging copies with the row pitch padded to 4
+ * elements, written by each run's first pass (about 4 bytes of device
+ * memory per element of those fields).  Keeps the fastest.
+ * The outputs are overwritten by the trial runs.  fz_batch_tuning reports
+ * the choice (tma_on, staged) and the median run times in ms (0 before
+ * tuning). */
 int fz_batch_autotune(fz_batch *batch, int reps, void *stream);
-int fz_batch_tuning(const fz_batch *batch, int *tma_on, double ms[2]);
+/* Set the load path by hand: tma 0 (direct loads), 1 (TMA for aligned
+ * rows); staged 1 with tma 1 (TMA for every 2-D/3-D field).  Allocates the
+ * staging copies when first needed.  FZ_OK, FZ_ERR_ARG or FZ_ERR_CUDA. */
+int fz_batch_set_load_path(fz_batch *batch, int tma, int staged);
+int fz_batch_tuning(const fz_batch *batch, int *tma_on, int *staged, double ms[3]);
 
 /* ---------------------------------------------------------------------
  * A request server with continuous batching.  Clients submit compress and

@@ -45,7 +45,7 @@ C_API = ["fz_create", "fz_destroy", "fz_compress_bound", "fz_stream_min_bytes",
          "fz_compress_ranged", "fz_shard_extent", "fz_concat_streams",
          "fz_concat_streams_host", "fz_batch_create", "fz_batch_destroy",
          "fz_batch_compress", "fz_batch_set_graph", "fz_batch_autotune",
-         "fz_batch_tuning", "fz_server_create", "fz_server_destroy",
+         "fz_batch_tuning", "fz_batch_set_load_path", "fz_server_create", "fz_server_destroy",
          "fz_server_submit", "fz_server_poll", "fz_server_fetch",
          "fz_server_get_stats", "fz_server_request_info", "fz_compress_staged", "fz_set_staged_shuffle",
          "fz_compress_noalloc",
@@ -173,7 +173,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         L.fz_batch_set_graph.argtypes = [_vp, ctypes.c_int]
         L.fz_batch_autotune.argtypes = [_vp, ctypes.c_int, _vp]
         L.fz_batch_tuning.argtypes = [_vp, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_double)]
+        L.fz_batch_set_load_path.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
         L.fz_server_create.argtypes = [ctypes.c_int, _u64, ctypes.c_int,
                                        ctypes.POINTER(_vp)]
         L.fz_server_destroy.argtypes = [_vp]
@@ -318,13 +320,21 @@ class Batch:
             raise FZError(st, "fz_batch_autotune")
         return self.tuning()
 
+    def set_load_path(self, tma: bool, staged: bool):
+        st = self._L.fz_batch_set_load_path(self._h, int(bool(tma)), int(bool(staged)))
+        if st != OK:
+            raise FZError(st, "fz_batch_set_load_path")
+
     def tuning(self):
-        on = ctypes.c_int()
-        ms = (ctypes.c_double * 2)()
-        st = self._L.fz_batch_tuning(self._h, ctypes.byref(on), ms)
+        """The load path in use (tma, staged) and the tuning runs' median
+        times: direct loads, TMA for aligned rows, TMA with staging copies."""
+        on, staged = ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * 3)()
+        st = self._L.fz_batch_tuning(self._h, ctypes.byref(on), ctypes.byref(staged), ms)
         if st != OK:
             raise FZError(st, "fz_batch_tuning")
-        return {"tma": bool(on.value), "ms_direct": ms[0], "ms_tma": ms[1]}
+        return {"tma": bool(on.value), "staged": bool(staged.value), "ms_direct": ms[0],
+                "ms_tma": ms[1], "ms_tma_staged": ms[2]}
 
     def close(self):
         if self._h:

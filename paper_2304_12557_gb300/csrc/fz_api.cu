@@ -409,6 +409,7 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
   fz::CompressArgs a{};
   a.x = d_in;
   for (int i = 0; i < 3; ++i) a.dims[i] = sh.d[i];
+  a.pitch = sh.d[0];
   a.ncx = (uint32_t)sh.ncx;
   a.ncy = (uint32_t)sh.ncy;
   a.n_chunks = sh.n_chunks;
@@ -634,6 +635,7 @@ int fz_compress_staged(fz_ctx *c, const float *d_in, const uint64_t dims[3], int
   fz::CompressArgs a{};
   a.x = d_in;
   for (int i = 0; i < 3; ++i) a.dims[i] = sh.d[i];
+  a.pitch = sh.d[0];
   a.ncx = (uint32_t)sh.ncx;
   a.ncy = (uint32_t)sh.ncy;
   a.n_chunks = sh.n_chunks;

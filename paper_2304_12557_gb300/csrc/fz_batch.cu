@@ -53,12 +53,6 @@ struct RangeSlots {
   uint32_t inv_min, max, nonfinite, pad;
 };
 
-struct RangeSeg {
-  const float *x;
-  uint64_t n;          // elements in this segment
-  uint32_t field;
-  uint32_t pad;
-};
 
 constexpr int kRangeSegElems = 1 << 16;   // 256 KiB per segment
 
@@ -66,8 +60,18 @@ __global__ void __launch_bounds__(256) range_batch_kernel(const RangeSeg *segs, 
                                                           RangeSlots *slots) {
   for (uint64_t sgi = blockIdx.x; sgi < n_segs; sgi += gridDim.x) {
     const RangeSeg sg = segs[sgi];
+    if (!sg.range && !sg.dst) continue;              // the same in the whole block
     float lo = INFINITY, hi = -INFINITY;
     uint32_t bad = 0;
+    // element l of the segment into the staging copy: row row0 + q, column
+    // col0 + l - q X (col0 + l < 2^31: the host stages rows below 2^30 only)
+    auto stage = [&](uint64_t l, float a) {
+      if (sg.dst) {
+        const uint32_t t = sg.col0 + (uint32_t)l;
+        const uint32_t q = sg.X.div(t);
+        sg.dst[(sg.row0 + q) * sg.pitch + (t - q * sg.X.d)] = a;
+      }
+    };
     // elements before the first 16-byte boundary, then 16-byte loads
     const uint64_t head0 = ((16u - (reinterpret_cast<uintptr_t>(sg.x) & 15u)) & 15u) / 4;
     const uint64_t head = head0 < sg.n ? head0 : sg.n;
@@ -76,6 +80,7 @@ __global__ void __launch_bounds__(256) range_batch_kernel(const RangeSeg *segs, 
       bad |= (__float_as_uint(a) & 0x7F800000u) == 0x7F800000u;
       lo = fminf(lo, a);
       hi = fmaxf(hi, a);
+      stage(threadIdx.x, a);
     }
     uint64_t done = head;
     {
@@ -89,6 +94,7 @@ __global__ void __launch_bounds__(256) range_batch_kernel(const RangeSeg *segs, 
           bad |= (__float_as_uint(a[k]) & 0x7F800000u) == 0x7F800000u;
           lo = fminf(lo, a[k]);
           hi = fmaxf(hi, a[k]);
+          stage(head + 4 * i + k, a[k]);
         }
       }
       done = head + n4 * 4;
@@ -98,6 +104,7 @@ __global__ void __launch_bounds__(256) range_batch_kernel(const RangeSeg *segs, 
       bad |= (__float_as_uint(a) & 0x7F800000u) == 0x7F800000u;
       lo = fminf(lo, a);
       hi = fmaxf(hi, a);
+      stage(i, a);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -105,7 +112,7 @@ __global__ void __launch_bounds__(256) range_batch_kernel(const RangeSeg *segs, 
       hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     bad = __any_sync(0xffffffffu, bad);
-    if ((threadIdx.x & 31) == 0) {
+    if ((threadIdx.x & 31) == 0 && sg.range) {
       RangeSlots *s = slots + sg.field;
       if (bad) atomicOr(&s->nonfinite, 1u);
       if (lo <= hi) {                      // the warp saw finite values
@@ -267,6 +274,9 @@ cudaError_t batch_kernel_attrs() {
 
 void BatchWs::release() {
   if (d_mem_) cudaFree(d_mem_);
+  if (d_stage_) cudaFree(d_stage_);
+  d_stage_ = nullptr;
+  stage_mem_ = 0;
   if (h_stage_) cudaFreeHost(h_stage_);
   if (h_res_) cudaFreeHost(h_res_);
   d_mem_ = nullptr;
@@ -284,8 +294,9 @@ int BatchWs::set(int device, const fz_field *fields, int n, cudaStream_t s) {
   cudaDeviceGetAttribute(&num_sms_, cudaDevAttrMultiProcessorCount, device);
   if (num_sms_ < 1) num_sms_ = 1;
   std::vector<CompressArgs> args(n);
-  std::vector<uint64_t> tile_off(n), status_off(n);
+  std::vector<uint64_t> tile_off(n), status_off(n), stage_off(n, ~0ull);
   std::vector<RangeSeg> segs;
+  uint64_t stage_floats = 0;
   WsClass by_ndim[4];
   for (int d = 1; d <= 3; ++d) by_ndim[d].ndim = d;
   uint64_t total_tiles = 0, total_status = 0;
@@ -305,6 +316,7 @@ int BatchWs::set(int device, const fz_field *fields, int n, cudaStream_t s) {
     a.x = h.d_in;
     a.ndim = h.ndim;
     for (int i = 0; i < 3; ++i) a.dims[i] = d[i];
+    a.pitch = d[0];
     a.ncx = ncx;
     a.ncy = ncy;
     a.n_chunks = nch;
@@ -323,11 +335,28 @@ int BatchWs::set(int device, const fz_field *fields, int n, cudaStream_t s) {
     c.fields.push_back((uint32_t)f);
     if (h.mode == FZ_EB_ABS) c.check = true;
     c.n_units += units;
-    if (h.mode == FZ_EB_REL) {
+    // rows not 16-byte aligned (below 2^30 elements): a staging copy with
+    // the row pitch rounded up to 4 elements, 256-byte aligned
+    const bool stageable = h.ndim >= 2 && !tma_eligible(h) && d[0] < (1ull << 30);
+    const uint64_t pitch = (d[0] + 3) / 4 * 4;
+    if (stageable) {
+      stage_off[f] = stage_floats;
+      stage_floats += (pitch * d[1] * d[2] + 63) / 64 * 64;
+    }
+    if (h.mode == FZ_EB_REL || stageable) {
       const uint64_t elems = d[0] * d[1] * d[2];
-      for (uint64_t s0 = 0; s0 < elems; s0 += kRangeSegElems)
-        segs.push_back({h.d_in + s0, std::min<uint64_t>(kRangeSegElems, elems - s0),
-                        (uint32_t)f, 0});
+      for (uint64_t s0 = 0; s0 < elems; s0 += kRangeSegElems) {
+        RangeSeg sg{};
+        sg.x = h.d_in + s0;
+        sg.n = std::min<uint64_t>(kRangeSegElems, elems - s0);
+        sg.field = (uint32_t)f;
+        sg.range = h.mode == FZ_EB_REL;
+        sg.row0 = s0 / d[0];
+        sg.col0 = (uint32_t)(s0 % d[0]);
+        sg.pitch = (uint32_t)pitch;
+        sg.X = FastDiv((uint32_t)std::min<uint64_t>(d[0], 0xFFFFFFFFull));
+        segs.push_back(sg);
+      }
     }
   }
   std::vector<WsClass> cls;
@@ -422,7 +451,6 @@ int BatchWs::set(int device, const fz_field *fields, int n, cudaStream_t s) {
       for (uint64_t k = 0; k < units; ++k) map[u++] = make_uint2(f, (uint32_t)k);
     }
   }
-  if (!segs.empty()) std::memcpy(hs + o_segs, segs.data(), segs.size() * sizeof(RangeSeg));
   std::memcpy(hs + o_toff, tile_off.data(), n * sizeof(uint64_t));
   host_.assign(fields, fields + n);
   args_.swap(args);
@@ -431,6 +459,10 @@ int BatchWs::set(int device, const fz_field *fields, int n, cudaStream_t s) {
   total_tiles_ = total_tiles;
   total_units_ = total_units;
   n_segs_ = segs.size();
+  segs_.swap(segs);
+  stage_off_.swap(stage_off);
+  stage_floats_ = stage_floats;
+  o_segs_ = o_segs;
   return upload(s);
 }
 
@@ -441,21 +473,42 @@ int BatchWs::upload(cudaStream_t s) {
   const size_t o_args = reinterpret_cast<uint8_t *>(d_args_) - static_cast<uint8_t *>(d_mem_);
   const size_t o_tmaps = reinterpret_cast<uint8_t *>(d_tmaps_) - static_cast<uint8_t *>(d_mem_);
   CUtensorMap *maps = reinterpret_cast<CUtensorMap *>(hs + o_tmaps);
+  const bool staged = tma_on_ && stage_on_ && stage_floats_ > 0;
+  if (staged && stage_mem_ < stage_floats_ * 4) {
+    if (d_stage_) cudaFree(d_stage_);
+    d_stage_ = nullptr;
+    stage_mem_ = 0;
+    if (cudaMalloc(&d_stage_, stage_floats_ * 4) != cudaSuccess) return FZ_ERR_CUDA;
+    stage_mem_ = stage_floats_ * 4;
+  }
   for (uint32_t f = 0; f < n_; ++f) {
     CompressArgs &a = args_[f];
     std::memset(&maps[f], 0, sizeof(CUtensorMap));
+    a.x = host_[f].d_in;
+    a.pitch = a.dims[0];
     a.use_tma = 0;
-    if (tma_on_ && tma_eligible(host_[f]) && encode_field_tmap(a.ndim, a.dims, a.x, &maps[f]))
+    if (staged && stage_off_[f] != ~0ull) {
+      a.x = d_stage_ + stage_off_[f];
+      a.pitch = (a.dims[0] + 3) / 4 * 4;
+      if (!encode_field_tmap_pitch(a.ndim, a.dims, a.pitch, a.x, &maps[f])) return FZ_ERR_CUDA;
       a.use_tma = 1;
+    } else if (tma_on_ && tma_eligible(host_[f]) &&
+               encode_field_tmap(a.ndim, a.dims, a.x, &maps[f])) {
+      a.use_tma = 1;
+    }
   }
+  for (RangeSeg &sg : segs_)
+    sg.dst = staged && stage_off_[sg.field] != ~0ull ? d_stage_ + stage_off_[sg.field] : nullptr;
+  if (!segs_.empty()) std::memcpy(hs + o_segs_, segs_.data(), segs_.size() * sizeof(RangeSeg));
   std::memcpy(hs + o_args, args_.data(), n_ * sizeof(CompressArgs));
   if (cudaMemcpyAsync(d_mem_, h_stage_, desc_bytes_, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return FZ_ERR_CUDA;
   return FZ_OK;
 }
 
-int BatchWs::set_tma(bool on, cudaStream_t s) {
-  tma_on_ = on;
+int BatchWs::set_load_path(bool tma, bool staged, cudaStream_t s) {
+  tma_on_ = tma;
+  stage_on_ = staged;
   return n_ ? upload(s) : FZ_OK;
 }
 
@@ -551,7 +604,7 @@ struct fz_batch {
   fz::BatchWs ws;
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
-  double tune_ms[2] = {0, 0};       // [direct, TMA] when tuned
+  double tune_ms[3] = {0, 0, 0};    // [direct, TMA, TMA + staging] when tuned
 };
 
 namespace {
@@ -588,6 +641,7 @@ int fz_batch_create(fz_ctx *ctx, const fz_field *fields, int n, fz_batch **out) 
   if (!B) return FZ_ERR_CUDA;
   B->ctx = ctx;
   B->device = device;
+  B->ws.set_load_path(true, false, nullptr);        // flags only: no fields yet
   int st = B->ws.set(device, fields, n, nullptr);
   if (st == FZ_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = FZ_ERR_CUDA;
   if (st != FZ_OK) {
@@ -656,11 +710,16 @@ int fz_batch_autotune(fz_batch *B, int reps, void *stream) {
   std::vector<uint64_t> sizes(n);
   std::vector<int> sts(n);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the load paths: direct loads everywhere; TMA boxes for the fields with
+  // 16-byte aligned rows; TMA boxes for every 2-D/3-D field, through
+  // staging copies of the others
+  const bool tma[3] = {false, true, true}, staged[3] = {false, false, true};
   double best = 0.0;
-  bool best_tma = B->ws.tma_on();
-  for (int choice = 0; choice < 2; ++choice) {
+  int best_c = 2;
+  for (int c = 0; c < 3; ++c) {
     drop_graph(B);
-    if (B->ws.set_tma(choice == 1, s) != FZ_OK || cudaStreamSynchronize(s) != cudaSuccess)
+    if (B->ws.set_load_path(tma[c], staged[c], s) != FZ_OK ||
+        cudaStreamSynchronize(s) != cudaSuccess)
       return FZ_ERR_CUDA;
     fz_batch_compress(B, sizes.data(), sts.data(), stream);       // warm-up (and graph)
     std::vector<double> t;
@@ -672,23 +731,35 @@ int fz_batch_autotune(fz_batch *B, int reps, void *stream) {
       t.push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
     }
     std::sort(t.begin(), t.end());
-    B->tune_ms[choice] = t[t.size() / 2];
-    if (choice == 0 || B->tune_ms[choice] < best) {
-      best = B->tune_ms[choice];
-      best_tma = choice == 1;
+    B->tune_ms[c] = t[t.size() / 2];
+    if (c == 0 || B->tune_ms[c] < best) {
+      best = B->tune_ms[c];
+      best_c = c;
     }
   }
   drop_graph(B);
-  if (B->ws.set_tma(best_tma, s) != FZ_OK || cudaStreamSynchronize(s) != cudaSuccess)
+  if (B->ws.set_load_path(tma[best_c], staged[best_c], s) != FZ_OK ||
+      cudaStreamSynchronize(s) != cudaSuccess)
     return FZ_ERR_CUDA;
   return FZ_OK;
 }
 
-int fz_batch_tuning(const fz_batch *B, int *tma_on, double ms[2]) {
-  if (!B || !tma_on || !ms) return FZ_ERR_ARG;
+int fz_batch_set_load_path(fz_batch *B, int tma, int staged) {
+  if (!B || (tma != 0 && tma != 1) || (staged != 0 && staged != 1)) return FZ_ERR_ARG;
+  DeviceScope scope(B->device);
+  if (!scope.ok) return FZ_ERR_CUDA;
+  drop_graph(B);
+  if (B->ws.set_load_path(tma == 1, staged == 1, nullptr) != FZ_OK ||
+      cudaStreamSynchronize(nullptr) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  return FZ_OK;
+}
+
+int fz_batch_tuning(const fz_batch *B, int *tma_on, int *staged, double ms[3]) {
+  if (!B || !tma_on || !staged || !ms) return FZ_ERR_ARG;
   *tma_on = B->ws.tma_on() ? 1 : 0;
-  ms[0] = B->tune_ms[0];
-  ms[1] = B->tune_ms[1];
+  *staged = B->ws.staged_on() ? 1 : 0;
+  for (int c = 0; c < 3; ++c) ms[c] = B->tune_ms[c];
   return FZ_OK;
 }
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "fz.h"
+#include "fz_device.cuh"
 
 namespace fz {
 
@@ -18,7 +19,24 @@ struct FieldRt;
 struct RangeResult;
 struct SetScratch;
 struct RangeSlots;
-struct RangeSeg;
+
+// A segment of one field for the batch's first pass: its value range (a
+// relative bound's field) and, for a field whose rows are not 16-byte
+// aligned, its elements copied into a staging copy with a padded row pitch
+// that the compressor then reads with TMA boxes.
+struct RangeSeg {
+  const float *x;
+  uint64_t n;          // elements in this segment
+  uint32_t field;
+  uint32_t range;      // 1: the field's relative bound needs its range
+  float *dst;          // the field's staging copy (NULL: none this run)
+  uint64_t row0;       // x row of the segment's first element
+  uint32_t col0;       // and its column
+  uint32_t pitch;      // the staging copy's row pitch (elements)
+  FastDiv X;           // the field's row length dims[0]
+  uint32_t pad;
+};
+
 
 struct WsClass {                   // the fields of one dimensionality
   int ndim = 0;
@@ -47,12 +65,16 @@ class BatchWs {
   // Per-field sizes and statuses of the last run (after it has completed);
   // ctx (may be NULL) classifies absolute-bound failures as NaN/Inf or range.
   int collect(fz_ctx *ctx, uint64_t *sizes, int *statuses, cudaStream_t s) const;
-  // Re-encode the tensor maps for a new load-path choice (idle workspace).
-  int set_tma(bool on, cudaStream_t s);
+  // Re-encode the tensor maps for a new load-path choice (idle workspace):
+  // tma, TMA boxes for fields whose rows are 16-byte aligned; staged (with
+  // tma), also for the others, through a staging copy with a padded row
+  // pitch that the first pass writes (device memory grown as needed).
+  int set_load_path(bool tma, bool staged, cudaStream_t s);
   void release();
 
   uint32_t size() const { return n_; }
   bool tma_on() const { return tma_on_; }
+  bool staged_on() const { return tma_on_ && stage_on_; }
   uint64_t wait_limit_ns = 2000000000ull;
 
  private:
@@ -61,6 +83,15 @@ class BatchWs {
   int device_ = 0;
   int num_sms_ = 1;
   bool tma_on_ = true;
+  bool stage_on_ = false;
+  // per field: its offset (floats) in the staging memory, or ~0 when its
+  // rows are read in place; the first pass's segments (host copy)
+  std::vector<uint64_t> stage_off_;
+  std::vector<RangeSeg> segs_;
+  size_t o_segs_ = 0;
+  uint64_t stage_floats_ = 0;
+  float *d_stage_ = nullptr;
+  size_t stage_mem_ = 0;
   uint32_t n_ = 0;
   std::vector<fz_field> host_;
   std::vector<CompressArgs> args_;

@@ -199,6 +199,11 @@ static cudaError_t launch_c0(const CompressArgs &a, const CUtensorMap *tm, int s
 // 128-byte swizzle, zero fill outside the field.  cuTensorMapEncodeTiled comes from the driver
 // through the runtime's entry-point query (no link-time libcuda).
 bool encode_field_tmap(int ndim, const uint64_t dims[3], const float *x, CUtensorMap *tm) {
+  return encode_field_tmap_pitch(ndim, dims, dims[0], x, tm);
+}
+
+bool encode_field_tmap_pitch(int ndim, const uint64_t dims[3], uint64_t pitch, const float *x,
+                             CUtensorMap *tm) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
     void *f = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -210,7 +215,7 @@ bool encode_field_tmap(int ndim, const uint64_t dims[3], const float *x, CUtenso
   }();
   if (!enc || ndim < 2) return false;
   cuuint64_t gdim[3] = {dims[0], dims[1], dims[2]};
-  cuuint64_t gstr[2] = {dims[0] * 4, dims[0] * dims[1] * 4};
+  cuuint64_t gstr[2] = {pitch * 4, pitch * dims[1] * 4};
   cuuint32_t estr[3] = {1, 1, 1};
   cuuint32_t box3[3] = {32, 32, 2}, box2[2] = {32, 32};
   const CUresult r =

@@ -240,7 +240,7 @@ __device__ __forceinline__ TileGeo tile_geo(const CompressArgs &a, const ChunkGr
 __device__ __forceinline__ float q_at(const CompressArgs &a, uint64_t x, uint64_t y, uint64_t z,
                                       float r) {
   const bool in = x < a.dims[0] && y < a.dims[1] && z < a.dims[2];
-  const float v = in ? __ldg(a.x + x + a.dims[0] * (y + a.dims[1] * z)) : 0.0f;
+  const float v = in ? __ldg(a.x + x + a.pitch * (y + a.dims[1] * z)) : 0.0f;
   return __fadd_rn(__fmul_rn(v, r), kRoundMagic);
 }
 // whether a brick's neighbours one step back along the march axis (3-D:
@@ -284,7 +284,7 @@ struct GlobalRows {
   const TileGeo &q;
   __device__ __forceinline__ void row(int p, int iy, int xo, float (&f)[8]) const {
     const uint64_t x = q.x0 + xo, y = q.y0 + iy, z = q.z0 + p;
-    const float *ptr = a.x + x + a.dims[0] * (y + a.dims[1] * z);
+    const float *ptr = a.x + x + a.pitch * (y + a.dims[1] * z);
     if (!q.edge) {
       load8<V>(ptr, f);
     } else {

@@ -23,6 +23,8 @@ struct FastDiv;
 struct CompressArgs {
   const float *x;
   uint64_t dims[3];            // unused dims = 1
+  uint64_t pitch;              // elements from one x row to the next: dims[0], or
+                               // a batch's row-aligned staging copy's padded pitch
   uint32_t ncx, ncy;           // chunk grid (x, y)
   uint64_t n_chunks;
   int mode;                    // 0 abs, 1 rel
@@ -83,6 +85,9 @@ void launch_range(const float *x, uint64_t n, float2 *partial, int nblocks,
 // passes a tensor map from encode_field_tmap.
 bool compress_uses_tma(int ndim, const CompressArgs &a);
 bool encode_field_tmap(int ndim, const uint64_t dims[3], const float *x, CUtensorMap *tm);
+// the same for rows `pitch` elements apart (pitch * 4 a multiple of 16)
+bool encode_field_tmap_pitch(int ndim, const uint64_t dims[3], uint64_t pitch, const float *x,
+                             CUtensorMap *tm);
 // Tiles per look-back unit of a single-field compression (the compression
 // kernel's compute warps per block; fz_compress_impl.cuh checks the two agree).
 constexpr uint64_t kCompressUnitTiles = 14;

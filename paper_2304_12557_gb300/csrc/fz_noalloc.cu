@@ -143,6 +143,7 @@ extern "C" int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], in
   fz::CompressArgs a{};
   a.x = d_in;
   for (int i = 0; i < 3; ++i) a.dims[i] = d[i];
+  a.pitch = d[0];
   a.ncx = ncx;
   a.ncy = ncy;
   a.n_chunks = n_chunks;

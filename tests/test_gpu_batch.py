@@ -161,7 +161,7 @@ def test_batch_autotune_keeps_streams(codec, torch):
     xs, outs, b = _make_batch(codec, torch, specs)
     try:
         t = b.autotune(reps=2)
-        assert t["ms_direct"] > 0 and t["ms_tma"] > 0
+        assert t["ms_direct"] > 0 and t["ms_tma"] > 0 and t["ms_tma_staged"] > 0
         sizes, sts = b.compress()
         _check(codec, specs, xs, outs, sizes, sts)
     finally:
@@ -201,3 +201,61 @@ def test_batch_rejects_bad_fields(codec, torch):
     with pytest.raises(fz.FZError) as e:
         fz.Batch(codec, [(x, out, "rel", -1.0)])
     assert e.value.status == fz.ERR_ARG
+
+
+def test_batch_every_load_path(codec, torch):
+    """The three load paths give the same streams: direct loads, TMA for the
+    aligned fields only, TMA for all through row-aligned staging copies.
+    The fields cover every row misalignment (dims[0] % 4 = 1, 2, 3), a field
+    that starts off a 16-byte boundary, absolute and relative bounds, escapes
+    in a staged field, and ragged edges."""
+    base = torch.from_numpy(fields.grf((40, 130), -2.5, 41).astype(np.float32).ravel()).cuda()
+    off = torch.empty(base.numel() + 1, dtype=torch.float32, device="cuda")
+    off[1:] = base
+    specs = [
+        (fields.grf((37, 45, 33), -3.0, 42).astype(np.float32), 3, "rel", 1e-3),
+        (fields.grf((19, 70, 66), -3.0, 43).astype(np.float32), 3, "abs", 1e-3),
+        (fields.grf((301, 259), -2.5, 44).astype(np.float32), 2, "rel", 1e-4),
+        (_outliers((24, 50, 71), 200, 45), 3, "abs", 0.5),
+        (fields.grf((64, 96, 128), -3.0, 46).astype(np.float32), 3, "rel", 1e-3),
+        (fields.grf((517, 203), -2.5, 47).astype(np.float32), 2, "abs", 1e-2),
+    ]
+    xs, outs, spec = [], [], []
+    for x, ndim, mode, eb in specs:
+        xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        out = torch.zeros(fz.compress_bound(list(xt.shape[::-1])[:ndim], ndim),
+                          dtype=torch.uint8, device="cuda")
+        xs.append(xt)
+        outs.append(out)
+        spec.append((xt, out, mode, eb, ndim))
+    xo = off[1:].view(40, 130)                      # 4-byte aligned only
+    xs.append(xo)
+    outs.append(torch.zeros(fz.compress_bound([130, 40], 2), dtype=torch.uint8, device="cuda"))
+    spec.append((xo, outs[-1], "rel", 1e-3, 2))
+    specs.append((xo.cpu().numpy(), 2, "rel", 1e-3))
+    want = []
+    for x, ndim, mode, eb in specs:
+        st, o = oracle.compress(np.ascontiguousarray(x), ndim,
+                                oracle.EB_ABS if mode == "abs" else oracle.EB_REL, eb)
+        assert st == oracle.OK
+        want.append(o)
+    b = fz.Batch(codec, spec)
+    try:
+        for tma, staged in [(True, True), (False, False), (True, False), (True, True)]:
+            b.set_load_path(tma, staged)
+            t = b.tuning()
+            assert t["tma"] == tma and t["staged"] == (tma and staged)
+            for o in outs:
+                o.zero_()
+            sizes, sts = b.compress()
+            for i in range(len(specs)):
+                assert sts[i] == fz.OK, (tma, staged, i, sts[i])
+                assert outs[i][: sizes[i]].cpu().numpy().tobytes() == want[i], (tma, staged, i)
+        assert fz.inspect(outs[3][:64].cpu().numpy().tobytes())["n_outliers"] >= 200
+        t = b.autotune(reps=2)
+        assert t["ms_direct"] > 0 and t["ms_tma"] > 0 and t["ms_tma_staged"] > 0
+        sizes, sts = b.compress()
+        for i in range(len(specs)):
+            assert outs[i][: sizes[i]].cpu().numpy().tobytes() == want[i], i
+    finally:
+        b.close()
