@@ -20,7 +20,8 @@
 //        whole-field y prefix;
 //   1-D  q(x)     = L + A'            A' = K_x on the chunks' last elements.
 // Every step is one exclusive or inclusive scan along one axis of the chunk
-// grid (face_scan_kernel); phase 2 of the decompressor adds the terms.
+// grid (face_scan_lines_kernel, face_scan_word_kernel); phase 2 of the
+// decompressor adds the terms.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -37,76 +38,89 @@ constexpr int kScanThreads = 256;
 // `axis` (the other two chunk coordinates equal) of in(c')(map(i)), for a
 // face of U x W words per chunk (i = u + U w).  map 0: i itself; 1: w set
 // to W - 1 (the face's last row); 2: u set to U - 1 (its last column).
-// A block takes one line of chunks along the axis and F consecutive face
-// words (F = 32, or 1 for one-word faces), S = 256 / F chunks per step;
-// unsigned arithmetic, so that a corrupt stream's sums wrap rather than
-// overflow.
-template <int F>
-__global__ void __launch_bounds__(kScanThreads)
-    face_scan_kernel(const uint32_t *in, uint32_t *out, uint32_t ncx, uint32_t ncy, uint32_t ncz,
-                     int axis, uint32_t U, uint32_t W, int map, int self) {
-  constexpr int S = kScanThreads / F;
-  __shared__ uint32_t sh[kScanThreads];
-  const uint32_t m = U * W;
-  const uint32_t groups = m / F;
-  const uint64_t line = blockIdx.x / groups;
-  const uint32_t i = (blockIdx.x % groups) * F + threadIdx.x % F;
-  const int s = threadIdx.x / F;
+// Unsigned arithmetic, so that a corrupt stream's sums wrap rather than
+// overflow.  The chunk at step k of a line is base + k * stride.
+struct Line {
   uint64_t base, stride, n;
-  if (axis == 0) {
-    base = (uint64_t)ncx * line; stride = 1; n = ncx;
-  } else if (axis == 1) {
+};
+__device__ __forceinline__ Line line_of(uint64_t line, uint32_t ncx, uint32_t ncy, uint32_t ncz,
+                                        int axis) {
+  if (axis == 0) return {(uint64_t)ncx * line, 1, ncx};
+  if (axis == 1) {
     const uint64_t cx = line % ncx, cz = line / ncx;
-    base = cx + (uint64_t)ncx * ncy * cz; stride = ncx; n = ncy;
-  } else {
-    base = line; stride = (uint64_t)ncx * ncy; n = ncz;
+    return {cx + (uint64_t)ncx * ncy * cz, ncx, ncy};
   }
+  return {line, (uint64_t)ncx * ncy, ncz};
+}
+__device__ __forceinline__ uint32_t mapped(uint32_t i, uint32_t U, uint32_t W, int map) {
   const uint32_t u = i % U, w = i / U;
-  const uint32_t mi = map == 1 ? u + U * (W - 1) : map == 2 ? (U - 1) + U * w : i;
+  return map == 1 ? u + U * (W - 1) : map == 2 ? (U - 1) + U * w : i;
+}
+
+// Faces of 32 words or more: one thread per (line, face word), consecutive
+// threads on consecutive words; each thread walks its line, loading 8 steps'
+// words at once before it sums them.
+__global__ void __launch_bounds__(kScanThreads)
+    face_scan_lines_kernel(const uint32_t *in, uint32_t *out, uint32_t ncx, uint32_t ncy,
+                           uint32_t ncz, int axis, uint32_t U, uint32_t W, int map, int self,
+                           uint64_t total) {
+  constexpr int kStep = 8;
+  const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const uint32_t m = U * W;
+  const uint32_t i = (uint32_t)(t % m);
+  const Line L = line_of(t / m, ncx, ncy, ncz, axis);
+  const uint32_t mi = mapped(i, U, W, map);
   uint32_t carry = 0;
-  for (uint64_t k0 = 0; k0 < n; k0 += S) {
-    const uint64_t k = k0 + s;
-    const uint64_t c = base + k * stride;
-    uint32_t val = 0, mv = 0;
-    if (k < n) {
-      mv = __ldg(in + c * m + mi);
-      if (self) val = __ldg(in + c * m + i);
+  for (uint64_t k0 = 0; k0 < L.n; k0 += kStep) {
+    uint32_t mv[kStep], val[kStep];
+#pragma unroll
+    for (int j = 0; j < kStep; ++j) {
+      mv[j] = 0;
+      val[j] = 0;
+      if (k0 + j < L.n) {
+        const uint64_t c = L.base + (k0 + j) * L.stride;
+        mv[j] = __ldg(in + c * m + mi);
+        if (self) val[j] = __ldg(in + c * m + i);
+      }
     }
-    uint32_t ex, tot;
-    if constexpr (F == 1) {
-      // scan over all 256 threads: within warps, then over the warp totals
-      const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-      uint32_t inc = mv;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-      }
-      if (lane == 31) sh[wp] = inc;
-      __syncthreads();
-      uint32_t before = 0;
-      tot = 0;
+    for (int j = 0; j < kStep; ++j) {
+      if (k0 + j < L.n) out[(L.base + (k0 + j) * L.stride) * m + i] = val[j] + carry;
+      carry += mv[j];
+    }
+  }
+}
+
+// One-word faces (1-D: the chunks' last elements): a block per line, 256
+// chunks per step, a block-wide scan over the step.
+__global__ void __launch_bounds__(kScanThreads)
+    face_scan_word_kernel(const uint32_t *in, uint32_t *out, uint32_t ncx, uint32_t ncy,
+                          uint32_t ncz, int axis, int self) {
+  __shared__ uint32_t sh[kScanThreads / 32];
+  const Line L = line_of(blockIdx.x, ncx, ncy, ncz, axis);
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  uint32_t carry = 0;
+  for (uint64_t k0 = 0; k0 < L.n; k0 += kScanThreads) {
+    const uint64_t k = k0 + threadIdx.x;
+    const uint64_t c = L.base + k * L.stride;
+    const uint32_t mv = k < L.n ? __ldg(in + c) : 0u;
+    uint32_t inc = mv;
 #pragma unroll
-      for (int j = 0; j < kScanThreads / 32; ++j) {
-        before += j < wp ? sh[j] : 0u;
-        tot += sh[j];
-      }
-      ex = before + inc - mv;
-    } else {
-      sh[threadIdx.x] = mv;
-      __syncthreads();
-      ex = 0;
-      tot = 0;
-      const int f = threadIdx.x % F;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) sh[wp] = inc;
+    __syncthreads();
+    uint32_t before = 0, tot = 0;
 #pragma unroll
-      for (int j = 0; j < S; ++j) {
-        const uint32_t y = sh[j * F + f];
-        ex += j < s ? y : 0u;
-        tot += y;
-      }
+    for (int j = 0; j < kScanThreads / 32; ++j) {
+      before += j < wp ? sh[j] : 0u;
+      tot += sh[j];
     }
     __syncthreads();                                   // sh is reused next step
-    if (k < n) out[c * m + i] = val + carry + ex;
+    if (k < L.n) out[c] = (self ? mv : 0u) + carry + before + inc - mv;
     carry += tot;
   }
 }
@@ -117,12 +131,13 @@ cudaError_t scan(const int32_t *in, int32_t *out, const uint32_t nc[3], int axis
   const uint32_t m = U * W;
   const uint32_t *i = reinterpret_cast<const uint32_t *>(in);
   uint32_t *o = reinterpret_cast<uint32_t *>(out);
-  if (m % 32 == 0) {
-    face_scan_kernel<32><<<(unsigned)(lines * (m / 32)), kScanThreads, 0, s>>>(
-        i, o, nc[0], nc[1], nc[2], axis, U, W, map, self);
+  if (m == 1) {
+    face_scan_word_kernel<<<(unsigned)lines, kScanThreads, 0, s>>>(i, o, nc[0], nc[1], nc[2], axis,
+                                                                   self);
   } else {
-    face_scan_kernel<1><<<(unsigned)(lines * m), kScanThreads, 0, s>>>(
-        i, o, nc[0], nc[1], nc[2], axis, U, W, map, self);
+    const uint64_t total = lines * m;
+    face_scan_lines_kernel<<<(unsigned)((total + kScanThreads - 1) / kScanThreads), kScanThreads, 0,
+                             s>>>(i, o, nc[0], nc[1], nc[2], axis, U, W, map, self, total);
   }
   return cudaGetLastError();
 }
