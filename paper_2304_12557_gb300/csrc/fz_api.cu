@@ -432,7 +432,7 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
   a.whole = whole;
   CUtensorMap tm;
   std::memset(&tm, 0, sizeof(tm));
-  const bool tma = !whole && fz::compress_uses_tma(sh.ndim, a) &&
+  const bool tma = fz::compress_uses_tma(sh.ndim, a) &&
                    fz::encode_field_tmap(sh.ndim, sh.d, d_in, &tm);
   prof_begin(c, 1, s);
   if (fz::launch_compress(sh.ndim, a, tma ? &tm : nullptr, c->num_sms, s,

@@ -236,22 +236,30 @@ bool compress_uses_tma(int ndim, const CompressArgs &a) {
   return !ldg_only && ndim >= 2 && vec_width(a) >= 4;
 }
 
-// The whole-field variant (stream version 2) reads its tiles with scalar
-// loads; a range-checked and an unchecked kernel per dimensionality.
+// The whole-field variant (stream version 2): TMA boxes for 2-D/3-D fields
+// whose rows are 16-byte aligned (16-byte halo and face loads), scalar loads
+// otherwise; a range-checked and an unchecked kernel of each.
 template <int NDIM>
-static cudaError_t launch_whole(const CompressArgs &a, int sms, bool pdl, cudaStream_t s) {
+static cudaError_t launch_whole(const CompressArgs &a, const CUtensorMap *tm, int sms, bool pdl,
+                                cudaStream_t s) {
+  const bool check = a.mode == 0 || a.range_given;
+  if constexpr (NDIM >= 2) {
+    if (tm && vec_width(a) >= 4)
+      return check ? launch_c3<NDIM, 4, true, true, true>(a, *tm, sms, pdl, s)
+                   : launch_c3<NDIM, 4, false, true, true>(a, *tm, sms, pdl, s);
+  }
   CUtensorMap none;
   memset(&none, 0, sizeof(none));
-  return (a.mode == 0 || a.range_given) ? launch_c3<NDIM, 1, true, false, true>(a, none, sms, pdl, s)
-                                        : launch_c3<NDIM, 1, false, false, true>(a, none, sms, pdl, s);
+  return check ? launch_c3<NDIM, 1, true, false, true>(a, none, sms, pdl, s)
+               : launch_c3<NDIM, 1, false, false, true>(a, none, sms, pdl, s);
 }
 
 cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *tm, int sms,
                             cudaStream_t s, bool after_range) {
   if (a.whole) {
-    if (ndim == 3) return launch_whole<3>(a, sms, after_range, s);
-    if (ndim == 2) return launch_whole<2>(a, sms, after_range, s);
-    return launch_whole<1>(a, sms, after_range, s);
+    if (ndim == 3) return launch_whole<3>(a, tm, sms, after_range, s);
+    if (ndim == 2) return launch_whole<2>(a, tm, sms, after_range, s);
+    return launch_whole<1>(a, nullptr, sms, after_range, s);
   }
   if (ndim == 3) return launch_c0<3>(a, tm, sms, after_range, s);
   if (ndim == 2) return launch_c0<2>(a, tm, sms, after_range, s);
