@@ -45,7 +45,9 @@ extern "C" {
 #define FZ_ERR_ARG         -1  /* bad pointer, ndim, dims, eb, alignment   */
 #define FZ_ERR_CAPACITY    -2  /* output buffer too small                  */
 #define FZ_ERR_NONFINITE   -3  /* NaN or Inf in the input field            */
-#define FZ_ERR_EB_RANGE    -4  /* some |x|/(2eb) rounds beyond 2^22-1, or
+#define FZ_ERR_EB_RANGE    -4  /* some |x|/(2eb) rounds beyond 2^28-1
+                                  (2^22-1 for a batch, a server request,
+                                  the no-alloc and the unfused entries), or
                                   the derived bound is not a normal float   */
 #define FZ_ERR_CORRUPT     -6  /* stream fails a structural check          */
 #define FZ_ERR_TIMEOUT     -7  /* a bounded device wait gave up            */
@@ -78,7 +80,7 @@ typedef struct fz_info {
   uint64_t stream_bytes;  /* 64 + 32*n_tiles + 16*nnz_blocks + 8*n_outliers*/
   uint32_t version;       /* 1: chunk-local Lorenzo (fz_compress), 2:
                              whole-field Lorenzo (fz_compress_whole)       */
-  uint32_t reserved;      /* 0                                             */
+  uint32_t wide;          /* 1: some |q| passes 2^22 - 1 (header byte 7)   */
 } fz_info;
 
 /* Create a context on CUDA device `device`: allocates the scratch used by
@@ -105,7 +107,9 @@ uint64_t fz_stream_min_bytes(const uint64_t dims[3], int ndim);
  *             field's value range (Sec. 4.1); eb finite and > 0
  *   d_out     device pointer, 16-byte aligned, out_capacity bytes
  *   out_size  host pointer; receives the stream size on success
- * The stream is a pure function of (input bytes, dims, mode, eb).
+ * The stream is a pure function of (input bytes, dims, mode, eb).  A field
+ * whose |q| passes 2^22 - 1 (up to 2^28 - 1) takes a second launch with
+ * integer quantisation; its stream sets header byte 7 (fz_info.wide).
  * Errors: FZ_ERR_ARG, FZ_ERR_NONFINITE, FZ_ERR_EB_RANGE, FZ_ERR_CAPACITY
  * (*out_size = bytes needed), FZ_ERR_TIMEOUT, FZ_ERR_CUDA. */
 int fz_compress(fz_ctx *ctx, const float *d_in, const uint64_t dims[3],

@@ -35,7 +35,8 @@ ERR_CORRUPT = -6
 EB_ABS = 0
 EB_REL = 1
 HEADER_BYTES = 64
-QMAX = 4194303
+QMAX = 268435455          # 2^28 - 1: largest |q| the quantiser takes
+QNARROW = 4194303        # 2^22 - 1: beyond it a stream sets header byte 7
 
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _i32p = ctypes.POINTER(ctypes.c_int32)

@@ -94,7 +94,7 @@ int fzo_derive_eb(int mode, double eb_req, float fmin, float fmax,
 int fzo_prequant1(float x, float ebx2_r, int32_t *q) {
   volatile float v = x * ebx2_r;         /* one binary32 multiply */
   float r = nearbyintf(v);               /* FE_TONEAREST: ties to even */
-  if (!(fabsf(r) <= (float)FZO_QMAX)) return FZO_ERR_EB_RANGE;
+  if (!(fabs((double)r) <= (double)FZO_QMAX)) return FZO_ERR_EB_RANGE;
   *q = (int32_t)r;
   return FZO_OK;
 }
@@ -422,11 +422,14 @@ static int compress_common(const float *x, const uint32_t dims[3], int ndim,
   int32_t *q = (int32_t *)malloc(n * sizeof(int32_t));
   int32_t *delta = (int32_t *)malloc(n * sizeof(int32_t));
   if (!q || !delta) { free(q); free(delta); return FZO_ERR_ARG; }
-  for (uint64_t i = 0; i < n; i++)
+  int wide = 0;                          /* some |q| beyond FZO_QNARROW */
+  for (uint64_t i = 0; i < n; i++) {
     if (fzo_prequant1(x[i], ebx2_r, &q[i])) {
       free(q); free(delta);
       return FZO_ERR_EB_RANGE;
     }
+    wide |= q[i] > FZO_QNARROW || q[i] < -FZO_QNARROW;
+  }
 
   /* step 2: chunk-local Lorenzo residuals */
   lorenzo_mode(q, dims, ndim, whole, delta);
@@ -487,7 +490,7 @@ static int compress_common(const float *x, const uint32_t dims[3], int ndim,
   }
   memset(out, 0, FZO_HEADER_BYTES);
   out[0] = 'F'; out[1] = 'Z'; out[2] = 'G'; out[3] = '1';
-  out[4] = whole ? 2 : 1; out[5] = (uint8_t)ndim; out[6] = (uint8_t)mode; out[7] = 0;
+  out[4] = whole ? 2 : 1; out[5] = (uint8_t)ndim; out[6] = (uint8_t)mode; out[7] = (uint8_t)wide;
   put_u32(out + 8, (uint32_t)d[0]);
   put_u32(out + 12, (uint32_t)d[1]);
   put_u32(out + 16, (uint32_t)d[2]);
@@ -529,7 +532,7 @@ int fzo_decompress(const uint8_t *in, uint64_t in_size, float *x,
   if (!in || !x) return FZO_ERR_ARG;
   if (in_size < FZO_HEADER_BYTES) return FZO_ERR_CORRUPT;
   if (in[0] != 'F' || in[1] != 'Z' || in[2] != 'G' || in[3] != '1' ||
-      (in[4] != 1 && in[4] != 2) || in[7] != 0)
+      (in[4] != 1 && in[4] != 2) || in[7] > 1)
     return FZO_ERR_CORRUPT;
   const int whole = in[4] == 2;
   int ndim = in[5], mode = in[6];
@@ -790,6 +793,7 @@ typedef struct {
   uint64_t *tile_out;
   uint8_t *po;
   int bad[MT_MAX_THREADS];
+  int wide[MT_MAX_THREADS];           /* some |q| beyond FZO_QNARROW */
   float lo[MT_MAX_THREADS], hi[MT_MAX_THREADS];
 } mt_comp;
 
@@ -811,9 +815,13 @@ static void mt_minmax(void *c, int64_t lo, int64_t hi, int k) {
 }
 static void mt_prequant(void *c, int64_t lo, int64_t hi, int k) {
   mt_comp *m = (mt_comp *)c;
-  int bad = 0;
-  for (int64_t i = lo; i < hi; i++) bad |= fzo_prequant1(m->x[i], m->ebx2_r, &m->q[i]) != FZO_OK;
+  int bad = 0, wide = 0;
+  for (int64_t i = lo; i < hi; i++) {
+    bad |= fzo_prequant1(m->x[i], m->ebx2_r, &m->q[i]) != FZO_OK;
+    wide |= m->q[i] > FZO_QNARROW || m->q[i] < -FZO_QNARROW;
+  }
   m->bad[k] = bad;
+  m->wide[k] = wide;
 }
 static void mt_lorenzo(void *c, int64_t lo, int64_t hi, int k) {
   mt_comp *m = (mt_comp *)c;
@@ -907,6 +915,8 @@ int fzo_compress_mt(const float *x, const uint32_t dims[3], int ndim, int mode,
   bad = 0;
   for (int k = 0; k < T; k++) bad |= m->bad[k];
   if (bad) { free(m->q); free(m->delta); free(m); return FZO_ERR_EB_RANGE; }
+  int wide = 0;
+  for (int k = 0; k < T; k++) wide |= m->wide[k];
   mt_for(n, T, mt_lorenzo, m);
   free(m->q);
   m->q = NULL;
@@ -933,7 +943,7 @@ int fzo_compress_mt(const float *x, const uint32_t dims[3], int ndim, int mode,
   }
   memset(out, 0, FZO_HEADER_BYTES);
   out[0] = 'F'; out[1] = 'Z'; out[2] = 'G'; out[3] = '1';
-  out[4] = 1; out[5] = (uint8_t)ndim; out[6] = (uint8_t)mode; out[7] = 0;
+  out[4] = 1; out[5] = (uint8_t)ndim; out[6] = (uint8_t)mode; out[7] = (uint8_t)wide;
   put_u32(out + 8, (uint32_t)d[0]);
   put_u32(out + 12, (uint32_t)d[1]);
   put_u32(out + 16, (uint32_t)d[2]);
@@ -1071,7 +1081,7 @@ int fzo_decompress_mt(const uint8_t *in, uint64_t in_size, float *x, uint64_t ca
   if (in_size < FZO_HEADER_BYTES) return FZO_ERR_CORRUPT;
   if (in[4] == 2) return fzo_decompress(in, in_size, x, cap_elems);   /* whole-field */
   if (in[0] != 'F' || in[1] != 'Z' || in[2] != 'G' || in[3] != '1' || in[4] != 1 ||
-      in[7] != 0)
+      in[7] > 1)
     return FZO_ERR_CORRUPT;
   int ndim = in[5], mode = in[6];
   uint32_t dims[3] = {get_u32(in + 8), get_u32(in + 12), get_u32(in + 16)};

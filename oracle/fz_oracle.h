@@ -45,7 +45,11 @@ extern "C" {
 #define FZO_HEADER_BYTES 64
 #define FZO_TILE_CODES 2048
 #define FZO_TILES_PER_CHUNK 4
-#define FZO_QMAX 4194303   /* 2^22 - 1: largest |q| accepted */
+#define FZO_QMAX 268435455    /* 2^28 - 1: largest |q| accepted (every 3-D
+                                 residual, a signed sum of 8 q, fits an i32
+                                 outlier record) */
+#define FZO_QNARROW 4194303   /* 2^22 - 1: a stream whose every |q| is at most
+                                 this has header byte 7 = 0, else 1 */
 
 /* --- individual steps (exported so the tests can pin each one) --- */
 

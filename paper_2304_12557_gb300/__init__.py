@@ -72,7 +72,7 @@ class _Info(ctypes.Structure):
                 ("range_max", ctypes.c_float), ("n_tiles", _u64),
                 ("nnz_blocks", _u64), ("n_outliers", _u64),
                 ("stream_bytes", _u64), ("version", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("wide", ctypes.c_uint32)]
 
 
 class _Field(ctypes.Structure):
@@ -225,7 +225,7 @@ def inspect(header: bytes) -> dict:
             "range_min": info.range_min, "range_max": info.range_max,
             "n_tiles": info.n_tiles, "nnz_blocks": info.nnz_blocks,
             "n_outliers": info.n_outliers, "stream_bytes": info.stream_bytes,
-            "version": info.version}
+            "version": info.version, "wide": bool(info.wide)}
 
 
 def pwrel_bound(eps: float) -> float:

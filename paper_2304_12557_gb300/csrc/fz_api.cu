@@ -377,7 +377,8 @@ int fz_debug_skip_publish(fz_ctx *c, uint64_t chunk) {
 // range from a range pass over d_in, else rng[0..1] is the range
 static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], int ndim,
                          int mode, double eb, const float *rng, void *d_out, uint64_t cap,
-                         uint64_t *out_size, void *stream, bool whole = false) {
+                         uint64_t *out_size, void *stream, bool whole = false,
+                         bool force_wide = false) {
   if (out_size) *out_size = 0;
   Shape sh;
   if (!c || !d_in || !d_out || !out_size || !make_shape(dims, ndim, &sh)) return FZ_ERR_ARG;
@@ -430,13 +431,15 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
   a.wait_limit_ns = c->wait_limit_ns;
   a.skip_publish_chunk = c->skip_publish;
   a.whole = whole;
+  a.allow_wide = 1;
+  a.wide = force_wide;
   CUtensorMap tm;
   std::memset(&tm, 0, sizeof(tm));
-  const bool tma = fz::compress_uses_tma(sh.ndim, a) &&
+  const bool tma = !force_wide && fz::compress_uses_tma(sh.ndim, a) &&
                    fz::encode_field_tmap(sh.ndim, sh.d, d_in, &tm);
   prof_begin(c, 1, s);
   if (fz::launch_compress(sh.ndim, a, tma ? &tm : nullptr, c->num_sms, s,
-                          mode == FZ_EB_REL && !rng) != cudaSuccess) {
+                          mode == FZ_EB_REL && !rng && !force_wide) != cudaSuccess) {
     mark_all_dirty(c);
     return FZ_ERR_CUDA;
   }
@@ -449,15 +452,28 @@ static int compress_impl(fz_ctx *c, const float *d_in, const uint64_t dims[3], i
   }
   c->call_used[0] = timed;
   const SetScratch r = *c->h_res;
-  if (r.err & (fz::kErrNonFinite | fz::kErrEbParam | fz::kErrRange | fz::kErrTimeout)) {
+  if (r.err & (fz::kErrNonFinite | fz::kErrEbParam | fz::kErrRange | fz::kErrTimeout |
+               fz::kErrWide)) {
     // the kernel may have stopped before zeroing the next call's look-back
     // words: clear every set before the next launch
     mark_all_dirty(c);
   }
   if (r.err & fz::kErrNonFinite) return FZ_ERR_NONFINITE;
+  if ((r.err & fz::kErrWide) && !force_wide)       // the range passes |q| = 2^22 - 1
+    return compress_impl(c, d_in, dims, ndim, mode, eb, rng, d_out, cap, out_size, stream,
+                         whole, true);
   if (r.err & (fz::kErrEbParam | fz::kErrRange)) {
-    // elements checked one by one: NaN/Inf fail the same check
-    if (mode == FZ_EB_ABS || rng) return classify_range_error(c, d_in, sh.n_elems, s);
+    // elements checked one by one: NaN/Inf fail the same check.  A finite
+    // field that passes |q| = 2^22 - 1 gets one more launch with the wide
+    // quantiser, which checks |q| <= 2^28 - 1 against the range pass that
+    // classify_range_error has just run (its result stays in c->range).
+    if (mode == FZ_EB_ABS || rng) {
+      const int cls = classify_range_error(c, d_in, sh.n_elems, s);
+      if (cls == FZ_ERR_EB_RANGE && !force_wide && !(r.err & fz::kErrEbParam))
+        return compress_impl(c, d_in, dims, ndim, mode, eb, rng, d_out, cap, out_size, stream,
+                             whole, true);
+      return cls;
+    }
     return FZ_ERR_EB_RANGE;
   }
   if (r.err & fz::kErrTimeout) return FZ_ERR_TIMEOUT;
@@ -776,6 +792,7 @@ static int decompress_whole(fz_ctx *c, fz::DecompressArgs a, const SetScratch &r
   if (st) return st;
   const int B = c->cur;
   a.set_cur = c->sets + B;
+  a.wide = r.wide ? 1 : 0;
   for (int k = 0; k < 3; ++k) a.face[k] = face[k];
   a.phase = 1;
   prof_begin(c, 3, s);
@@ -803,6 +820,33 @@ static int decompress_whole(fz_ctx *c, fz::DecompressArgs a, const SetScratch &r
   const SetScratch q = *c->h_res;
   if (q.err & fz::kErrCorrupt) return FZ_ERR_CORRUPT;
   if (q.nout != 2ull * r.hdr_nout) return FZ_ERR_CORRUPT;
+  return FZ_OK;
+}
+
+// A version-1 stream of the wide quantiser (header byte 7), after the
+// offsets pass: the kernel that converts q as integers.
+static int decompress_wide(fz_ctx *c, fz::DecompressArgs a, const SetScratch &r, int grid,
+                           cudaStream_t s, bool timed) {
+  int st = prepare_set(c, s);
+  if (st) return st;
+  const int B = c->cur;
+  a.set_cur = c->sets + B;
+  a.wide = 1;
+  a.phase = 0;
+  prof_begin(c, 3, s);
+  if (fz::launch_decompress(a, grid, s) != cudaSuccess) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  prof_end(c, 3, s);
+  c->hdr_dirty[B] = true;
+  if ((st = read_set(c, B, s, timed ? c->call_ev[3] : nullptr))) {
+    mark_all_dirty(c);
+    return st;
+  }
+  const SetScratch q = *c->h_res;
+  if (q.err & fz::kErrCorrupt) return FZ_ERR_CORRUPT;
+  if (q.nout != r.hdr_nout) return FZ_ERR_CORRUPT;
   return FZ_OK;
 }
 
@@ -868,6 +912,7 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   if (r.err & fz::kErrCorrupt) return FZ_ERR_CORRUPT;
   if (r.err & fz::kErrCapacity) return FZ_ERR_CAPACITY;
   if (r.version == 2) return decompress_whole(c, a, r, grid, s, timed);
+  if (r.wide) return decompress_wide(c, a, r, grid, s, timed);
   if (r.nout != r.hdr_nout) return FZ_ERR_CORRUPT;
   return FZ_OK;
 }
@@ -938,7 +983,7 @@ int fz_inspect(const void *hdr, uint64_t n, fz_info *out) {
   if (n < 64) return FZ_ERR_CORRUPT;
   const uint8_t *p = static_cast<const uint8_t *>(hdr);
   if (p[0] != 'F' || p[1] != 'Z' || p[2] != 'G' || p[3] != '1' || p[4] < 1 || p[4] > 2 ||
-      p[7] != 0)
+      p[7] > 1)
     return FZ_ERR_CORRUPT;
   const int ndim = p[5], mode = p[6];
   if (ndim < 1 || ndim > 3 || mode > 1) return FZ_ERR_CORRUPT;
@@ -962,7 +1007,7 @@ int fz_inspect(const void *hdr, uint64_t n, fz_info *out) {
   out->n_tiles = sh.n_tiles;
   out->stream_bytes = 64 + 32 * sh.n_tiles + 16 * out->nnz_blocks + 8 * out->n_outliers;
   out->version = p[4];
-  out->reserved = 0;
+  out->wide = p[7];
   return FZ_OK;
 }
 

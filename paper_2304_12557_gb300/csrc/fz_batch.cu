@@ -326,6 +326,7 @@ int BatchWs::set(int device, const fz_field *fields, int n, cudaStream_t s) {
     a.out_capacity = h.out_capacity;
     a.wait_limit_ns = wait_limit_ns;
     a.skip_publish_chunk = ~0ull;
+    a.allow_wide = 0;                 // |q| up to 2^22 - 1 (no second launch)
     tile_off[f] = total_tiles;
     total_tiles += tiles;
     const uint64_t units = (tiles + kCompWarps - 1) / kCompWarps;

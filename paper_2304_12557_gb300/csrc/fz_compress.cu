@@ -138,10 +138,10 @@ static int vec_width(const CompressArgs &a) {
   return 1;
 }
 
-template <int NDIM, int V, bool CHECK, bool TMA, bool WHOLE = false>
+template <int NDIM, int V, bool CHECK, bool TMA, bool WHOLE = false, bool WIDE = false>
 static cudaError_t launch_c3(const CompressArgs &a, const CUtensorMap &tm, int sms, bool pdl,
                              cudaStream_t s) {
-  auto k = compress_kernel<NDIM, V, CHECK, TMA, false, WHOLE>;
+  auto k = compress_kernel<NDIM, V, CHECK, TMA, false, WHOLE, WIDE>;
   const int smem = TMA ? kCompSmemTma : kCompSmemLdg;
   static int per_sm = 0;                    // resident blocks per SM, once
   if (per_sm == 0) {
@@ -254,8 +254,24 @@ static cudaError_t launch_whole(const CompressArgs &a, const CUtensorMap *tm, in
                : launch_c3<NDIM, 1, false, false, true>(a, none, sms, pdl, s);
 }
 
+// The wide quantiser's launch (|q| up to 2^28 - 1): the integer path for
+// every tile, scalar loads; its range was checked before (no per-element
+// check).
+template <int NDIM>
+static cudaError_t launch_wide(const CompressArgs &a, int sms, cudaStream_t s) {
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  return a.whole ? launch_c3<NDIM, 1, false, false, true, true>(a, none, sms, false, s)
+                 : launch_c3<NDIM, 1, false, false, false, true>(a, none, sms, false, s);
+}
+
 cudaError_t launch_compress(int ndim, const CompressArgs &a, const CUtensorMap *tm, int sms,
                             cudaStream_t s, bool after_range) {
+  if (a.wide) {
+    if (ndim == 3) return launch_wide<3>(a, sms, s);
+    if (ndim == 2) return launch_wide<2>(a, sms, s);
+    return launch_wide<1>(a, sms, s);
+  }
   if (a.whole) {
     if (ndim == 3) return launch_whole<3>(a, tm, sms, after_range, s);
     if (ndim == 2) return launch_whole<2>(a, tm, sms, after_range, s);
@@ -270,6 +286,11 @@ template <int NDIM>
 static cudaError_t launch_o(const CompressArgs &a, uint64_t out_section, cudaStream_t s) {
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
   const unsigned blocks = (unsigned)((n_tiles + kOutWarps - 1) / kOutWarps);
+  if (a.wide) {
+    if (a.whole) outlier_kernel<NDIM, 1, true, true><<<blocks, kOutWarps * 32, 0, s>>>(a, out_section);
+    else outlier_kernel<NDIM, 1, false, true><<<blocks, kOutWarps * 32, 0, s>>>(a, out_section);
+    return cudaGetLastError();
+  }
   if (a.whole) {
     outlier_kernel<NDIM, 1, true><<<blocks, kOutWarps * 32, 0, s>>>(a, out_section);
     return cudaGetLastError();

@@ -84,6 +84,7 @@ struct __align__(8) FieldRt {
   EbParams p;
   float fmin, fmax;
   uint32_t ok;
+  uint32_t wide;                 // the wide quantiser (|q| up to 2^28 - 1)
   FastDiv dx, dy;
 };
 
@@ -159,7 +160,10 @@ __device__ __forceinline__ void field_range(const CompressArgs &a, float &fmin, 
 
 // fl(v + 1.5*2^23) of v = fl(x * r): the integer rint(v) sits in the low
 // mantissa bits; returned as raw bits (biased by kMagicBits).
-__device__ __forceinline__ int32_t quant_bits(float x, float r) {
+// With `wide`, rint(fl(x * r)) by integer conversion (ties to even), biased
+// the same way, for |q| up to 2^28 - 1.
+__device__ __forceinline__ int32_t quant_bits(float x, float r, bool wide = false) {
+  if (wide) return __float2int_rn(__fmul_rn(x, r)) + (int32_t)kMagicBits;
   return (int32_t)__float_as_uint(__fadd_rn(__fmul_rn(x, r), kRoundMagic));
 }
 
@@ -177,11 +181,28 @@ __device__ __forceinline__ FieldRt derive_field(const CompressArgs &a, uint32_t 
   rt.fmax = fmax;
   bool ok = rt.p.ok && !nonfinite;
   err = 0;
-  if (ok && a.mode == 1 && !a.range_given) {
+  rt.wide = a.wide ? 1u : 0u;
+  // |fl(m r)| below 2^28 <=> |rint| <= 2^28 - 1 (floats there are 16 apart)
+  auto fits_wide = [&](float m) { return fabsf(__fmul_rn(m, rt.p.ebx2_r)) < kWideLimit; };
+  if (ok && !a.wide && a.mode == 1 && !a.range_given) {
     const float m = fmaxf(fabsf(fmin), fabsf(fmax));
     const uint32_t b = (uint32_t)quant_bits(m, rt.p.ebx2_r) - kBiasBits;
-    ok = b <= kBiasedMax;
-    if (!ok) err |= kErrRange;
+    if (b > kBiasedMax) {
+      ok = false;
+      err |= a.allow_wide && fits_wide(m) ? kErrWide : kErrRange;
+    }
+  }
+  if (ok && a.wide) {
+    // the wide quantiser's launch: the range pass over the data bounds
+    // every element (relative bounds: the field's own pass; absolute bounds
+    // and supplied ranges: the pass the caller ran after the first launch)
+    const float m = a.mode == 1 && !a.range_given
+                        ? fmaxf(fabsf(fmin), fabsf(fmax))
+                        : fmaxf(fabsf(a.range->fmin), fabsf(a.range->fmax));
+    if (!fits_wide(m) || a.range->nonfinite) {
+      ok = false;
+      err |= kErrRange;
+    }
   }
   if (!rt.p.ok) err |= kErrEbParam;
   if (nonfinite) err |= kErrNonFinite;
@@ -242,6 +263,13 @@ __device__ __forceinline__ float q_at(const CompressArgs &a, uint64_t x, uint64_
   const bool in = x < a.dims[0] && y < a.dims[1] && z < a.dims[2];
   const float v = in ? __ldg(a.x + x + a.pitch * (y + a.dims[1] * z)) : 0.0f;
   return __fadd_rn(__fmul_rn(v, r), kRoundMagic);
+}
+// the same as a biased integer, through the wide quantiser when `wide`
+__device__ __forceinline__ int32_t qi_at(const CompressArgs &a, uint64_t x, uint64_t y, uint64_t z,
+                                         float r, bool wide) {
+  if (!wide) return __float_as_int(q_at(a, x, y, z, r));
+  const bool in = x < a.dims[0] && y < a.dims[1] && z < a.dims[2];
+  return quant_bits(in ? __ldg(a.x + x + a.pitch * (y + a.dims[1] * z)) : 0.0f, r, true);
 }
 // whether a brick's neighbours one step back along the march axis (3-D:
 // the plane below, 2-D: the row above, 1-D: the element before) count:
@@ -352,10 +380,11 @@ __device__ __forceinline__ void load_halo(const CompressArgs &a, const TileGeo &
 // (bits - kBiasBits) into qmax, checking the value range per element
 // (absolute bounds; with a relative bound the range pass has shown that every
 // element passes).
-template <int NDIM, bool CHECK, class Src>
+template <int NDIM, bool CHECK, class Src, bool WIDE = false>
 __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q, int g,
                                                 float r, const float (&hf)[32],
                                                 int32_t (&v)[64], uint32_t &qmax) {
+  constexpr bool wide = WIDE;
   const unsigned full = 0xffffffffu;
   if constexpr (NDIM == 3) {
 #pragma unroll
@@ -365,8 +394,8 @@ __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q
       src.row(1, iy, 0, p1);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const int32_t q0 = quant_bits(p0[k], r), q1 = quant_bits(p1[k], r);
-        const int32_t qh = quant_bits(hf[8 * iy + k], r);   // hf = 0 when t == 0: q = 0
+        const int32_t q0 = quant_bits(p0[k], r, wide), q1 = quant_bits(p1[k], r, wide);
+        const int32_t qh = quant_bits(hf[8 * iy + k], r, wide);   // hf = 0 when t == 0: q = 0
         if (CHECK) qmax = max(qmax, max((uint32_t)q0 - kBiasBits, (uint32_t)q1 - kBiasBits));
         v[8 * iy + k] = q0 - qh;
         v[32 + 8 * iy + k] = q1 - q0;
@@ -379,14 +408,14 @@ __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q
       src.row(0, row, 0, f8);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        v[8 * row + k] = quant_bits(f8[k], r);
+        v[8 * row + k] = quant_bits(f8[k], r, wide);
         if (CHECK) qmax = max(qmax, (uint32_t)v[8 * row + k] - kBiasBits);
       }
     }
 #pragma unroll
     for (int ix = 0; ix < 8; ++ix) {                 // D_y
       int32_t up = __shfl_up_sync(full, v[ix + 56], 8);
-      if (q.by == 0) up = quant_bits(hf[ix], r);        // hf = 0 when t == 0: q = 0
+      if (q.by == 0) up = quant_bits(hf[ix], r, wide);        // hf = 0 when t == 0: q = 0
 #pragma unroll
       for (int iy = 7; iy >= 1; --iy) v[ix + 8 * iy] -= v[ix + 8 * (iy - 1)];
       v[ix] -= up;
@@ -398,7 +427,7 @@ __device__ __forceinline__ void residuals_first(const Src &src, const TileGeo &q
       src.row(0, 0, 8 * row, f8);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        v[8 * row + k] = quant_bits(f8[k], r);
+        v[8 * row + k] = quant_bits(f8[k], r, wide);
         if (CHECK) qmax = max(qmax, (uint32_t)v[8 * row + k] - kBiasBits);
       }
     }
@@ -595,9 +624,10 @@ __device__ __forceinline__ void mask_padding(const CompressArgs &a, const TileGe
 
 // Part 2: the remaining differences (no more input reads) and code 0 for
 // padding positions.
-template <int NDIM, bool WHOLE = false>
+template <int NDIM, bool WHOLE = false, bool WIDE = false>
 __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const TileGeo &q, int g,
                                                float r, int32_t (&v)[64]) {
+  constexpr bool wide = WIDE;
   using G = Geo<NDIM>;
   const unsigned full = 0xffffffffu;
   if constexpr (NDIM == 3) {
@@ -607,8 +637,8 @@ __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const Tile
       for (int ix = 0; ix < 8; ++ix) {
         int32_t up = __shfl_up_sync(full, v[ix + 24 + 32 * iz], 4);
         if (q.by == 0)
-          up = WHOLE && q.y0 > 0 ? __float_as_int(q_at(a, q.x0 + ix, q.y0 - 1, q.z0 + iz, r)) -
-                                         __float_as_int(q_at(a, q.x0 + ix, q.y0 - 1, q.z0 + iz - 1, r))
+          up = WHOLE && q.y0 > 0 ? qi_at(a, q.x0 + ix, q.y0 - 1, q.z0 + iz, r, wide) -
+                                         qi_at(a, q.x0 + ix, q.y0 - 1, q.z0 + iz - 1, r, wide)
                                    : 0;
 #pragma unroll
         for (int iy = 3; iy >= 1; --iy) v[ix + 8 * iy + 32 * iz] -= v[ix + 8 * (iy - 1) + 32 * iz];
@@ -627,10 +657,9 @@ __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const Tile
           const uint64_t x = q.x0 - 1;
           const int iy = NDIM == 3 ? row % 4 : row, iz = NDIM == 3 ? row / 4 : 0;
           const uint64_t y = q.y0 + iy, z = q.z0 + iz;
-          left = __float_as_int(q_at(a, x, y, z, r)) - __float_as_int(q_at(a, x, y - 1, z, r));
+          left = qi_at(a, x, y, z, r, wide) - qi_at(a, x, y - 1, z, r, wide);
           if (NDIM == 3)
-            left -= __float_as_int(q_at(a, x, y, z - 1, r)) -
-                    __float_as_int(q_at(a, x, y - 1, z - 1, r));
+            left -= qi_at(a, x, y, z - 1, r, wide) - qi_at(a, x, y - 1, z - 1, r, wide);
         }
       }
 #pragma unroll
@@ -640,7 +669,7 @@ __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const Tile
   } else {
     int32_t hq = (int32_t)kMagicBits;
     if (march_halo<NDIM, WHOLE>(q) && g == 0)
-      hq = quant_bits((q.x0 - 1 < a.dims[0]) ? __ldcs(a.x + q.x0 - 1) : 0.0f, r);
+      hq = quant_bits((q.x0 - 1 < a.dims[0]) ? __ldcs(a.x + q.x0 - 1) : 0.0f, r, wide);
     int32_t left = __shfl_up_sync(full, v[63], 1);
     if (g == 0) left = hq;
 #pragma unroll
@@ -662,15 +691,16 @@ __device__ __forceinline__ void residuals_rest(const CompressArgs &a, const Tile
 
 // all residuals from global memory (the rare escape repack and the outlier
 // pass, when the TMA box no longer holds the tile)
-template <int NDIM, int V, bool WHOLE = false>
+template <int NDIM, int V, bool WHOLE = false, bool WIDE = false>
 __device__ __forceinline__ void residuals_global(const CompressArgs &a, uint64_t T, int g,
                                                  float r, int32_t (&v)[64]) {
   const TileGeo q = tile_geo<NDIM>(a, ChunkGrid(a), T, g);
   uint32_t unused = 0;
   float hf[32];
   load_halo<NDIM, V, WHOLE>(a, q, hf);
-  residuals_first<NDIM, false>(GlobalRows<NDIM, V>{a, q}, q, g, r, hf, v, unused);
-  residuals_rest<NDIM, WHOLE>(a, q, g, r, v);
+  residuals_first<NDIM, false, GlobalRows<NDIM, V>, WIDE>(GlobalRows<NDIM, V>{a, q}, q, g, r, hf,
+                                                          v, unused);
+  residuals_rest<NDIM, WHOLE, WIDE>(a, q, g, r, v);
 }
 
 // residuals -> pairs of 16-bit sign-magnitude codes (Sec. 3.2), even code in
@@ -709,11 +739,11 @@ __device__ __forceinline__ uint32_t pack_codes_escaped(const int32_t (&v)[64], u
 // The rare escape path, kept out of the hot loop: recompute the lane's
 // residuals from global memory, pack them with escapes into pb[32g..32g+31]
 // and return the lane's escape count.
-template <int NDIM, int V, bool WHOLE = false>
+template <int NDIM, int V, bool WHOLE = false, bool WIDE = false>
 __device__ __forceinline__ uint32_t escape_repack(const CompressArgs &a, uint64_t T, int g, float r,
                                                uint32_t *pb) {
   int32_t v[64];
-  residuals_global<NDIM, V, WHOLE>(a, T, g, r, v);
+  residuals_global<NDIM, V, WHOLE, WIDE>(a, T, g, r, v);
   uint32_t w[32];
   const uint32_t n = pack_codes_escaped(v, w);
 #pragma unroll
@@ -779,7 +809,7 @@ __device__ __forceinline__ void finish_tile(const CompressArgs &a, CompShared *s
       h->magic[0] = 'F'; h->magic[1] = 'Z'; h->magic[2] = 'G'; h->magic[3] = '1';
       h->version = a.whole ? 2 : 1;         // 2: whole-field residuals
       h->ndim = (uint8_t)NDIM; h->mode = (uint8_t)a.mode;
-      h->reserved0 = 0;
+      h->reserved0 = rt.wide ? kHdrWide : 0;   // the wide quantiser's streams
       h->dims[0] = (uint32_t)a.dims[0]; h->dims[1] = (uint32_t)a.dims[1];
       h->dims[2] = (uint32_t)a.dims[2];
       h->n_tiles = (uint32_t)n_tiles;
@@ -894,7 +924,8 @@ __device__ __forceinline__ void scan_warp(const CompressArgs &a0, const BatchArg
 // One block per SM.  A single field's launch (BATCH = false) reads its field
 // from the kernel parameters; a batched launch reads each unit's field from
 // the batch's descriptors.
-template <int NDIM, int V, bool CHECK, bool TMA, bool BATCH, bool WHOLE = false>
+template <int NDIM, int V, bool CHECK, bool TMA, bool BATCH, bool WHOLE = false,
+          bool WIDE = false>
 __global__ void __launch_bounds__(kCompThreads, 1)
     compress_kernel(const CompressArgs a0, const __grid_constant__ CUtensorMap tmap0,
                     const BatchArgs b) {
@@ -1035,6 +1066,16 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       const ChunkGrid cg(rt.dx, rt.dy);
       SetScratch *cur = a.set_cur;
       const TileGeo q = tile_geo<NDIM>(a, cg, T, g);
+      uint32_t w[32];
+      bool narrow, escape;
+      if constexpr (WIDE) {
+        // the wide quantiser: every tile takes the integer path below
+        (void)q;
+        next_unit();
+        if (g == 0 && tma_of(nw)) issue(nw);
+        narrow = false;
+        escape = true;
+      } else {
       float hf[32];
       // a batch's TMA fields have 16-byte aligned rows: vector halo loads
       if (BATCH && V < 4 && tma_of(cw)) load_halo<NDIM, 4>(a, q, hf);
@@ -1060,14 +1101,14 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       residuals_rest_f<NDIM, WHOLE>(a, q, g, rt.p.ebx2_r, vf);
       if (CHECK && __any_sync(full, qmax > kBiasedMax) && g == 0) atomicOr(&cur->err, kErrRange);
 
-      uint32_t w[32];
       // narrow: every code of the tile fits in 7 bits and the sign, so the
       // planes of magnitude bits 7..14 are zero and half the transpose is
       // skipped; escape: some |residual| needs more than 15 bits
       if (q.edge) mask_padding<NDIM>(a, q, vf);
       const uint32_t o = pack_codes_f(vf, w);        // vf is dead from here on
-      const bool narrow = !__any_sync(full, (o & ~0x4B00007Fu) != 0u);
-      const bool escape = __any_sync(full, (o & ~0x4B007FFFu) != 0u);
+      narrow = !__any_sync(full, (o & ~0x4B00007Fu) != 0u);
+      escape = __any_sync(full, (o & ~0x4B007FFFu) != 0u);
+      }
       // drain this round's plane buffer before anything below writes it
       Pending &drain = kDef == 0 ? prev1 : prev2;
       if (drain.T != kNoTile) {
@@ -1079,7 +1120,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       if (!narrow && escape) {
         // rare: some |residual| needs more than 15 bits; recompute and repack
         // with escapes out of line (through this round's plane buffer)
-        nout_lane = escape_repack<NDIM, V, WHOLE>(a, T, g, rt.p.ebx2_r, pb);
+        nout_lane = escape_repack<NDIM, V, WHOLE, WIDE>(a, T, g, rt.p.ebx2_r, pb);
 #pragma unroll
         for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
         __syncwarp();
@@ -1154,19 +1195,17 @@ __global__ void __launch_bounds__(kCompThreads, 1)
 // ====================================================================
 constexpr int kOutWarps = 4;                    // outlier pass: warps per block, one tile each
 
-template <int NDIM, int V, bool WHOLE = false>
+template <int NDIM, int V, bool WHOLE = false, bool WIDE = false>
 __global__ void __launch_bounds__(kOutWarps * 32)
     outlier_kernel(const CompressArgs a, uint64_t out_section) {
   const int g = threadIdx.x & 31;
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
   const uint64_t T = (uint64_t)blockIdx.x * kOutWarps + (threadIdx.x >> 5);
   if (T >= n_tiles || a.tile_out_count[T] == 0) return;
-  float fmin = 0.f, fmax = 0.f;
-  bool nonfinite = false;
-  field_range(a, fmin, fmax, nonfinite);
-  const EbParams p = derive_eb(a.mode, a.eb_req, fmin, fmax);
+  uint32_t err = 0;
+  const FieldRt rt = derive_field(a, err);         // the compressor's bound and quantiser
   int32_t v[64];
-  residuals_global<NDIM, V, WHOLE>(a, T, g, p.ebx2_r, v);
+  residuals_global<NDIM, V, WHOLE, WIDE>(a, T, g, rt.p.ebx2_r, v);
   uint32_t cnt = 0;
 #pragma unroll
   for (int e = 0; e < 64; ++e) cnt += (uint32_t)abs(v[e]) > 32767u;

@@ -28,6 +28,7 @@ constexpr int kDecSmemBytes = kDecWarps * kDecWarpSmem;
 
 struct Hdr {
   int version, ndim, mode;
+  bool wide;                     // header byte 7: |q| may pass 2^22 - 1
   uint32_t dims[3];
   uint64_t n_tiles, nnz, nout, n_chunks, ncx, ncy, n_elems;
   float ebx2;
@@ -43,10 +44,11 @@ __device__ Hdr read_header(const DecompressArgs &a) {
   const StreamHeader *s = reinterpret_cast<const StreamHeader *>(a.in);
   if (s->magic[0] != 'F' || s->magic[1] != 'Z' || s->magic[2] != 'G' || s->magic[3] != '1')
     return h;
-  if (!(s->version == 1 || (s->version == 2 && a.accept_whole)) || s->reserved0 != 0 ||
-      s->mode > 1)
+  if (!(s->version == 1 || (s->version == 2 && a.accept_whole)) ||
+      (s->reserved0 != 0 && s->reserved0 != kHdrWide) || s->mode > 1)
     return h;
   h.version = s->version;
+  h.wide = s->reserved0 == kHdrWide;
   h.ndim = s->ndim;
   h.mode = s->mode;
   if (h.ndim < 1 || h.ndim > 3) return h;
@@ -442,7 +444,7 @@ __device__ __forceinline__ void add_corrections(const DecompressArgs &a, uint64_
 //        [2] (x, y) at c*1024 + 32y + x;
 //   2-D: [0] y at c*128 + y, [1] x at c*64 + x;   1-D: [0] at c.
 // Faces hold L at the chunk's last x ([0]), last y ([1]), last z ([2]).
-template <int NDIM, int PHASE>
+template <int NDIM, int PHASE, bool WIDE = false>
 __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_t *pbuf,
                                   SetScratch *cur) {
   using G = Geo<NDIM>;
@@ -457,6 +459,9 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
   const FastDiv dx((uint32_t)h.ncx), dy((uint32_t)h.ncy);
   const uint64_t X = h.dims[0], Y = h.dims[1];
   const float e2 = h.ebx2;
+  // the float bias of 1.5 * 2^23 that the prefix sums carry into every q
+  // (none for the wide quantiser's streams: q is converted as an integer)
+  const int32_t bias = WIDE ? 0 : (int32_t)kMagicBits;
   // chunks are dealt out statically: their payload offsets come from the
   // offsets pass, so no chunk waits for another
   const uint64_t n_warps = (uint64_t)gridDim.x * kDecWarps;
@@ -526,16 +531,16 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
           const int4 p = __ldg(cc + 8 * iy), q = __ldg(cc + 8 * iy + 1);
           const int32_t r8[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
 #pragma unroll
-          for (int ix = 0; ix < 8; ++ix) carry[ix + 8 * iy] = r8[ix] + (int32_t)kMagicBits;
+          for (int ix = 0; ix < 8; ++ix) carry[ix + 8 * iy] = r8[ix] + bias;
         }
       } else if constexpr (NDIM == 2) {
         const int4 *cb = reinterpret_cast<const int4 *>(a.corr[1] + c * 64 + 8 * bx);
         const int4 p = __ldg(cb), q = __ldg(cb + 1);
         const int32_t r8[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int ix = 0; ix < 8; ++ix) carry[ix] = r8[ix] + (int32_t)kMagicBits;
+        for (int ix = 0; ix < 8; ++ix) carry[ix] = r8[ix] + bias;
       } else {
-        carry[0] = __ldg(a.corr[0] + c) + (int32_t)kMagicBits;
+        carry[0] = __ldg(a.corr[0] + c) + bias;
       }
     }
 #pragma unroll 1
@@ -619,7 +624,7 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
         }
       }
       // the chunk origin carries the float bias of 1.5*2^23 into every q
-      if (PHASE == 0 && t == 0 && g == 0) v[0] += (int32_t)kMagicBits;
+      if (PHASE == 0 && t == 0 && g == 0) v[0] += bias;
       inverse_lorenzo<NDIM>(v, carry, g);
       if constexpr (PHASE == 1) {
         write_faces<NDIM>(a, c, t, bx, by, g, v);
@@ -628,9 +633,15 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
       if constexpr (PHASE == 2) add_corrections<NDIM>(a, c, t, bx, by, v);
       // q -> fl(float(q) * 2eb), 8-float rows
       auto row_floats = [&](int row, float (&f)[8]) {
+        if constexpr (WIDE) {
+          // q beyond 2^22: unbiased integers, converted (the same fl(float(q) * 2eb))
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          f[k] = __fmul_rn(__fsub_rn(__int_as_float(v[8 * row + k]), kRoundMagic), e2);
+          for (int k = 0; k < 8; ++k) f[k] = __fmul_rn(__int2float_rn(v[8 * row + k]), e2);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            f[k] = __fmul_rn(__fsub_rn(__int_as_float(v[8 * row + k]), kRoundMagic), e2);
+        }
       };
       bool staged = false;
       if constexpr (NDIM >= 2) staged = vw == 1;
@@ -728,6 +739,7 @@ __global__ void __launch_bounds__(kOffChunks) dec_offsets_kernel(const Decompres
     else if (h.n_chunks > a.status_cap) atomicOr(&cur->err, kErrCorrupt);
     cur->version = h.ok ? (uint32_t)h.version : 0;
     cur->ndim = h.ok ? (uint32_t)h.ndim : 0;
+    cur->wide = h.ok && h.wide ? 1u : 0u;
     cur->ncx = h.ok ? (uint32_t)h.ncx : 0;
     cur->ncy = h.ok ? (uint32_t)h.ncy : 0;
     cur->n_chunks = h.ok ? h.n_chunks : 0;
@@ -797,7 +809,9 @@ __global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const Dec
   const int w = threadIdx.x >> 5;
   const Hdr h = read_header(a);
   if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
-  if (h.version != 1) return;            // version 2: phases 1 and 2 follow
+  // version 2 (phases 1 and 2 follow) and the wide quantiser's streams
+  // (decompress_wide_kernel follows) are left to their own kernels
+  if (h.version != 1 || h.wide) return;
   uint32_t *pbuf = dsmem + w * (kDecWarpSmem / 4);
   grid_dependency_wait();                // the offsets pass's chunk offsets
   if (h.ndim == 3) decompress_chunks<3, 0>(a, h, pbuf, cur);
@@ -805,19 +819,34 @@ __global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const Dec
   else decompress_chunks<1, 0>(a, h, pbuf, cur);
 }
 
+// a version-1 stream of the wide quantiser (header byte 7)
+__global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_wide_kernel(const DecompressArgs a) {
+  extern __shared__ __align__(16) uint32_t dsmem[];
+  SetScratch *cur = a.set_cur;
+  const int w = threadIdx.x >> 5;
+  const Hdr h = read_header(a);
+  if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
+  if (h.version != 1 || !h.wide) return;
+  uint32_t *pbuf = dsmem + w * (kDecWarpSmem / 4);
+  grid_dependency_wait();
+  if (h.ndim == 3) decompress_chunks<3, 0, true>(a, h, pbuf, cur);
+  else if (h.ndim == 2) decompress_chunks<2, 0, true>(a, h, pbuf, cur);
+  else decompress_chunks<1, 0, true>(a, h, pbuf, cur);
+}
+
 // phases 1 and 2 of a version-2 stream (after the offsets pass and phase 0)
-template <int PHASE>
+template <int PHASE, bool WIDE>
 __global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_whole_kernel(const DecompressArgs a) {
   extern __shared__ __align__(16) uint32_t dsmem[];
   SetScratch *cur = a.set_cur;
   const int w = threadIdx.x >> 5;
   const Hdr h = read_header(a);
   if (!h.ok || a.out_cap_elems < h.n_elems || h.n_chunks > a.status_cap) return;
-  if (h.version != 2) return;
+  if (h.version != 2 || h.wide != WIDE) return;
   uint32_t *pbuf = dsmem + w * (kDecWarpSmem / 4);
-  if (h.ndim == 3) decompress_chunks<3, PHASE>(a, h, pbuf, cur);
-  else if (h.ndim == 2) decompress_chunks<2, PHASE>(a, h, pbuf, cur);
-  else decompress_chunks<1, PHASE>(a, h, pbuf, cur);
+  if (h.ndim == 3) decompress_chunks<3, PHASE, WIDE>(a, h, pbuf, cur);
+  else if (h.ndim == 2) decompress_chunks<2, PHASE, WIDE>(a, h, pbuf, cur);
+  else decompress_chunks<1, PHASE, WIDE>(a, h, pbuf, cur);
 }
 
 // The grid: enough blocks for max_chunks chunks, at most two per SM (the
@@ -843,17 +872,24 @@ cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s)
   cfg.attrs = attr;
   // phases 1 and 2 wait for everything before them (no dependency wait inside)
   cfg.numAttrs = a.phase == 0 ? 1 : 0;
-  if (a.phase == 1) return cudaLaunchKernelEx(&cfg, decompress_whole_kernel<1>, a);
-  if (a.phase == 2) return cudaLaunchKernelEx(&cfg, decompress_whole_kernel<2>, a);
+  if (a.wide) {
+    if (a.phase == 1) return cudaLaunchKernelEx(&cfg, decompress_whole_kernel<1, true>, a);
+    if (a.phase == 2) return cudaLaunchKernelEx(&cfg, decompress_whole_kernel<2, true>, a);
+    return cudaLaunchKernelEx(&cfg, decompress_wide_kernel, a);
+  }
+  if (a.phase == 1) return cudaLaunchKernelEx(&cfg, decompress_whole_kernel<1, false>, a);
+  if (a.phase == 2) return cudaLaunchKernelEx(&cfg, decompress_whole_kernel<2, false>, a);
   return cudaLaunchKernelEx(&cfg, decompress_kernel, a);
 }
 
 int decompress_blocks_per_sm() {
   int n = 0;
-  cudaFuncSetAttribute(decompress_whole_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kDecSmemBytes);
-  cudaFuncSetAttribute(decompress_whole_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       kDecSmemBytes);
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaFuncSetAttribute(decompress_whole_kernel<1, false>, at, kDecSmemBytes);
+  cudaFuncSetAttribute(decompress_whole_kernel<2, false>, at, kDecSmemBytes);
+  cudaFuncSetAttribute(decompress_whole_kernel<1, true>, at, kDecSmemBytes);
+  cudaFuncSetAttribute(decompress_whole_kernel<2, true>, at, kDecSmemBytes);
+  cudaFuncSetAttribute(decompress_wide_kernel, at, kDecSmemBytes);
   cudaFuncSetAttribute(decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        kDecSmemBytes);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, decompress_kernel, kDecWarps * 32,

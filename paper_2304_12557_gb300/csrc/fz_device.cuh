@@ -28,6 +28,12 @@ constexpr uint32_t kMagicBits = 0x4B400000u;   // bits of kRoundMagic
 constexpr uint32_t kBiasBits = 0x4B000001u;
 constexpr int32_t kPadBiased = 0x3FFFFF;       // biased form of q = 0
 constexpr uint32_t kBiasedMax = 0x7FFFFEu;     // biased form of q = 2^22-1
+// The quantiser's wide range: |q| <= 2^28 - 1 (a 3-D residual, a signed
+// sum of eight q, then fits an i32 outlier record).  Fields within 2^22 - 1
+// use the fp32 rounding trick; the others take integer conversion (their
+// streams set header byte 7 to 1).
+constexpr float kWideLimit = 268435456.0f;      // 2^28: |fl(x r)| below it
+constexpr uint8_t kHdrWide = 1;                 // header byte 7
 
 // error bits gathered in device memory, mapped to FZ_ERR_* on the host
 constexpr uint32_t kErrRange = 1u;     // |q| too large or non-finite input
@@ -36,6 +42,7 @@ constexpr uint32_t kErrTimeout = 4u;   // bounded wait ran out
 constexpr uint32_t kErrCapacity = 8u;  // payload would pass out_capacity
 constexpr uint32_t kErrCorrupt = 16u;  // decompressor: inconsistent stream
 constexpr uint32_t kErrNonFinite = 32u;
+constexpr uint32_t kErrWide = 64u;     // the field needs the wide quantiser's launch
 
 // look-back status word: [63:62] flag, [61:32] blocks, [31:0] outliers.
 // Unit u's word lives at status[u * kStatusStride]: spacing the words out
@@ -111,7 +118,8 @@ struct SetScratch {
   uint32_t version;     // decompressor: the header's stream version (0: invalid)
   uint32_t ndim;        // decompressor: the header's dimensionality
   uint32_t ncx, ncy;    // decompressor: the chunk grid's x and y extents
-  uint32_t pad[3];
+  uint32_t wide;        // decompressor: header byte 7 (the wide quantiser)
+  uint32_t pad[2];
 };
 static_assert(sizeof(SetScratch) == 64, "scratch block is 64 bytes");
 

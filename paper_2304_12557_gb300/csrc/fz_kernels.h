@@ -36,6 +36,11 @@ struct CompressArgs {
   int ndim;                    // batches: the field's dimensionality
   int whole;                   // whole-field Lorenzo (stream version 2): residuals
                                // across chunk faces
+  int allow_wide;              // a field past |q| = 2^22 - 1 stops with kErrWide for
+                               // a second launch (else kErrRange)
+  int wide;                    // this launch uses the wide quantiser (|q| up to
+                               // 2^28 - 1), checked against the range pass's
+                               // result in *range
   SetScratch *set_cur, *set_next;
   uint64_t *status_cur, *status_next;
   uint32_t *tile_out_prefix;   // per tile: exclusive outlier prefix
@@ -66,6 +71,8 @@ struct DecompressArgs {
   // corrections corr[0..2], written out.  Face layouts in fz_whole.cu.
   int accept_whole;
   int phase;
+  int wide;                    // streams of the wide quantiser (header byte 7): the
+                               // kernels that convert q as integers
   int32_t *face[3];
   const int32_t *corr[3];
 };

@@ -142,6 +142,7 @@ extern "C" int fz_compress_noalloc(const float *d_in, const uint64_t dims[3], in
   }
   fz::CompressArgs a{};
   a.x = d_in;
+  a.allow_wide = 0;                   // |q| up to 2^22 - 1 (no second launch)
   for (int i = 0; i < 3; ++i) a.dims[i] = d[i];
   a.pitch = d[0];
   a.ncx = ncx;

@@ -112,6 +112,7 @@ struct Req {
   uint64_t dims[3] = {1, 1, 1};
   int ndim = 0, mode = FZ_EB_REL;
   double eb = 0.0;
+  bool wide = false;             // decompress: a stream of the wide quantiser
   // pool memory
   uint64_t in_off = kNone, out_off = kNone, scratch_off = kNone;
   uint64_t out_cap = 0, scratch_bytes = 0;
@@ -408,6 +409,7 @@ bool step(fz_server *S) {
     a.chunk_olo = reinterpret_cast<uint32_t *>(arrays + align_up(4 * r.max_chunks, kAlign));
     a.wait_limit_ns = 2000000000ull;
     a.skip_publish_chunk = ~0ull;
+    a.wide = r.wide ? 1 : 0;
     cudaStreamWaitEvent(S->s_dec, S->ev_uploads, 0);
     cudaEventRecord(r.ev_start, S->s_dec);
     cudaMemsetAsync(scr, 0, 2 * sizeof(fz::SetScratch) + units * fz::kStatusStride * 8, S->s_dec);
@@ -552,6 +554,7 @@ int fz_server_submit(fz_server *S, const fz_request *q, uint64_t *id) {
     if (fz_inspect(q->h_in, q->in_bytes, &info) != FZ_OK) return FZ_ERR_CORRUPT;
     if (info.stream_bytes != q->in_bytes) return FZ_ERR_CORRUPT;
     if (info.version != 1) return FZ_ERR_VERSION;
+    r.wide = info.wide != 0;
     r.in_bytes = q->in_bytes;
     r.n_elems = info.dims[0] * info.dims[1] * info.dims[2];
     r.n_chunks = info.n_tiles / fz::kTilesPerChunk;

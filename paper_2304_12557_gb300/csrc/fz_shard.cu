@@ -77,6 +77,9 @@ int concat_plan(const uint8_t (*hdrs)[64], const uint64_t *sizes, int n, ConcatP
   const uint64_t min_bytes = fz_stream_min_bytes(dims, first.ndim);
   if (min_bytes == 0 || min_bytes != 64 + 32 * tiles) return FZ_ERR_CORRUPT;
   std::memcpy(plan->hdr, hdrs[0], 64);
+  // the wide quantiser's flag: set when any slab needed it (the codes and
+  // outlier records are the same either way)
+  for (int i = 0; i < n; ++i) plan->hdr[7] |= hdrs[i][7];
   put32(plan->hdr + 8 + 4 * ax, (uint32_t)slow);
   put32(plan->hdr + 20, (uint32_t)tiles);
   put32(plan->hdr + 44, (uint32_t)nnz);

@@ -314,3 +314,70 @@ def test_host_buffer_calls(codec, torch):
     y = codec.decompress_host(s)
     _, xr = oracle.decompress(ostream)
     np.testing.assert_array_equal(y.ravel().view(np.uint32), xr.view(np.uint32))
+
+
+# ------------------------------------------------------------ wide quantiser
+def _wide_cases():
+    rng = np.random.default_rng(91)
+    rough = {1: (70001,), 2: (130, 211), 3: (19, 37, 45)}
+    out = []
+    for nd, shape in rough.items():
+        x = (rng.standard_normal(shape) * 3e4).astype(np.float32)
+        out.append((f"rough{nd}d_abs", x, nd, fz.EB_ABS, 5e-4))
+        out.append((f"rough{nd}d_rel", x, nd, fz.EB_REL, 2e-8))
+    smooth = (fields.grf((40, 64, 96), -3.0, 92) * 1e5).astype(np.float32)
+    out.append(("smooth3d_abs", smooth, 3, fz.EB_ABS, 2e-3))
+    out.append(("smooth3d_rel", smooth, 3, fz.EB_REL, 1e-8))
+    return out
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_wide_quantiser_matches_the_oracle(codec, torch, case):
+    """|q| past 2^22 - 1 (up to 2^28 - 1): the second launch with integer
+    quantisation gives the oracle's stream (header byte 7 set) and its
+    reconstruction; absolute bounds reach it through the range pass that
+    classifies the first launch's range error, relative bounds through the
+    range pass itself."""
+    name, x, ndim, mode, eb = _wide_cases()[case]
+    g, xr = check_parity(codec, torch, x, ndim, mode, eb)
+    info = fz.inspect(g[:64])
+    assert info["wide"], name
+    # the reconstruction is within the bound
+    err = np.abs(x.ravel().astype(np.float64) - xr.astype(np.float64))
+    slack = 2.0 ** -22 * np.maximum(np.abs(x.ravel()), np.abs(xr)).astype(np.float64)
+    assert np.all(err <= info["eb"] + slack)
+
+
+def test_wide_quantiser_limits_and_other_entries(codec, torch):
+    x = (np.random.default_rng(93).standard_normal((19, 37, 45)) * 3e4).astype(np.float32)
+    # beyond 2^28 - 1: refused by both, in both modes
+    assert _status(codec, torch, x * np.float32(1e4), 3, fz.EB_ABS, 5e-4)[0] == fz.ERR_EB_RANGE
+    assert oracle.compress(x * np.float32(1e4), 3, oracle.EB_ABS, 5e-4)[0] == oracle.ERR_EB_RANGE
+    assert _status(codec, torch, x, 3, fz.EB_REL, 1e-10)[0] == fz.ERR_EB_RANGE
+    assert oracle.compress(x, 3, oracle.EB_REL, 1e-10)[0] == oracle.ERR_EB_RANGE
+    # whole-field Lorenzo with the wide quantiser
+    st, ostream = oracle.compress(x, 3, oracle.EB_ABS, 5e-4, whole=True)
+    assert st == oracle.OK and ostream[7] == 1
+    s = codec.compress(torch.from_numpy(x).cuda(), mode="abs", eb=5e-4, whole=True)
+    assert s.cpu().numpy().tobytes() == ostream
+    y = codec.decompress(s).cpu().numpy().ravel()
+    st, want = oracle.decompress(ostream)
+    np.testing.assert_array_equal(y.view(np.uint32), want.view(np.uint32))
+    # a server decompresses a wide stream like fz_decompress
+    st, stream = oracle.compress(x, 3, oracle.EB_ABS, 5e-4)
+    srv = fz.Server(0, pool_bytes=256 << 20)
+    try:
+        got = srv.fetch(srv.submit_decompress(np.frombuffer(stream, np.uint8).copy()))
+    finally:
+        srv.close()
+    st, want = oracle.decompress(stream)
+    np.testing.assert_array_equal(got.reshape(-1).view(np.uint32), want.view(np.uint32))
+    # batches keep |q| within 2^22 - 1
+    xt = torch.from_numpy(x).cuda()
+    out = torch.zeros(fz.compress_bound([45, 37, 19], 3), dtype=torch.uint8, device="cuda")
+    b = fz.Batch(codec, [(xt, out, "rel", 2e-8, 3)])
+    try:
+        sizes, sts = b.compress()
+        assert sts[0] == fz.ERR_EB_RANGE
+    finally:
+        b.close()

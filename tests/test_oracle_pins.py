@@ -244,10 +244,41 @@ def test_prequant_ties_to_even():
 
 
 def test_prequant_range_guard():
-    assert oracle.prequant1(4194303.0, 1.0) == (0, 4194303)
-    assert oracle.prequant1(-4194303.0, 1.0) == (0, -4194303)
-    assert oracle.prequant1(4194304.0, 1.0)[0] == oracle.ERR_EB_RANGE
-    assert oracle.prequant1(-4194303.5, 1.0)[0] == oracle.ERR_EB_RANGE
+    # |q| <= 2^28 - 1: every 3-D residual (a signed sum of eight q) fits the
+    # outlier record's i32.  Floats near 2^28 are 16 apart.
+    assert oracle.QMAX == 2 ** 28 - 1
+    assert oracle.prequant1(4194304.0, 1.0) == (0, 4194304)
+    assert oracle.prequant1(-4194303.5, 1.0) == (0, -4194304)
+    assert oracle.prequant1(268435440.0, 1.0) == (0, 268435440)
+    assert oracle.prequant1(-268435440.0, 1.0) == (0, -268435440)
+    assert oracle.prequant1(268435456.0, 1.0)[0] == oracle.ERR_EB_RANGE
+    assert oracle.prequant1(-268435456.0, 1.0)[0] == oracle.ERR_EB_RANGE
+    assert oracle.prequant1(float("inf"), 1.0)[0] == oracle.ERR_EB_RANGE
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_wide_quantiser_flag_and_round_trip(ndim):
+    # a field whose |q| passes 2^22 - 1 sets header byte 7 and still round
+    # trips to the closed form fl(float(q) * 2eb); the 3-D stencil's residuals
+    # then need outlier records beyond 2^22
+    rng = np.random.default_rng(31 + ndim)
+    shape = {1: (70001,), 2: (130, 211), 3: (19, 37, 45)}[ndim]
+    x = (rng.standard_normal(shape) * 3e4).astype(np.float32)
+    st, s = oracle.compress(x, ndim, oracle.EB_ABS, 5e-4)
+    assert st == oracle.OK
+    assert s[7] == 1
+    ebx2, ebx2_r = struct.unpack("<2f", s[36:44])
+    q = np.rint(x.astype(np.float32) * np.float32(ebx2_r)).astype(np.int64)
+    assert np.abs(q).max() > 2 ** 22
+    st, xr = oracle.decompress(s)
+    assert st == oracle.OK
+    exp = (q.astype(np.float32) * np.float32(ebx2)).astype(np.float32).ravel()
+    np.testing.assert_array_equal(xr.view(np.uint32), exp.view(np.uint32))
+    # the same field a little smaller stays narrow: byte 7 = 0
+    st, s2 = oracle.compress((x / 64).astype(np.float32), ndim, oracle.EB_ABS, 5e-4)
+    assert st == oracle.OK and s2[7] == 0
+    # and beyond 2^28 - 1 it is refused
+    assert oracle.compress(x * np.float32(1e4), ndim, oracle.EB_ABS, 5e-4)[0] == oracle.ERR_EB_RANGE
 
 
 def test_derive_eb_rounds_down_and_reciprocal():
