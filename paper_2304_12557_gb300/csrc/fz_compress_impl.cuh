@@ -935,6 +935,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
   const unsigned full = 0xffffffffu;
   const int g = threadIdx.x & 31, wid = threadIdx.x >> 5;
   grid_dependency_wait();                // a preceding range pass's result
+  if constexpr (!BATCH) grid_launch_dependents();   // the call's result copy may be scheduled
   constexpr int kDef = defer_rounds<BATCH>(), kBufs = plane_bufs<BATCH>();
   // per compute warp: [TMA box 8 KB] (TMA only) [plane buffers]; then the
   // block's CompShared; then (batches) one WarpField per compute warp

@@ -805,6 +805,7 @@ __global__ void __launch_bounds__(kOffChunks) dec_offsets_kernel(const Decompres
 
 __global__ void __launch_bounds__(kDecWarps * 32, 3) decompress_kernel(const DecompressArgs a) {
   extern __shared__ __align__(16) uint32_t dsmem[];
+  grid_launch_dependents();              // the call's result copy may be scheduled now
   SetScratch *cur = a.set_cur;
   const int w = threadIdx.x >> 5;
   const Hdr h = read_header(a);
@@ -858,6 +859,29 @@ cudaError_t launch_dec_offsets(const DecompressArgs &a, uint64_t max_chunks, int
   if (blocks > (uint64_t)sms * 2) blocks = (uint64_t)sms * 2;
   dec_offsets_kernel<<<(unsigned)(blocks ? blocks : 1), kOffChunks, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+// The 64-byte result block to (mapped host) memory once the grid before it
+// on the stream has finished.
+__global__ void __launch_bounds__(32) copy_result_kernel(const SetScratch *src, SetScratch *dst) {
+  grid_dependency_wait();
+  constexpr int kWords = (int)(sizeof(SetScratch) / 4);
+  if (threadIdx.x < kWords)
+    reinterpret_cast<uint32_t *>(dst)[threadIdx.x] =
+        reinterpret_cast<const uint32_t *>(src)[threadIdx.x];
+}
+
+cudaError_t launch_copy_result(const SetScratch *src, SetScratch *dst, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(32);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, copy_result_kernel, src, dst);
 }
 
 cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s) {

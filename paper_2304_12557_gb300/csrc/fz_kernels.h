@@ -120,6 +120,9 @@ cudaError_t launch_dec_offsets(const DecompressArgs &a, uint64_t max_chunks, int
                                cudaStream_t s);
 cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s);
 // look-back status words the offsets pass uses and clears in the other set
+// one warp copies a 64-byte result block to (mapped host) memory, after the
+// kernel before it on the stream (programmatic dependent launch)
+cudaError_t launch_copy_result(const SetScratch *src, SetScratch *dst, cudaStream_t s);
 uint64_t decompress_status_words(uint64_t n_chunks);
 
 // the unfused compression path (fz_staged.cu): intermediate data in HBM
