@@ -44,19 +44,20 @@ WORKLOAD_DESC = ("512x512x512 float32 lognormal density exp(0.5 g), g a unit-std
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# each kernel on the 512^3 workload, from one ncu capture of this benchmark's
-# kernels.  A figure stands only while the kernel's sources are the ones that
-# were captured (SHA-256 over them); otherwise the line reports null.
+# each kernel on the 512^3 workload: the mean of two warmed-up launches of one
+# ncu capture of that kernel alone (-k, -c 2) in this benchmark.  A figure
+# stands only while the kernel's sources are the ones that were captured
+# (SHA-256 over them); otherwise the line reports null.
 TRAFFIC = {
     "compress_kernel": (("fz_compress.cu", "fz_compress_impl.cuh", "fz_device.cuh", "fz_kernels.h"),
-                        "01a8b3b518e34d96c1d15f96020cda5d7b70fd0fa3ed40c61f4d42731941a812",
-                        537730304 + 73928576),
+                        "4e28c932ee334039abe9c713ab4df73555757e328454988133f6b9f1888b574c",
+                        537734016 + 75448576),
     "decompress_kernel": (("fz_decompress.cu", "fz_device.cuh", "fz_kernels.h"),
-                          "cdbfb55b3e23e848a58e6056c4831aeea459fb9f0418e14de0df026eab31f8b6",
-                          96729344 + 471590784),
+                          "5364ad8ff3401c28669c7db25067b54362aad14732720885ad81b5a6136b5900",
+                          96759680 + 473136896),
     "range_kernel": (("fz_compress.cu", "fz_device.cuh", "fz_kernels.h"),
-                     "5268631cca749c88a1faef474ab0a06ac314f2258683a7ce5665afeee9f97395",
-                     536893824 + 77440),
+                     "486d97e3bc628d72aeac5cd9d6048c343949b3e5465ba5a5154b264c5e2b6adf",
+                     536902144 + 1532928),
 }
 
 
