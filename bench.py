@@ -166,6 +166,55 @@ def cpu_oracle_round_trip(x, reps=1, all_cores=False):
     return time.perf_counter() - t0, len(s)
 
 
+def run_cpu_baseline_table(args, rank):
+    """The cpu_baseline leg over the configurations: the CPU oracle as it
+    stands timed on the host cores, compress and decompress separately, on the
+    64^3 bumps, the 1800x3600 climate-like and the 512^3 lognormal fields at
+    relative bounds 1e-2, 1e-3 and 1e-4: once single-threaded and once with
+    the all-cores variant, whose streams and reconstructions must equal the
+    single-threaded ones byte for byte (rank 0 only; no GPU work)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    from paper_2304_12557_gb300 import fields
+    oracle.build()
+    cfgs = [("bumps3d_64", fields.bumps3d(64), 3), ("climate2d_1800x3600", fields.climate2d(), 2),
+            ("cosmo3d_512", fields.cosmo3d(512), 3)]
+    rows = []
+    for name, x, ndim in cfgs:
+        nbytes = 4 * x.size
+        for eb in (1e-2, 1e-3, 1e-4):
+            row = {"field": name, "rel_eb": eb}
+            ref = None
+            for label, all_cores in (("one_thread", False), ("all_cores", True)):
+                t0 = time.perf_counter()
+                st, s = oracle.compress(x, ndim, oracle.EB_REL, eb, all_cores=all_cores)
+                t1 = time.perf_counter()
+                assert st == oracle.OK, (name, eb, st)
+                st, y = oracle.decompress(s, x.size, all_cores=all_cores)
+                t2 = time.perf_counter()
+                assert st == oracle.OK, (name, eb, st)
+                if ref is None:
+                    ref = (s, y.tobytes())
+                    row["ratio"] = nbytes / len(s)
+                else:
+                    row["all_cores_identical"] = s == ref[0] and y.tobytes() == ref[1]
+                row[label] = {"compress_gbs": nbytes / (t1 - t0) / 1e9,
+                              "decompress_gbs": nbytes / (t2 - t1) / 1e9,
+                              "compress_s": t1 - t0, "decompress_s": t2 - t1}
+            rows.append(row)
+    print(json.dumps({"metric": "CPU oracle compress/decompress GB/s of fp32 input per field and bound",
+                      "value": None, "unit": "GB/s",
+                      "config": {"workload": "cpu_baseline",
+                                 "fields": [c[0] for c in cfgs], "rel_eb": [1e-2, 1e-3, 1e-4]},
+                      "cpu_baseline": {"kind": "oracle", "cores": oracle.threads(),
+                                       "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                                       "sample": "each field whole, one compress and one "
+                                                 "decompress per variant and bound"},
+                      "rows": rows}), flush=True)
+
+
 def cpu_model() -> str:
     try:
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -877,10 +926,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="cosmo3d_512",
-                    choices=["cosmo3d_512", "batch256", "serve", "quality"],
+                    choices=["cosmo3d_512", "batch256", "serve", "quality", "cpu_baseline"],
                     help="cosmo3d_512: the single-field round trip (default); batch256: "
                          "256 uneven fields through one planned batch; serve: the request "
-                         "server under Poisson arrivals; quality: rate-distortion report")
+                         "server under Poisson arrivals; quality: rate-distortion report; "
+                         "cpu_baseline: the CPU oracle timed per field and bound")
     ap.add_argument("--size", type=int, default=512,
                     help="edge of the cubic field (512 = the workload; smaller "
                          "sizes only for profiling captures)")
@@ -903,6 +953,8 @@ def main():
         run_serve(args, rank, world, local_rank)
     elif args.workload == "quality":
         run_quality(args, rank)
+    elif args.workload == "cpu_baseline":
+        run_cpu_baseline_table(args, rank)
     else:
         run_ours(args, rank, world, local_rank, dist)
     if dist is not None:
