@@ -142,7 +142,16 @@ int fz_decompress(fz_ctx *ctx, const void *d_in, uint64_t in_size,
 
 /* Host-buffer forms of the two calls: copy h_in to the device, run the
  * device call on context-owned staging buffers (grown as needed), copy the
- * result back to h_out.  Same arguments and errors as the device forms. */
+ * result back to h_out.  Same arguments and errors as the device forms.
+ * fz_decompress_host of a version-1 stream whose field is 64 MiB or more
+ * works in up to four slabs of whole chunk planes (3-D), chunk rows (2-D)
+ * or chunks (1-D): the stream is copied in on a second stream of the
+ * context (header, flags and outlier records first, then the payload in
+ * pieces), each slab is decoded once its payload is in, and its part of the
+ * field is copied out on a third stream while later slabs are decoded and
+ * the rest of the stream comes in.  The call orders itself after earlier
+ * work on `stream` and returns when h_out is complete.  h_in and h_out in
+ * pinned memory let the copies overlap; pageable buffers work too. */
 int fz_compress_host(fz_ctx *ctx, const float *h_in, const uint64_t dims[3],
                      int ndim, int mode, double eb, void *h_out,
                      uint64_t out_capacity, uint64_t *out_size, void *stream);

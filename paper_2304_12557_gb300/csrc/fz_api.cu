@@ -31,6 +31,11 @@ struct fz_ctx {
   int range_blocks = 0;
   SetScratch *h_res = nullptr;         // pinned, mapped
   SetScratch *h_res_dev = nullptr;     // h_res as the device addresses it
+  // the pipelined host-buffer decompression: copy streams, events and the
+  // slab boundaries' payload offsets (mapped pinned memory)
+  cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+  cudaEvent_t pipe_ev[24] = {};
+  uint32_t *h_slab = nullptr, *h_slab_dev = nullptr;
   RangeResult *h_range = nullptr;      // pinned
   int cur = 0;
   uint64_t dirty_hi[2] = {0, 0};
@@ -298,6 +303,11 @@ void fz_destroy(fz_ctx *c) {
   cudaFree(c->stage_in);
   cudaFree(c->stage_out);
   if (c->h_res) cudaFreeHost(c->h_res);
+  if (c->h_slab) cudaFreeHost(c->h_slab);
+  for (cudaEvent_t e : c->pipe_ev)
+    if (e) cudaEventDestroy(e);
+  if (c->pipe_in) cudaStreamDestroy(c->pipe_in);
+  if (c->pipe_out) cudaStreamDestroy(c->pipe_out);
   if (c->h_range) cudaFreeHost(c->h_range);
   for (cudaEvent_t e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -857,17 +867,12 @@ static int decompress_wide(fz_ctx *c, fz::DecompressArgs a, const SetScratch &r,
   return FZ_OK;
 }
 
-int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
-                  uint64_t cap_elems, void *stream) {
-  if (!c || !d_in || !d_out) return FZ_ERR_ARG;
-  if ((reinterpret_cast<uintptr_t>(d_in) & 15u) || (reinterpret_cast<uintptr_t>(d_out) & 3u))
-    return FZ_ERR_ARG;
-  if (in_size < 64) return FZ_ERR_CORRUPT;
-  DeviceGuard guard(c->device);
-  if (!guard.ok) return FZ_ERR_CUDA;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool timed = c->call_timing;
-  if (timed) cudaEventRecord(c->call_ev[2], s);
+// The decompression call up to its first decoding launch: argument checks,
+// scratch, and the offsets pass (every chunk's first payload block and first
+// outlier record) on stream s.
+static int decompress_begin(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
+                            uint64_t cap_elems, cudaStream_t s, fz::DecompressArgs *out_a,
+                            int *out_grid, int *out_set) {
   // every chunk carries 128 bytes of flags, which bounds the chunk count
   uint64_t bound = (in_size - 64) / 128;
   const uint64_t max_chunks = kMaxCodes / fz::kChunkCodes + 1;
@@ -891,7 +896,6 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   a.wait_limit_ns = c->wait_limit_ns;
   a.skip_publish_chunk = c->skip_publish;
   a.accept_whole = 1;
-  const int grid = c->num_sms * c->dec_blocks_per_sm;
   prof_reset(c);
   prof_begin(c, 4, s);
   if (fz::launch_dec_offsets(a, bound, c->num_sms, s) != cudaSuccess) {
@@ -899,12 +903,18 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
     return FZ_ERR_CUDA;
   }
   prof_end(c, 4, s);
-  prof_begin(c, 3, s);
-  if (fz::launch_decompress(a, grid, s) != cudaSuccess) {
-    mark_all_dirty(c);
-    return FZ_ERR_CUDA;
-  }
-  prof_end(c, 3, s);
+  *out_a = a;
+  *out_grid = c->num_sms * c->dec_blocks_per_sm;
+  *out_set = A;
+  return FZ_OK;
+}
+
+// The rest of the call after its decoding launches: the result block, the
+// set's bookkeeping, the error mapping, and the passes of version-2 and wide
+// streams (which the version-1 kernel leaves alone).
+static int decompress_end(fz_ctx *c, const fz::DecompressArgs &a, int grid, int A,
+                          cudaStream_t s, bool timed) {
+  int st;
   if ((st = read_set(c, A, s, timed ? c->call_ev[3] : nullptr))) {
     mark_all_dirty(c);
     return st;
@@ -923,6 +933,33 @@ int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
   if (r.nout != r.hdr_nout) return FZ_ERR_CORRUPT;
   return FZ_OK;
 }
+
+int fz_decompress(fz_ctx *c, const void *d_in, uint64_t in_size, float *d_out,
+                  uint64_t cap_elems, void *stream) {
+  if (!c || !d_in || !d_out) return FZ_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_in) & 15u) || (reinterpret_cast<uintptr_t>(d_out) & 3u))
+    return FZ_ERR_ARG;
+  if (in_size < 64) return FZ_ERR_CORRUPT;
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return FZ_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool timed = c->call_timing;
+  if (timed) cudaEventRecord(c->call_ev[2], s);
+  fz::DecompressArgs a;
+  int grid, A;
+  int st = decompress_begin(c, d_in, in_size, d_out, cap_elems, s, &a, &grid, &A);
+  if (st) return st;
+  prof_begin(c, 3, s);
+  if (fz::launch_decompress(a, grid, s) != cudaSuccess) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  prof_end(c, 3, s);
+  return decompress_end(c, a, grid, A, s, timed);
+}
+
+// host-buffer decompressions of this many output bytes or more are pipelined
+constexpr uint64_t kPipelineBytes = 64ull << 20;
 
 static int grow(void **p, uint64_t *cap, uint64_t need) {
   if (need <= *cap && *p) return FZ_OK;
@@ -961,6 +998,117 @@ int fz_compress_host(fz_ctx *c, const float *h_in, const uint64_t dims[3], int n
   return FZ_OK;
 }
 
+// Streams and events of the pipelined host-buffer decompression, made on
+// first use.
+static int ensure_pipe(fz_ctx *c) {
+  if (c->pipe_in) return FZ_OK;
+  if (cudaStreamCreateWithFlags(&c->pipe_in, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->pipe_out, cudaStreamNonBlocking) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  for (cudaEvent_t &e : c->pipe_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return FZ_ERR_CUDA;
+  if (cudaHostAlloc(reinterpret_cast<void **>(&c->h_slab), 8 * sizeof(uint32_t),
+                    cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->h_slab_dev), c->h_slab, 0) !=
+          cudaSuccess)
+    return FZ_ERR_CUDA;
+  return FZ_OK;
+}
+
+// A version-1 stream decompressed from host memory into host memory in
+// slabs of whole chunk planes (3-D), chunk rows (2-D) or chunks (1-D), whose
+// outputs are contiguous.  Copies in run on one stream (header, flags and
+// outlier records first, then the payload in kPieces pieces), the offsets
+// pass and one decoding launch per slab on the call's stream, each slab's
+// output copied out on a third stream as soon as it is decoded: the stream
+// comes in while earlier slabs' fields go out (the link carries both
+// directions at once), and the kernels hide behind the copies.
+static int decompress_host_pipelined(fz_ctx *c, const uint8_t *h_in, uint64_t in_size,
+                                     const fz_info &info, const Shape &sh, float *h_out,
+                                     cudaStream_t s) {
+  constexpr int kSlabs = 4, kPieces = 8;
+  int st;
+  if ((st = ensure_pipe(c))) return st;
+  const uint64_t n = sh.n_elems;
+  uint8_t *d_in = static_cast<uint8_t *>(c->stage_in);
+  float *d_out = static_cast<float *>(c->stage_out);
+  const uint64_t flags_end = 64 + 32 * sh.n_tiles;
+  const uint64_t pay_end = flags_end + 16 * (uint64_t)info.nnz_blocks;
+  // slabs: "lines" of chunks whose elements are contiguous
+  const int nd = info.ndim;
+  const uint64_t per_line = nd == 3 ? sh.ncx * sh.ncy : nd == 2 ? sh.ncx : 1;
+  const uint64_t lines = sh.n_chunks / per_line;
+  const uint64_t line_elems = nd == 3 ? 8 * sh.d[0] * sh.d[1] : nd == 2 ? 128 * sh.d[0] : 8192;
+  const int K = (int)(lines < (uint64_t)kSlabs ? lines : kSlabs);
+  uint64_t lo[kSlabs + 1];
+  for (int k = 0; k <= K; ++k) lo[k] = lines * k / K * per_line;
+  cudaEvent_t *ev = c->pipe_ev;   // 0 start, 1 header, 2..9 pieces, 10 offsets, 11.. slabs, 23 out
+  cudaStream_t si = c->pipe_in, so = c->pipe_out;
+  if (cudaEventRecord(ev[0], s) != cudaSuccess || cudaStreamWaitEvent(si, ev[0], 0) != cudaSuccess ||
+      cudaStreamWaitEvent(so, ev[0], 0) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  // header and flags, the outlier records, then the payload in pieces
+  if (cudaMemcpyAsync(d_in, h_in, flags_end, cudaMemcpyHostToDevice, si) != cudaSuccess ||
+      (in_size > pay_end && cudaMemcpyAsync(d_in + pay_end, h_in + pay_end, in_size - pay_end,
+                                            cudaMemcpyHostToDevice, si) != cudaSuccess) ||
+      cudaEventRecord(ev[1], si) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  const uint64_t pay = pay_end - flags_end;
+  const uint64_t piece = ((pay + kPieces - 1) / kPieces + 15) / 16 * 16;
+  int pieces = 0;
+  for (uint64_t off = 0; off < pay; off += piece, ++pieces) {
+    const uint64_t nb = pay - off < piece ? pay - off : piece;
+    if (cudaMemcpyAsync(d_in + flags_end + off, h_in + flags_end + off, nb,
+                        cudaMemcpyHostToDevice, si) != cudaSuccess ||
+        cudaEventRecord(ev[2 + pieces], si) != cudaSuccess)
+      return FZ_ERR_CUDA;
+  }
+  // the offsets pass once the flags are in
+  if (cudaStreamWaitEvent(s, ev[1], 0) != cudaSuccess) return FZ_ERR_CUDA;
+  fz::DecompressArgs a;
+  int grid, A;
+  if ((st = decompress_begin(c, d_in, in_size, d_out, n, s, &a, &grid, &A))) return st;
+  // each slab boundary's first payload block, read back through mapped memory
+  fz::GatherIdx gi{};
+  for (int k = 1; k < K; ++k) gi.idx[k - 1] = lo[k];
+  if (K > 1 && (fz::launch_gather_u32(c->out_prefix, gi, K - 1, c->h_slab_dev, s) != cudaSuccess ||
+                cudaEventRecord(ev[10], s) != cudaSuccess ||
+                cudaEventSynchronize(ev[10]) != cudaSuccess)) {
+    mark_all_dirty(c);
+    return FZ_ERR_CUDA;
+  }
+  for (int k = 0; k < K; ++k) {
+    // the payload up to the slab's end (offsets from a corrupt stream are
+    // clamped; the offsets pass has flagged it)
+    uint64_t end_blk = k + 1 < K ? c->h_slab[k] : info.nnz_blocks;
+    if (end_blk > info.nnz_blocks) end_blk = info.nnz_blocks;
+    const uint64_t need = 16 * end_blk;
+    const int last = need == 0 ? -1 : (int)((need - 1) / piece);
+    if (last >= 0 && cudaStreamWaitEvent(s, ev[2 + (last < pieces ? last : pieces - 1)], 0) !=
+                         cudaSuccess)
+      return FZ_ERR_CUDA;
+    a.chunk_lo = lo[k];
+    a.chunk_hi = lo[k + 1];
+    const uint64_t slab_chunks = lo[k + 1] - lo[k];
+    const uint64_t want = (slab_chunks + 3) / 4;                 // a warp per chunk
+    const int g = (int)(want < (uint64_t)grid ? (want ? want : 1) : grid);
+    if (fz::launch_decompress(a, g, s) != cudaSuccess || cudaEventRecord(ev[11 + k], s) != cudaSuccess ||
+        cudaStreamWaitEvent(so, ev[11 + k], 0) != cudaSuccess) {
+      mark_all_dirty(c);
+      return FZ_ERR_CUDA;
+    }
+    const uint64_t e0 = lo[k] / per_line * line_elems;
+    uint64_t e1 = lo[k + 1] / per_line * line_elems;
+    if (e1 > n) e1 = n;
+    if (e1 > e0 && cudaMemcpyAsync(h_out + e0, d_out + e0, 4 * (e1 - e0), cudaMemcpyDeviceToHost,
+                                   so) != cudaSuccess)
+      return FZ_ERR_CUDA;
+  }
+  if (cudaEventRecord(ev[23], so) != cudaSuccess || cudaStreamWaitEvent(s, ev[23], 0) != cudaSuccess)
+    return FZ_ERR_CUDA;
+  return decompress_end(c, a, grid, A, s, false);
+}
+
 int fz_decompress_host(fz_ctx *c, const void *h_in, uint64_t in_size, float *h_out,
                        uint64_t cap_elems, void *stream) {
   if (!c || !h_in || !h_out) return FZ_ERR_ARG;
@@ -975,6 +1123,11 @@ int fz_decompress_host(fz_ctx *c, const void *h_in, uint64_t in_size, float *h_o
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if ((st = grow(&c->stage_in, &c->stage_in_cap, in_size))) return st;
   if ((st = grow(&c->stage_out, &c->stage_out_cap, n * 4))) return st;
+  Shape sh;
+  if (info.version == 1 && !info.wide && make_shape(info.dims, info.ndim, &sh) &&
+      n * 4 >= kPipelineBytes)
+    return decompress_host_pipelined(c, static_cast<const uint8_t *>(h_in), in_size, info, sh,
+                                     h_out, s);
   if (cudaMemcpyAsync(c->stage_in, h_in, in_size, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return FZ_ERR_CUDA;
   st = fz_decompress(c, c->stage_in, in_size, static_cast<float *>(c->stage_out), n, stream);

@@ -465,14 +465,16 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
   // chunks are dealt out statically: their payload offsets come from the
   // offsets pass, so no chunk waits for another
   const uint64_t n_warps = (uint64_t)gridDim.x * kDecWarps;
-  uint64_t c = (uint64_t)blockIdx.x * kDecWarps + (threadIdx.x >> 5);
+  // the chunks this launch decompresses: [chunk_lo, chunk_hi), chunk_hi 0 for all
+  auto live = [&](uint64_t cc) { return cc < h.n_chunks && (a.chunk_hi == 0 || cc < a.chunk_hi); };
+  uint64_t c = a.chunk_lo + (uint64_t)blockIdx.x * kDecWarps + (threadIdx.x >> 5);
   bool oob = false;
   uint32_t matched = 0, bad = 0;
 
   auto load_plan = [&](uint64_t cc) {
     uint32_t fw = 0;
     uint64_t base = 0;
-    if (cc < h.n_chunks) {
+    if (live(cc)) {
       fw = __ldg(reinterpret_cast<const uint32_t *>(flags + 128 * cc) + g);
       base = __ldg(a.chunk_off + cc);
     }
@@ -483,16 +485,16 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
   uint32_t cur_narrow = cp.narrow;   // the current chunk's narrow tiles
 #pragma unroll
   for (int t = 0; t < kTilesPerChunk; ++t) {
-    if (c < h.n_chunks) oob |= gather_tile(payload, h.nnz, pbuf + 1024 * t, plane_flags(cp.fw, t, g),
+    if (live(c)) oob |= gather_tile(payload, h.nnz, pbuf + 1024 * t, plane_flags(cp.fw, t, g),
                                            tile_rank(cp, t), g);
     else cp_async_commit();
   }
-  while (c < h.n_chunks) {
+  while (live(c)) {
     const uint64_t cn = c + n_warps;
     // next chunk's flags and offset: in flight while tile 0 is decoded
     uint32_t fw_n = 0;
     uint64_t base_n = 0;
-    if (cn < h.n_chunks) {
+    if (live(cn)) {
       fw_n = __ldg(reinterpret_cast<const uint32_t *>(flags + 128 * cn) + g);
       base_n = __ldg(a.chunk_off + cn);
     }
@@ -564,7 +566,7 @@ __device__ void decompress_chunks(const DecompressArgs &a, const Hdr &h, uint32_
       }
       __syncwarp();                      // the buffer is free: refill it for the next chunk
       if (t == 0) np = plan_chunk(fw_n, base_n, g);
-      if (cn < h.n_chunks)
+      if (live(cn))
         oob |= gather_tile(payload, h.nnz, pb, plane_flags(np.fw, t, g), tile_rank(np, t), g);
       else
         cp_async_commit();
@@ -869,6 +871,17 @@ __global__ void __launch_bounds__(32) copy_result_kernel(const SetScratch *src, 
   if (threadIdx.x < kWords)
     reinterpret_cast<uint32_t *>(dst)[threadIdx.x] =
         reinterpret_cast<const uint32_t *>(src)[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(32) gather_u32_kernel(const uint32_t *src, GatherIdx idx, int n,
+                                                        uint32_t *dst) {
+  if ((int)threadIdx.x < n) dst[threadIdx.x] = src[idx.idx[threadIdx.x]];
+}
+
+cudaError_t launch_gather_u32(const uint32_t *src, GatherIdx idx, int n, uint32_t *dst,
+                              cudaStream_t s) {
+  gather_u32_kernel<<<1, 32, 0, s>>>(src, idx, n < 8 ? n : 8, dst);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_copy_result(const SetScratch *src, SetScratch *dst, cudaStream_t s) {

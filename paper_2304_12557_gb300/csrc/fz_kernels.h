@@ -75,6 +75,9 @@ struct DecompressArgs {
                                // kernels that convert q as integers
   int32_t *face[3];
   const int32_t *corr[3];
+  // decompress only the chunks [chunk_lo, chunk_hi) (chunk_hi 0: to the
+  // last chunk); the offsets pass always covers the whole stream
+  uint64_t chunk_lo, chunk_hi;
 };
 
 // Version-2 decompression, between phases 1 and 2: the cross-chunk sums of
@@ -123,6 +126,12 @@ cudaError_t launch_decompress(const DecompressArgs &a, int grid, cudaStream_t s)
 // one warp copies a 64-byte result block to (mapped host) memory, after the
 // kernel before it on the stream (programmatic dependent launch)
 cudaError_t launch_copy_result(const SetScratch *src, SetScratch *dst, cudaStream_t s);
+// dst[i] = src[idx[i]] for i < n <= 8 (one warp; dst may be mapped host memory)
+struct GatherIdx {
+  uint64_t idx[8];
+};
+cudaError_t launch_gather_u32(const uint32_t *src, GatherIdx idx, int n, uint32_t *dst,
+                              cudaStream_t s);
 uint64_t decompress_status_words(uint64_t n_chunks);
 
 // the unfused compression path (fz_staged.cu): intermediate data in HBM

@@ -316,6 +316,62 @@ def test_host_buffer_calls(codec, torch):
     np.testing.assert_array_equal(y.ravel().view(np.uint32), xr.view(np.uint32))
 
 
+def _host_pipeline_cases():
+    rng = np.random.default_rng(77)
+    out = []
+    # 3-D: 256^3 floats (64 MiB of output): four slabs of chunk planes
+    out.append(("grf3d_256", fields.grf((256, 256, 256), -3.0, 71).astype(np.float32), 3,
+                fz.EB_REL, 1e-3))
+    # 3-D with a ragged last chunk plane and escapes in every slab
+    x = fields.grf((261, 250, 260), -2.5, 72).astype(np.float32)
+    x.reshape(-1)[rng.integers(0, x.size, 4000)] = 5e4
+    out.append(("grf3d_ragged_escapes", x, 3, fz.EB_ABS, 1e-2))
+    # 2-D: chunk rows of 128 rows, the last one ragged
+    out.append(("grf2d_4100x4099", fields.grf((4100, 4099), -3.0, 73).astype(np.float32), 2,
+                fz.EB_REL, 1e-4))
+    # 1-D: chunks of 8192 values, the last one ragged
+    out.append(("noise1d", (np.cumsum(rng.standard_normal((1 << 24) + 4321)) * 1e-2)
+                .astype(np.float32), 1, fz.EB_REL, 1e-3))
+    return out
+
+
+@pytest.mark.parametrize("case", range(4))
+def test_host_buffer_decompression_in_slabs(codec, torch, case):
+    # fields of 64 MiB or more: the host-buffer decompression copies the
+    # stream in and the field out in slabs, overlapped with the decoding
+    name, x, nd, mode, eb = _host_pipeline_cases()[case]
+    assert 4 * x.size >= 64 << 20, name
+    st, ostream = oracle.compress(x, nd, mode, eb, all_cores=True)
+    assert st == oracle.OK
+    s = codec.compress_host(x, mode="rel" if mode == fz.EB_REL else "abs", eb=eb, ndim=nd)
+    assert s.tobytes() == ostream, name
+    y = codec.decompress_host(s)
+    _, xr = oracle.decompress(ostream, all_cores=True)
+    np.testing.assert_array_equal(y.ravel().view(np.uint32), xr.view(np.uint32), err_msg=name)
+    # the device-buffer call and the host-buffer call alternate on one context
+    ys = codec.decompress(torch.from_numpy(np.frombuffer(ostream, np.uint8).copy()).cuda())
+    assert torch.equal(ys.reshape(-1).cpu(), torch.from_numpy(xr)), name
+    y2 = codec.decompress_host(s)
+    np.testing.assert_array_equal(y2.ravel().view(np.uint32), xr.view(np.uint32), err_msg=name)
+
+
+def test_host_buffer_decompression_in_slabs_corrupt(codec, torch):
+    x = fields.grf((256, 256, 256), -3.0, 74).astype(np.float32)
+    s = codec.compress_host(x, mode="rel", eb=1e-3).copy()
+    # a flag byte of the second slab set where its block was zero: the
+    # offsets no longer add up to the header's block count
+    flags = s[64:64 + 32 * (x.size // 2048)]
+    zero = np.flatnonzero(flags[flags.size // 2:] != 0xFF)[0] + flags.size // 2
+    s[64 + zero] |= (~s[64 + zero]) & 0xFF
+    with pytest.raises(fz.FZError) as e:
+        codec.decompress_host(s)
+    assert e.value.status == fz.ERR_CORRUPT
+    y = codec.decompress_host(codec.compress_host(x, mode="rel", eb=1e-3))
+    _, ostream = oracle.compress(x, 3, fz.EB_REL, 1e-3, all_cores=True)
+    _, xr = oracle.decompress(ostream, all_cores=True)
+    np.testing.assert_array_equal(y.ravel().view(np.uint32), xr.view(np.uint32))
+
+
 # ------------------------------------------------------------ wide quantiser
 def _wide_cases():
     rng = np.random.default_rng(91)
