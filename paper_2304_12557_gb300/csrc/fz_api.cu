@@ -896,6 +896,8 @@ static int decompress_begin(fz_ctx *c, const void *d_in, uint64_t in_size, float
   a.wait_limit_ns = c->wait_limit_ns;
   a.skip_publish_chunk = c->skip_publish;
   a.accept_whole = 1;
+  a.chunk_lo = 0;
+  a.chunk_hi = 0;                                  // every chunk
   prof_reset(c);
   prof_begin(c, 4, s);
   if (fz::launch_dec_offsets(a, bound, c->num_sms, s) != cudaSuccess) {

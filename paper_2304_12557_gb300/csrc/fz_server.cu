@@ -410,6 +410,8 @@ bool step(fz_server *S) {
     a.wait_limit_ns = 2000000000ull;
     a.skip_publish_chunk = ~0ull;
     a.wide = r.wide ? 1 : 0;
+    a.chunk_lo = 0;
+    a.chunk_hi = 0;                                // every chunk
     cudaStreamWaitEvent(S->s_dec, S->ev_uploads, 0);
     cudaEventRecord(r.ev_start, S->s_dec);
     cudaMemsetAsync(scr, 0, 2 * sizeof(fz::SetScratch) + units * fz::kStatusStride * 8, S->s_dec);
