@@ -355,6 +355,34 @@ def test_host_buffer_decompression_in_slabs(codec, torch, case):
     np.testing.assert_array_equal(y2.ravel().view(np.uint32), xr.view(np.uint32), err_msg=name)
 
 
+@pytest.mark.parametrize("case", ["grf3d", "escapes2d", "narrow_cap"])
+def test_host_buffer_compression_into_pinned_memory(codec, torch, case):
+    # a pinned output buffer, as the end-to-end measurement uses, and one too
+    # small for the stream
+    rng = np.random.default_rng(81)
+    if case == "grf3d":
+        x, nd, mode, eb = fields.grf((96, 128, 160), -3.0, 82).astype(np.float32), 3, "rel", 1e-3
+    else:
+        x = fields.grf((700, 900), -2.5, 83).astype(np.float32)
+        x.reshape(-1)[rng.integers(0, x.size, 3000)] = 4e4
+        nd, mode, eb = 2, "abs", 1e-2
+    st, ostream = oracle.compress(x, nd, fz.EB_REL if mode == "rel" else fz.EB_ABS, eb)
+    assert st == oracle.OK
+    cap = len(ostream) + 4096 if case != "narrow_cap" else len(ostream) - 1
+    pinned = torch.empty(cap, dtype=torch.uint8, pin_memory=True)
+    out = pinned.numpy()
+    if case == "narrow_cap":
+        with pytest.raises(fz.FZError) as e:
+            codec.compress_host(x, mode=mode, eb=eb, ndim=nd, out=out)
+        assert e.value.status == fz.ERR_CAPACITY
+        return
+    s = codec.compress_host(x, mode=mode, eb=eb, ndim=nd, out=out)
+    assert s.tobytes() == ostream, case
+    y = codec.decompress_host(s)
+    _, xr = oracle.decompress(ostream)
+    np.testing.assert_array_equal(y.ravel().view(np.uint32), xr.view(np.uint32))
+
+
 def test_host_buffer_decompression_in_slabs_corrupt(codec, torch):
     x = fields.grf((256, 256, 256), -3.0, 74).astype(np.float32)
     s = codec.compress_host(x, mode="rel", eb=1e-3).copy()
