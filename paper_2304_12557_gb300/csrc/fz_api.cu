@@ -1108,6 +1108,8 @@ static int decompress_host_pipelined(fz_ctx *c, const uint8_t *h_in, uint64_t in
   }
   if (cudaEventRecord(ev[23], so) != cudaSuccess || cudaStreamWaitEvent(s, ev[23], 0) != cudaSuccess)
     return FZ_ERR_CUDA;
+  a.chunk_lo = 0;                                    // any further pass covers every chunk
+  a.chunk_hi = 0;
   return decompress_end(c, a, grid, A, s, false);
 }
 
