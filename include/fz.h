@@ -331,22 +331,27 @@ int fz_batch_compress(fz_batch *batch, uint64_t *out_sizes, int *statuses, void 
 /* Capture runs in a CUDA graph (default on) or launch them directly. */
 int fz_batch_set_graph(fz_batch *batch, int on);
 
-/* Autotune the batch's load path over three choices, `reps` timed runs
+/* Autotune the batch's load path over four choices, `reps` timed runs
  * each: [0] direct loads for every field; [1] TMA tile loads for the
  * fields whose rows allow them (2-D/3-D, rows 16-byte aligned), direct
  * loads for the others (the default); [2] TMA tile loads for every 2-D/3-D
  * field, the others through staging copies with the row pitch padded to 4
  * elements, written by each run's first pass (about 4 bytes of device
- * memory per element of those fields).  Keeps the fastest.
+ * memory per element of those fields); [3] TMA for every 2-D/3-D field of
+ * four rows or more, the unaligned ones by four row-class boxes per tile
+ * (rows grouped by index mod 4 share a 16-byte offset and form a tensor of
+ * their own), read in place.  Keeps the fastest.
  * The outputs are overwritten by the trial runs.  fz_batch_tuning reports
- * the choice (tma_on, staged) and the median run times in ms (0 before
- * tuning). */
+ * the choice (tma 0/1/2, staged) and the median run times in ms of the four
+ * paths (0 before tuning). */
 int fz_batch_autotune(fz_batch *batch, int reps, void *stream);
 /* Set the load path by hand: tma 0 (direct loads), 1 (TMA for aligned
- * rows); staged 1 with tma 1 (TMA for every 2-D/3-D field).  Allocates the
- * staging copies when first needed.  FZ_OK, FZ_ERR_ARG or FZ_ERR_CUDA. */
+ * rows), 2 (TMA for aligned rows, row-class boxes for the others); staged 1
+ * with tma 1 (TMA for every 2-D/3-D field through staging copies).
+ * Allocates the staging copies when first needed.  FZ_OK, FZ_ERR_ARG or
+ * FZ_ERR_CUDA. */
 int fz_batch_set_load_path(fz_batch *batch, int tma, int staged);
-int fz_batch_tuning(const fz_batch *batch, int *tma_on, int *staged, double ms[3]);
+int fz_batch_tuning(const fz_batch *batch, int *tma, int *staged, double ms[4]);
 
 /* ---------------------------------------------------------------------
  * A request server with continuous batching.  Clients submit compress and

@@ -320,21 +320,24 @@ class Batch:
             raise FZError(st, "fz_batch_autotune")
         return self.tuning()
 
-    def set_load_path(self, tma: bool, staged: bool):
-        st = self._L.fz_batch_set_load_path(self._h, int(bool(tma)), int(bool(staged)))
+    def set_load_path(self, tma, staged: bool):
+        """tma 0/False: direct loads; 1/True: TMA for aligned rows; 2: also
+        row-class TMA boxes for the other 2-D/3-D fields."""
+        st = self._L.fz_batch_set_load_path(self._h, int(tma), int(bool(staged)))
         if st != OK:
             raise FZError(st, "fz_batch_set_load_path")
 
     def tuning(self):
-        """The load path in use (tma, staged) and the tuning runs' median
-        times: direct loads, TMA for aligned rows, TMA with staging copies."""
+        """The load path in use (tma 0/1/2, staged) and the tuning runs'
+        median times: direct loads, TMA for aligned rows, TMA with staging
+        copies, TMA with row-class boxes."""
         on, staged = ctypes.c_int(), ctypes.c_int()
-        ms = (ctypes.c_double * 3)()
+        ms = (ctypes.c_double * 4)()
         st = self._L.fz_batch_tuning(self._h, ctypes.byref(on), ctypes.byref(staged), ms)
         if st != OK:
             raise FZError(st, "fz_batch_tuning")
-        return {"tma": bool(on.value), "staged": bool(staged.value), "ms_direct": ms[0],
-                "ms_tma": ms[1], "ms_tma_staged": ms[2]}
+        return {"tma": on.value, "staged": bool(staged.value), "ms_direct": ms[0],
+                "ms_tma": ms[1], "ms_tma_staged": ms[2], "ms_tma_classes": ms[3]}
 
     def close(self):
         if self._h:

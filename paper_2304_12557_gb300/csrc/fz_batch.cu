@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "fz.h"
@@ -58,6 +59,7 @@ constexpr int kRangeSegElems = 1 << 16;   // 256 KiB per segment
 
 __global__ void __launch_bounds__(256) range_batch_kernel(const RangeSeg *segs, uint64_t n_segs,
                                                           RangeSlots *slots) {
+  grid_launch_dependents();              // the preparation may be scheduled now
   for (uint64_t sgi = blockIdx.x; sgi < n_segs; sgi += gridDim.x) {
     const RangeSeg sg = segs[sgi];
     if (!sg.range && !sg.dst) continue;              // the same in the whole block
@@ -127,6 +129,8 @@ __global__ void __launch_bounds__(256) range_batch_kernel(const RangeSeg *segs, 
 // same derivation and quantiser check as a single field's launch.
 __global__ void prepare_kernel(const CompressArgs *fields, RangeResult *ranges,
                                const RangeSlots *slots, FieldRt *rt, uint32_t n) {
+  grid_dependency_wait();                // the first pass's ranges
+  grid_launch_dependents();              // the compression may be scheduled now
   const uint32_t f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= n) return;
   const CompressArgs &a = fields[f];
@@ -181,9 +185,23 @@ __device__ __forceinline__ void batch_tile_outliers(const CompressArgs &a, const
 // Escapes of every field of a batch: a warp reads 32 tiles' outlier counts
 // at once (the batch's counts are contiguous, fields in order) and works
 // only on the tiles that recorded some.
+// The run's result blocks (the fields' and the launch-level one) into
+// mapped pinned memory, once the escapes pass has finished.
+__global__ void __launch_bounds__(128) copy_results_kernel(const SetScratch *src, SetScratch *dst,
+                                                           uint64_t count) {
+  grid_dependency_wait();
+  const uint64_t words = count * (sizeof(SetScratch) / 4);
+  const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+  uint32_t *d = reinterpret_cast<uint32_t *>(dst);
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
 __global__ void __launch_bounds__(128) outlier_batch_kernel(BatchArgs b, const uint64_t *tile_off,
                                                             uint32_t n_fields, uint64_t n_tiles,
                                                             const uint32_t *counts) {
+  grid_dependency_wait();                // the compressions' per-tile counts
   const int g = threadIdx.x & 31;
   const uint64_t n_warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t base = 32 * (blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5));
@@ -237,6 +255,25 @@ bool shape_of(const uint64_t dims[3], int ndim, uint64_t *n_chunks, uint32_t *nc
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// A launch that may begin while the kernel before it on the stream drains
+// (programmatic dependent launch); each of the run's kernels waits for the
+// previous one's results before it reads them.
+template <class... P, class... A>
+cudaError_t pdl_launch(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       A &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
 // a0 carries only the launch-level error block and the wait limit.  CHECK:
 // some field of the class needs the per-element quantiser check (absolute
 // bounds, or a relative bound against a supplied range).
@@ -246,8 +283,7 @@ cudaError_t launch_batch_compress(const CompressArgs &a0, const BatchArgs &b, in
   auto k = compress_kernel<NDIM, 1, CHECK, NDIM >= 2, true>;
   CUtensorMap none;
   std::memset(&none, 0, sizeof(none));
-  k<<<sms, kCompThreads, kCompSmemBatch, s>>>(a0, none, b);
-  return cudaGetLastError();
+  return pdl_launch(k, dim3(sms), dim3(kCompThreads), kCompSmemBatch, s, a0, none, b);
 }
 
 bool tma_eligible(const fz_field &h) {
@@ -380,6 +416,7 @@ int BatchWs::set(int device, const fz_field *fields, int n, cudaStream_t s) {
   };
   const size_t o_args = take(n * sizeof(CompressArgs), 64);
   const size_t o_tmaps = take(n * sizeof(CUtensorMap), 128);
+  const size_t o_cmaps = take(4 * n * sizeof(CUtensorMap), 128);
   const size_t o_map = take(std::max<uint64_t>(total_units, 1) * sizeof(uint2), 64);
   const size_t o_segs = take(std::max<size_t>(segs.size(), 1) * sizeof(RangeSeg), 64);
   const size_t o_toff = take(n * sizeof(uint64_t), 64);
@@ -414,13 +451,17 @@ int BatchWs::set(int device, const fz_field *fields, int n, cudaStream_t s) {
     if (h_res_) cudaFreeHost(h_res_);
     h_res_ = nullptr;
     res_cap_ = 0;
-    if (cudaMallocHost(&h_res_, (n + 1) * 2 * sizeof(SetScratch)) != cudaSuccess)
+    if (cudaHostAlloc(reinterpret_cast<void **>(&h_res_), (n + 1) * 2 * sizeof(SetScratch),
+                      cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void **>(&h_res_dev_), h_res_, 0) !=
+            cudaSuccess)
       return FZ_ERR_CUDA;
     res_cap_ = (uint32_t)(n + 1) * 2;
   }
   uint8_t *m = static_cast<uint8_t *>(d_mem_);
   d_args_ = reinterpret_cast<CompressArgs *>(m + o_args);
   d_tmaps_ = reinterpret_cast<CUtensorMap *>(m + o_tmaps);
+  d_cmaps_ = reinterpret_cast<CUtensorMap *>(m + o_cmaps);
   d_unit_map_ = reinterpret_cast<uint2 *>(m + o_map);
   d_segs_ = reinterpret_cast<RangeSeg *>(m + o_segs);
   d_tile_off_ = reinterpret_cast<uint64_t *>(m + o_toff);
@@ -474,7 +515,9 @@ int BatchWs::upload(cudaStream_t s) {
   const size_t o_args = reinterpret_cast<uint8_t *>(d_args_) - static_cast<uint8_t *>(d_mem_);
   const size_t o_tmaps = reinterpret_cast<uint8_t *>(d_tmaps_) - static_cast<uint8_t *>(d_mem_);
   CUtensorMap *maps = reinterpret_cast<CUtensorMap *>(hs + o_tmaps);
-  const bool staged = tma_on_ && stage_on_ && stage_floats_ > 0;
+  const size_t o_cmaps = reinterpret_cast<uint8_t *>(d_cmaps_) - static_cast<uint8_t *>(d_mem_);
+  CUtensorMap *cmaps = reinterpret_cast<CUtensorMap *>(hs + o_cmaps);
+  const bool staged = tma_mode_ == 1 && stage_on_ && stage_floats_ > 0;
   if (staged && stage_mem_ < stage_floats_ * 4) {
     if (d_stage_) cudaFree(d_stage_);
     d_stage_ = nullptr;
@@ -485,6 +528,7 @@ int BatchWs::upload(cudaStream_t s) {
   for (uint32_t f = 0; f < n_; ++f) {
     CompressArgs &a = args_[f];
     std::memset(&maps[f], 0, sizeof(CUtensorMap));
+    std::memset(&cmaps[4 * f], 0, 4 * sizeof(CUtensorMap));
     a.x = host_[f].d_in;
     a.pitch = a.dims[0];
     a.use_tma = 0;
@@ -493,9 +537,12 @@ int BatchWs::upload(cudaStream_t s) {
       a.pitch = (a.dims[0] + 3) / 4 * 4;
       if (!encode_field_tmap_pitch(a.ndim, a.dims, a.pitch, a.x, &maps[f])) return FZ_ERR_CUDA;
       a.use_tma = 1;
-    } else if (tma_on_ && tma_eligible(host_[f]) &&
+    } else if (tma_mode_ >= 1 && tma_eligible(host_[f]) &&
                encode_field_tmap(a.ndim, a.dims, a.x, &maps[f])) {
       a.use_tma = 1;
+    } else if (tma_mode_ == 2 && a.ndim >= 2 &&
+               encode_class_tmaps(a.ndim, a.dims, a.pitch, a.x, &cmaps[4 * f])) {
+      a.use_tma = 2;
     }
   }
   for (RangeSeg &sg : segs_)
@@ -507,8 +554,8 @@ int BatchWs::upload(cudaStream_t s) {
   return FZ_OK;
 }
 
-int BatchWs::set_load_path(bool tma, bool staged, cudaStream_t s) {
-  tma_on_ = tma;
+int BatchWs::set_load_path(int tma, bool staged, cudaStream_t s) {
+  tma_mode_ = tma;
   stage_on_ = staged;
   return n_ ? upload(s) : FZ_OK;
 }
@@ -521,14 +568,17 @@ int BatchWs::enqueue(cudaStream_t s) {
     const unsigned blocks = (unsigned)std::min<uint64_t>(n_segs_, (uint64_t)num_sms_ * 8);
     range_batch_kernel<<<blocks, 256, 0, s>>>(d_segs_, n_segs_, d_slots_);
   }
-  prepare_kernel<<<(n_ + 127) / 128, 128, 0, s>>>(d_args_, d_ranges_, d_slots_, d_rt_, n_);
-  if (cudaGetLastError() != cudaSuccess) return FZ_ERR_CUDA;
+  if (pdl_launch(prepare_kernel, dim3((n_ + 127) / 128), dim3(128), 0, s,
+                 static_cast<const CompressArgs *>(d_args_), d_ranges_,
+                 static_cast<const RangeSlots *>(d_slots_), d_rt_, n_) != cudaSuccess)
+    return FZ_ERR_CUDA;
   int ci = 0;
   for (const WsClass &c : cls_) {
     BatchArgs b{};
     b.fields = d_args_;
     b.rt = d_rt_;
     b.tmaps = d_tmaps_;
+    b.cmaps = d_cmaps_;
     b.unit_map = d_unit_map_ + c.unit_off;
     b.n_units = c.n_units;
     b.ticket = d_tickets_ + ci++;
@@ -553,13 +603,18 @@ int BatchWs::enqueue(cudaStream_t s) {
     const uint64_t warps = (total_tiles_ + 31) / 32;
     const unsigned blocks =
         (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 3) / 4, num_sms_ * 8ull));
-    outlier_batch_kernel<<<blocks, 128, 0, s>>>(b, d_tile_off_, n_, total_tiles_,
-                                                 d_tile_out_ + total_tiles_);
-    if (cudaGetLastError() != cudaSuccess) return FZ_ERR_CUDA;
+    if (pdl_launch(outlier_batch_kernel, dim3(blocks), dim3(128), 0, s, b,
+                   static_cast<const uint64_t *>(d_tile_off_), n_, total_tiles_,
+                   static_cast<const uint32_t *>(d_tile_out_ + total_tiles_)) != cudaSuccess)
+      return FZ_ERR_CUDA;
   }
   // the fields' result blocks and the launch-level one behind them
-  if (cudaMemcpyAsync(h_res_, d_sets_, (n_ + 1) * sizeof(SetScratch), cudaMemcpyDeviceToHost,
-                      s) != cudaSuccess)
+  // the fields' result blocks and the launch-level one, written into the
+  // mapped pinned copy by a kernel behind the escapes pass (a device-to-host
+  // copy at the end of the run would add a few microseconds)
+  if (pdl_launch(copy_results_kernel, dim3((unsigned)std::min<uint64_t>((n_ + 7) / 8, 1024)),
+                 dim3(128), 0, s, static_cast<const SetScratch *>(d_sets_), h_res_dev_,
+                 (uint64_t)n_ + 1) != cudaSuccess)
     return FZ_ERR_CUDA;
   return FZ_OK;
 }
@@ -605,7 +660,8 @@ struct fz_batch {
   fz::BatchWs ws;
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
-  double tune_ms[3] = {0, 0, 0};    // [direct, TMA, TMA + staging] when tuned
+  // [direct, TMA where aligned, TMA + staging, TMA + row classes] when tuned
+  double tune_ms[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -642,7 +698,7 @@ int fz_batch_create(fz_ctx *ctx, const fz_field *fields, int n, fz_batch **out) 
   if (!B) return FZ_ERR_CUDA;
   B->ctx = ctx;
   B->device = device;
-  B->ws.set_load_path(true, false, nullptr);        // flags only: no fields yet
+  B->ws.set_load_path(1, false, nullptr);           // flags only: no fields yet
   int st = B->ws.set(device, fields, n, nullptr);
   if (st == FZ_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = FZ_ERR_CUDA;
   if (st != FZ_OK) {
@@ -713,11 +769,13 @@ int fz_batch_autotune(fz_batch *B, int reps, void *stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the load paths: direct loads everywhere; TMA boxes for the fields with
   // 16-byte aligned rows; TMA boxes for every 2-D/3-D field, through
-  // staging copies of the others
-  const bool tma[3] = {false, true, true}, staged[3] = {false, false, true};
+  // staging copies of the others; one box per tile for the aligned fields
+  // and four row-class boxes for the others
+  const int tma[4] = {0, 1, 1, 2};
+  const bool staged[4] = {false, false, true, false};
   double best = 0.0;
-  int best_c = 2;
-  for (int c = 0; c < 3; ++c) {
+  int best_c = 3;
+  for (int c = 0; c < 4; ++c) {
     drop_graph(B);
     if (B->ws.set_load_path(tma[c], staged[c], s) != FZ_OK ||
         cudaStreamSynchronize(s) != cudaSuccess)
@@ -746,21 +804,22 @@ int fz_batch_autotune(fz_batch *B, int reps, void *stream) {
 }
 
 int fz_batch_set_load_path(fz_batch *B, int tma, int staged) {
-  if (!B || (tma != 0 && tma != 1) || (staged != 0 && staged != 1)) return FZ_ERR_ARG;
+  if (!B || tma < 0 || tma > 2 || (staged != 0 && staged != 1) || (staged && tma != 1))
+    return FZ_ERR_ARG;
   DeviceScope scope(B->device);
   if (!scope.ok) return FZ_ERR_CUDA;
   drop_graph(B);
-  if (B->ws.set_load_path(tma == 1, staged == 1, nullptr) != FZ_OK ||
+  if (B->ws.set_load_path(tma, staged == 1, nullptr) != FZ_OK ||
       cudaStreamSynchronize(nullptr) != cudaSuccess)
     return FZ_ERR_CUDA;
   return FZ_OK;
 }
 
-int fz_batch_tuning(const fz_batch *B, int *tma_on, int *staged, double ms[3]) {
-  if (!B || !tma_on || !staged || !ms) return FZ_ERR_ARG;
-  *tma_on = B->ws.tma_on() ? 1 : 0;
+int fz_batch_tuning(const fz_batch *B, int *tma, int *staged, double ms[4]) {
+  if (!B || !tma || !staged || !ms) return FZ_ERR_ARG;
+  *tma = B->ws.tma_mode();
   *staged = B->ws.staged_on() ? 1 : 0;
-  for (int c = 0; c < 3; ++c) ms[c] = B->tune_ms[c];
+  for (int c = 0; c < 4; ++c) ms[c] = B->tune_ms[c];
   return FZ_OK;
 }
 

@@ -66,15 +66,17 @@ class BatchWs {
   // ctx (may be NULL) classifies absolute-bound failures as NaN/Inf or range.
   int collect(fz_ctx *ctx, uint64_t *sizes, int *statuses, cudaStream_t s) const;
   // Re-encode the tensor maps for a new load-path choice (idle workspace):
-  // tma, TMA boxes for fields whose rows are 16-byte aligned; staged (with
-  // tma), also for the others, through a staging copy with a padded row
-  // pitch that the first pass writes (device memory grown as needed).
-  int set_load_path(bool tma, bool staged, cudaStream_t s);
+  // tma 1, TMA boxes for fields whose rows are 16-byte aligned; tma 2, also
+  // the row-class boxes for the other 2-D/3-D fields (four maps each, see
+  // issue_class_boxes); staged (with tma 1), TMA boxes for the others
+  // through a staging copy with a padded row pitch that the first pass
+  // writes (device memory grown as needed).
+  int set_load_path(int tma, bool staged, cudaStream_t s);
   void release();
 
   uint32_t size() const { return n_; }
-  bool tma_on() const { return tma_on_; }
-  bool staged_on() const { return tma_on_ && stage_on_; }
+  int tma_mode() const { return tma_mode_; }
+  bool staged_on() const { return tma_mode_ == 1 && stage_on_; }
   uint64_t wait_limit_ns = 2000000000ull;
 
  private:
@@ -82,7 +84,7 @@ class BatchWs {
 
   int device_ = 0;
   int num_sms_ = 1;
-  bool tma_on_ = true;
+  int tma_mode_ = 1;
   bool stage_on_ = false;
   // per field: its offset (floats) in the staging memory, or ~0 when its
   // rows are read in place; the first pass's segments (host copy)
@@ -105,6 +107,7 @@ class BatchWs {
   size_t zero_off_ = 0, zero_bytes_ = 0;
   CompressArgs *d_args_ = nullptr;
   CUtensorMap *d_tmaps_ = nullptr;
+  CUtensorMap *d_cmaps_ = nullptr;   // 4 per field: the row-class maps
   uint2 *d_unit_map_ = nullptr;
   RangeSeg *d_segs_ = nullptr;
   uint64_t *d_tile_off_ = nullptr;
@@ -117,7 +120,8 @@ class BatchWs {
   // pinned host memory: the descriptor image and the result blocks
   void *h_stage_ = nullptr;
   size_t stage_cap_ = 0;
-  SetScratch *h_res_ = nullptr;
+  SetScratch *h_res_ = nullptr;     // pinned, mapped
+  SetScratch *h_res_dev_ = nullptr; // h_res_ as the device addresses it
   uint32_t res_cap_ = 0;
 };
 

@@ -202,8 +202,7 @@ bool encode_field_tmap(int ndim, const uint64_t dims[3], const float *x, CUtenso
   return encode_field_tmap_pitch(ndim, dims, dims[0], x, tm);
 }
 
-bool encode_field_tmap_pitch(int ndim, const uint64_t dims[3], uint64_t pitch, const float *x,
-                             CUtensorMap *tm) {
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = [] {
     void *f = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -213,6 +212,42 @@ bool encode_field_tmap_pitch(int ndim, const uint64_t dims[3], uint64_t pitch, c
       f = nullptr;
     return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
   }();
+  return enc;
+}
+
+// Class k holds the rows R = 4 j + k (R = y + Y z).  Its rows start at
+// x + 4 (R pitch) bytes, all at the same offset r_k = ((x / 4) + k pitch) mod
+// 4 floats past a 16-byte boundary; the map starts at that boundary (r_k
+// floats before row k, inside the field's allocation, which is at least
+// 16-byte aligned), takes X + r_k floats per row and the class's rows 16
+// pitch bytes apart, so that it covers exactly the class's rows and nothing
+// past the field's last element.
+bool encode_class_tmaps(int ndim, const uint64_t dims[3], uint64_t pitch, const float *x,
+                        CUtensorMap tm[4]) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+  if (!enc || ndim < 2) return false;
+  const uint64_t rows = ndim == 3 ? dims[1] * dims[2] : dims[1];
+  const uintptr_t xa = reinterpret_cast<uintptr_t>(x);
+  if (rows < 4 || (xa & 3u) || pitch < dims[0]) return false;
+  for (int k = 0; k < 4; ++k) {
+    const uintptr_t start = xa + 4 * (uintptr_t)k * pitch;
+    const uint64_t rk = (start >> 2) & 3u;
+    cuuint64_t gdim[2] = {dims[0] + rk, (rows - (uint64_t)k + 3) / 4};
+    cuuint64_t gstr[1] = {16 * pitch};
+    cuuint32_t box[2] = {(cuuint32_t)(ndim == 3 ? kClassRow3 : kClassRow2), 8};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&tm[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                           reinterpret_cast<void *>(start - 4 * rk), gdim, gstr, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+  }
+  return true;
+}
+
+bool encode_field_tmap_pitch(int ndim, const uint64_t dims[3], uint64_t pitch, const float *x,
+                             CUtensorMap *tm) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
   if (!enc || ndim < 2) return false;
   cuuint64_t gdim[3] = {dims[0], dims[1], dims[2]};
   cuuint64_t gstr[2] = {pitch * 4, pitch * dims[1] * 4};

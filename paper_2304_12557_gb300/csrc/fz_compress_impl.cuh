@@ -55,12 +55,25 @@ template <bool BATCH>
 __host__ __device__ constexpr int defer_rounds() { return BATCH ? 0 : 1; }
 template <bool BATCH>
 __host__ __device__ constexpr int plane_bufs() { return defer_rounds<BATCH>() == 0 ? 1 : defer_rounds<BATCH>() + 1; }
-// per compute warp: [TMA box 8 KB][plane buffers, 4 KB each]
+// per compute warp: [TMA boxes][plane buffers, 4 KB each].  A single field
+// takes one 8 KB box per tile; a batch has room for the row-class boxes of
+// fields whose rows are not 16-byte aligned (9 KB, see issue_class_boxes).
 template <bool BATCH>
-__host__ __device__ constexpr int box_stride() { return 8192 + plane_bufs<BATCH>() * 4096; }
-constexpr int kPlaneOff = 8192;
+__host__ __device__ constexpr int box_bytes() { return BATCH ? 9216 : 8192; }
+template <bool BATCH>
+__host__ __device__ constexpr int box_stride() { return box_bytes<BATCH>() + plane_bufs<BATCH>() * 4096; }
 constexpr int kHalf2D = 4096;                   // second x half of a 2-D box
 constexpr uint32_t kTileBoxBytes = 32 * 32 * 2 * 4;  // one tile (3-D: 2 planes; 2-D: 2 halves)
+// Row-class boxes: a field's rows (index R = y + Y z) in four classes by
+// R mod 4 start at one 16-byte offset each, so each class is a 2-D tensor of
+// rows 16 * pitch bytes apart whose base is rounded down to 16 bytes; its
+// map's x runs from that base, r_k = the class's offset in floats (0..3),
+// ahead of x = 0.  Per tile: 3-D, for each of the 2 planes and 4 classes, a
+// box of 8 rows of 36 floats (1152 B); 2-D, for each class, 8 rows of 68.
+constexpr int kClassRow3 = 36, kClassRow2 = 68;
+constexpr int kClassBox3 = 8 * kClassRow3 * 4, kClassBox2 = 8 * kClassRow2 * 4;
+static_assert(8 * kClassBox3 <= 9216 && 4 * kClassBox2 <= 9216, "class boxes fit the box area");
+static_assert(kClassBox3 % 128 == 0 && kClassBox2 % 128 == 0, "class boxes 128-byte aligned");
 
 // the rounds a block has in flight, in shared memory behind the warps' areas
 struct RoundSlot {
@@ -95,6 +108,7 @@ struct BatchArgs {
   const CompressArgs *fields;    // per field (device)
   const FieldRt *rt;             // per field, written by the batch's prepare pass
   const CUtensorMap *tmaps;      // per field (TMA launches), 64-byte aligned
+  const CUtensorMap *cmaps;      // per field 4 row-class maps (use_tma 2), 64-byte aligned
   const uint2 *unit_map;         // per unit of the launch: (field, unit within the field)
   uint64_t n_units;
   uint32_t *ticket;              // the launch's unit counter, zero at launch
@@ -341,6 +355,51 @@ struct BoxRows {
     const float4 w = *reinterpret_cast<const float4 *>(box + base + swz(r, c0 + 1));
     f[0] = u.x; f[1] = u.y; f[2] = u.z; f[3] = u.w;
     f[4] = w.x; f[5] = w.y; f[6] = w.z; f[7] = w.w;
+  }
+};
+
+// The same rows from the warp's row-class boxes (issue_class_boxes): brick
+// row (p, iy) lies in class k = (R0 + iy) mod 4 of its plane (R0: the
+// tile's first row index on it), at box row by (3-D) or 2 by + iy / 4 (2-D),
+// shifted by the class's offset r[k]; k and r[k] are the same in every
+// lane, so the shift is a uniform branch over three 16-byte loads.
+template <int NDIM>
+struct ClassBoxRows {
+  const uint8_t *box;
+  int bx, by;
+  uint32_t r0[2];                // R0 mod 4 of the tile's planes (2-D: [0])
+  uint32_t shift;                // r[k] for k = 0..3, two bits each
+  __device__ __forceinline__ void row(int p, int iy, int, float (&f)[8]) const {
+    const uint32_t k = (r0[NDIM == 3 ? p : 0] + (uint32_t)iy) & 3u;
+    const uint32_t sh = (shift >> (2 * k)) & 3u;
+    const uint8_t *rowp;
+    if constexpr (NDIM == 3)
+      rowp = box + (p * 4 + k) * kClassBox3 + by * (kClassRow3 * 4) + bx * 32;
+    else
+      rowp = box + k * kClassBox2 + (2 * by + (iy >> 2)) * (kClassRow2 * 4) + bx * 32;
+    const float4 u = *reinterpret_cast<const float4 *>(rowp);
+    const float4 v = *reinterpret_cast<const float4 *>(rowp + 16);
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (sh != 0) w = *reinterpret_cast<const float4 *>(rowp + 32);   // uniform
+    const float e[12] = {u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w, w.x, w.y, w.z, w.w};
+    switch (sh) {
+      case 0:
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] = e[j];
+        break;
+      case 1:
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] = e[j + 1];
+        break;
+      case 2:
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] = e[j + 2];
+        break;
+      default:
+#pragma unroll
+        for (int j = 0; j < 8; ++j) f[j] = e[j + 3];
+        break;
+    }
   }
 };
 
@@ -772,6 +831,40 @@ __device__ __forceinline__ void issue_box(const CompressArgs &a, const ChunkGrid
   }
 }
 
+// The row-class boxes of tile T (fields whose rows are not 16-byte
+// aligned; the four class maps cm[0..3] are 2-D, x then row-of-class).
+// Every box starts at the tile's x origin (a multiple of 32 floats, so
+// 16-byte aligned in the map) and at the class's first row at or after the
+// tile's first row R0 on the plane; rows past the field read as zero, and
+// rows of the next plane that a tile reaching past y = Y picks up are
+// padding the kernel masks.
+template <int NDIM>
+__device__ __forceinline__ void issue_class_boxes(const CompressArgs &a, const ChunkGrid &cg,
+                                                  const CUtensorMap *cm, uint8_t *box,
+                                                  uint64_t *bar, uint64_t T) {
+  const uint32_t c = (uint32_t)(T >> 2);
+  const int t = (int)(T & 3);
+  const uint32_t r = cg.x.div(c);
+  const uint32_t cx = c - r * cg.x.d, cz = cg.y.div(r), cy = r - cz * cg.y.d;
+  if constexpr (NDIM == 3) {
+    mbar_expect_tx(bar, 8 * kClassBox3);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const uint64_t R0 = (uint64_t)cy * 32 + a.dims[1] * ((uint64_t)cz * 8 + 2 * t + p);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        tma_load_2d(box + (p * 4 + k) * kClassBox3, cm + k, bar, (int)(cx * 32),
+                    (int)((R0 + 3 - k) / 4));
+    }
+  } else {
+    mbar_expect_tx(bar, 4 * kClassBox2);
+    const uint64_t R0 = (uint64_t)cy * 128 + 32 * t;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      tma_load_2d(box + k * kClassBox2, cm + k, bar, (int)(cx * 64), (int)((R0 + 3 - k) / 4));
+  }
+}
+
 // the compacted blocks of a finished tile, stored in a later round
 struct Pending {
   uint32_t T;          // tile index in its field (kNoTile: none; < 2^21)
@@ -935,11 +1028,12 @@ __global__ void __launch_bounds__(kCompThreads, 1)
   const unsigned full = 0xffffffffu;
   const int g = threadIdx.x & 31, wid = threadIdx.x >> 5;
   grid_dependency_wait();                // a preceding range pass's result
-  if constexpr (!BATCH) grid_launch_dependents();   // the call's result copy may be scheduled
+  grid_launch_dependents();              // the launch after this one may be scheduled
   constexpr int kDef = defer_rounds<BATCH>(), kBufs = plane_bufs<BATCH>();
   // per compute warp: [TMA box 8 KB] (TMA only) [plane buffers]; then the
   // block's CompShared; then (batches) one WarpField per compute warp
   constexpr int stride = TMA ? box_stride<BATCH>() : kBufs * 4096;
+  constexpr int kPlaneOff = box_bytes<BATCH>();
   CompShared *sh = reinterpret_cast<CompShared *>(smem + kCompWarps * stride);
   WarpField *wfield = reinterpret_cast<WarpField *>(
       smem + kCompWarps * stride + kCompShBytes + (wid < kCompWarps ? wid : 0) * kWarpFieldBytes);
@@ -1013,8 +1107,14 @@ __global__ void __launch_bounds__(kCompThreads, 1)
     if constexpr (TMA) {
       const FieldRt rt = rt_of(w.field);
       fence_proxy_async_smem();          // earlier generic reads of the box first
-      issue_box<NDIM>(BATCH ? b.fields[w.field] : a0, ChunkGrid(rt.dx, rt.dy),
-                      BATCH ? &b.tmaps[w.field] : &tmap0, box, bar, w.T);
+      bool cls = false;
+      if constexpr (BATCH && NDIM >= 2) cls = b.fields[w.field].use_tma == 2;
+      if (cls)
+        issue_class_boxes<NDIM>(b.fields[w.field], ChunkGrid(rt.dx, rt.dy), &b.cmaps[4 * w.field],
+                                box, bar, w.T);
+      else
+        issue_box<NDIM>(BATCH ? b.fields[w.field] : a0, ChunkGrid(rt.dx, rt.dy),
+                        BATCH ? &b.tmaps[w.field] : &tmap0, box, bar, w.T);
     }
   };
 
@@ -1078,19 +1178,37 @@ __global__ void __launch_bounds__(kCompThreads, 1)
         escape = true;
       } else {
       float hf[32];
-      // a batch's TMA fields have 16-byte aligned rows: vector halo loads
-      if (BATCH && V < 4 && tma_of(cw)) load_halo<NDIM, 4>(a, q, hf);
+      // a batch's one-box TMA fields have 16-byte aligned rows: vector halo
+      // loads (the row-class fields' rows are not aligned)
+      const int tmode = BATCH ? (tma_of(cw) ? a.use_tma : 0) : (TMA ? 1 : 0);
+      if (BATCH && V < 4 && tmode == 1) load_halo<NDIM, 4>(a, q, hf);
       else load_halo<NDIM, V, WHOLE>(a, q, hf);
       float2 vf[32];                                // fp32 residuals, codes 2i, 2i+1 in vf[i]
       uint32_t qmax = 0;
       // a single field's launch compiles one load path; a batch picks per field
-      const bool use_box = BATCH ? tma_of(cw) : TMA;
-      if (use_box) {
+      if (tmode != 0) {
         if (!mbar_wait_bounded(bar, phase, a0.wait_limit_ns) && g == 0)
           atomicOr(&cur->err, kErrTimeout);
         phase ^= 1u;
-        residuals_first_f<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, rt.p.ebx2_r, hf, vf,
-                                       qmax);
+        bool done = false;
+        if constexpr (BATCH && NDIM >= 2) {
+          if (tmode == 2) {
+            // row classes: each class's offset from 16 bytes, and the class
+            // of the tile's first row on each plane
+            ClassBoxRows<NDIM> cr{box, q.bx, q.by, {0u, 0u}, 0u};
+            const uint64_t xw = reinterpret_cast<uintptr_t>(a.x) >> 2;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              cr.shift |= (uint32_t)((xw + k * a.pitch) & 3u) << (2 * k);
+            cr.r0[0] = (uint32_t)((q.y0 + (NDIM == 3 ? a.dims[1] * q.z0 : 0)) & 3u);
+            cr.r0[1] = (uint32_t)((q.y0 + a.dims[1] * (q.z0 + 1)) & 3u);
+            residuals_first_f<NDIM, CHECK>(cr, q, rt.p.ebx2_r, hf, vf, qmax);
+            done = true;
+          }
+        }
+        if (!done)
+          residuals_first_f<NDIM, CHECK>(BoxRows<NDIM>{box, q.bx, q.by}, q, rt.p.ebx2_r, hf, vf,
+                                         qmax);
         __syncwarp();                    // every lane is done with the box
       } else {
         residuals_first_f<NDIM, CHECK>(GlobalRows<NDIM, V>{a, q}, q, rt.p.ebx2_r, hf, vf, qmax);

@@ -32,7 +32,8 @@ struct CompressArgs {
   const RangeResult *range;    // relative mode: min/max/non-finite of a range pass
   int range_given;             // relative mode: use [range_lo, range_hi] instead
   float range_lo, range_hi;
-  int use_tma;                 // batches: this field's tiles come by TMA
+  int use_tma;                 // batches: 0 direct loads, 1 one TMA box per tile (rows
+                               // 16-byte aligned), 2 row-class boxes (rows not aligned)
   int ndim;                    // batches: the field's dimensionality
   int whole;                   // whole-field Lorenzo (stream version 2): residuals
                                // across chunk faces
@@ -96,6 +97,11 @@ void launch_range(const float *x, uint64_t n, float2 *partial, int nblocks,
 bool compress_uses_tma(int ndim, const CompressArgs &a);
 bool encode_field_tmap(int ndim, const uint64_t dims[3], const float *x, CUtensorMap *tm);
 // the same for rows `pitch` elements apart (pitch * 4 a multiple of 16)
+// The four row-class maps of a 2-D/3-D field whose rows need not be 16-byte
+// aligned (rows R = y + Y z by R mod 4; see issue_class_boxes): false when
+// the field has fewer than four rows or a map does not encode.
+bool encode_class_tmaps(int ndim, const uint64_t dims[3], uint64_t pitch, const float *x,
+                        CUtensorMap tm[4]);
 bool encode_field_tmap_pitch(int ndim, const uint64_t dims[3], uint64_t pitch, const float *x,
                              CUtensorMap *tm);
 // Tiles per look-back unit of a single-field compression (the compression

@@ -156,6 +156,47 @@ def test_batch_relative_only(codec, torch):
         b.close()
 
 
+def test_batch_row_class_boxes_edges(codec, torch):
+    """Row-class TMA boxes (load path tma 2) on the shapes where the classes
+    shift: every row width mod 4, field starts 4, 8 and 12 bytes past a
+    16-byte boundary, planes whose row count is not a multiple of 4 (the
+    class of a plane's first row moves from plane to plane), tiles reaching
+    past y, z and x, a 2-D field of exactly 4 rows and one of 3 (which keeps
+    direct loads), and escapes."""
+    rng = np.random.default_rng(61)
+    shapes = [((13, 5, 37), 3, 1), ((9, 7, 66), 3, 2), ((21, 33, 99), 3, 3), ((4, 301), 2, 1),
+              ((3, 150), 2, 2), ((129, 67), 2, 3), ((17, 40, 70), 3, 0), ((2, 45, 41), 3, 1)]
+    xs, outs, spec, want = [], [], [], []
+    for i, (shape, ndim, lead) in enumerate(shapes):
+        x = fields.grf(shape, -2.5, 62 + i).astype(np.float32)
+        mode, eb = ("abs", 1e-2) if i % 2 else ("rel", 1e-3)
+        if i == 2:
+            x.reshape(-1)[rng.integers(0, x.size, 300)] = 3e4
+        buf = torch.zeros(x.size + 4, dtype=torch.float32, device="cuda")
+        xt = buf[lead: lead + x.size].view(*shape)
+        xt.copy_(torch.from_numpy(x))
+        out = torch.zeros(fz.compress_bound(list(shape[::-1])[:ndim], ndim), dtype=torch.uint8,
+                          device="cuda")
+        xs.append((buf, xt))
+        outs.append(out)
+        spec.append((xt, out, mode, eb, ndim))
+        st, o = oracle.compress(x, ndim, oracle.EB_ABS if mode == "abs" else oracle.EB_REL, eb)
+        assert st == oracle.OK
+        want.append(o)
+    b = fz.Batch(codec, spec)
+    try:
+        for tma in (2, 1, 2):
+            b.set_load_path(tma, False)
+            for o in outs:
+                o.zero_()
+            sizes, sts = b.compress()
+            for i in range(len(spec)):
+                assert sts[i] == fz.OK, (tma, i, sts[i])
+                assert outs[i][: sizes[i]].cpu().numpy().tobytes() == want[i], (tma, i)
+    finally:
+        b.close()
+
+
 def test_batch_autotune_keeps_streams(codec, torch):
     specs = _specs()[:14]
     xs, outs, b = _make_batch(codec, torch, specs)
@@ -204,8 +245,9 @@ def test_batch_rejects_bad_fields(codec, torch):
 
 
 def test_batch_every_load_path(codec, torch):
-    """The three load paths give the same streams: direct loads, TMA for the
-    aligned fields only, TMA for all through row-aligned staging copies.
+    """The four load paths give the same streams: direct loads, TMA for the
+    aligned fields only, TMA for all through row-aligned staging copies, TMA
+    for all with row-class boxes for the unaligned fields.
     The fields cover every row misalignment (dims[0] % 4 = 1, 2, 3), a field
     that starts off a 16-byte boundary, absolute and relative bounds, escapes
     in a staged field, and ragged edges."""
@@ -241,10 +283,10 @@ def test_batch_every_load_path(codec, torch):
         want.append(o)
     b = fz.Batch(codec, spec)
     try:
-        for tma, staged in [(True, True), (False, False), (True, False), (True, True)]:
+        for tma, staged in [(1, True), (0, False), (2, False), (1, False), (1, True), (2, False)]:
             b.set_load_path(tma, staged)
             t = b.tuning()
-            assert t["tma"] == tma and t["staged"] == (tma and staged)
+            assert t["tma"] == tma and t["staged"] == (tma == 1 and staged)
             for o in outs:
                 o.zero_()
             sizes, sts = b.compress()
@@ -254,6 +296,7 @@ def test_batch_every_load_path(codec, torch):
         assert fz.inspect(outs[3][:64].cpu().numpy().tobytes())["n_outliers"] >= 200
         t = b.autotune(reps=2)
         assert t["ms_direct"] > 0 and t["ms_tma"] > 0 and t["ms_tma_staged"] > 0
+        assert t["ms_tma_classes"] > 0
         sizes, sts = b.compress()
         for i in range(len(specs)):
             assert outs[i][: sizes[i]].cpu().numpy().tobytes() == want[i], i
