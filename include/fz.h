@@ -314,8 +314,9 @@ typedef struct fz_batch fz_batch;
 /* Plan a batch of n fields on ctx's device: validates every field (FZ_ERR_ARG;
  * FZ_ERR_CAPACITY when an output cannot hold the header and flags) and
  * allocates the batch's descriptors and scratch (FZ_ERR_CUDA).  Fields
- * whose rows are 16-byte aligned take TMA tile loads, the others direct
- * loads (load path [1] of fz_batch_autotune).  The batch keeps ctx for later
+ * whose rows are 16-byte aligned take TMA tile loads, the other 2-D/3-D
+ * fields of four rows or more row-class TMA boxes, the rest direct loads
+ * (load path [3] of fz_batch_autotune).  The batch keeps ctx for later
  * calls; destroy the batch before the context. */
 int fz_batch_create(fz_ctx *ctx, const fz_field *fields, int n, fz_batch **batch);
 
@@ -334,13 +335,13 @@ int fz_batch_set_graph(fz_batch *batch, int on);
 /* Autotune the batch's load path over four choices, `reps` timed runs
  * each: [0] direct loads for every field; [1] TMA tile loads for the
  * fields whose rows allow them (2-D/3-D, rows 16-byte aligned), direct
- * loads for the others (the default); [2] TMA tile loads for every 2-D/3-D
+ * loads for the others; [2] TMA tile loads for every 2-D/3-D
  * field, the others through staging copies with the row pitch padded to 4
  * elements, written by each run's first pass (about 4 bytes of device
  * memory per element of those fields); [3] TMA for every 2-D/3-D field of
  * four rows or more, the unaligned ones by four row-class boxes per tile
  * (rows grouped by index mod 4 share a 16-byte offset and form a tensor of
- * their own), read in place.  Keeps the fastest.
+ * their own), read in place (the default).  Keeps the fastest.
  * The outputs are overwritten by the trial runs.  fz_batch_tuning reports
  * the choice (tma 0/1/2, staged) and the median run times in ms of the four
  * paths (0 before tuning). */

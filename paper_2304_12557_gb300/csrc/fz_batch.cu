@@ -698,7 +698,7 @@ int fz_batch_create(fz_ctx *ctx, const fz_field *fields, int n, fz_batch **out) 
   if (!B) return FZ_ERR_CUDA;
   B->ctx = ctx;
   B->device = device;
-  B->ws.set_load_path(1, false, nullptr);           // flags only: no fields yet
+  B->ws.set_load_path(2, false, nullptr);           // flags only: no fields yet
   int st = B->ws.set(device, fields, n, nullptr);
   if (st == FZ_OK && cudaStreamSynchronize(nullptr) != cudaSuccess) st = FZ_ERR_CUDA;
   if (st != FZ_OK) {

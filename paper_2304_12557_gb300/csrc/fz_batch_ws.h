@@ -84,7 +84,7 @@ class BatchWs {
 
   int device_ = 0;
   int num_sms_ = 1;
-  int tma_mode_ = 1;
+  int tma_mode_ = 2;
   bool stage_on_ = false;
   // per field: its offset (floats) in the staging memory, or ~0 when its
   // rows are read in place; the first pass's segments (host copy)
