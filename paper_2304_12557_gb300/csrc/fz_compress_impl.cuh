@@ -38,30 +38,35 @@ namespace fz {
 // loaded one round ahead) or, for fields whose rows are not 16-byte aligned
 // and for 1-D fields, straight from global memory.
 
-constexpr int kCompWarps = 14;                  // compute warps per block
+constexpr int kCompWarps = 15;                  // compute warps per block
 static_assert(kCompWarps == kCompressUnitTiles, "a look-back unit is one tile per compute warp");
 constexpr int kCompThreads = 32 * (kCompWarps + 1);   // + the scan warp
 constexpr int kRing = 4;                        // rounds in flight per block
 // A warp stores a tile's compacted blocks after computing later tiles, so
-// that the scan warp has time to resolve the tile's prefix; the tile's bit
-// planes wait in one of plane_bufs() plane buffers.  Each buffer is drained
-// (the tile that last used it stored) right before the next tile's planes
-// are written into it: with defer_rounds() = 1 (two buffers) a tile of
-// round r is stored in round r + 2, before that round's planes, so its
-// prefix has one and a half rounds to arrive; with no deferral (one buffer)
-// about half a round.  A batch keeps each warp's field arguments in shared
-// memory as well and has room for one buffer only.
+// that the scan warp has time to resolve the tile's prefix.  The blocks wait
+// in the warp's ring: a shared-memory area of ring_blocks() 16-byte blocks
+// whose two ends take the tiles of even and odd rounds.  A tile of round r
+// is stored in round r + 2, right before round r + 2 uses that end, so its
+// prefix has one and a half rounds to arrive.  Each round first transposes
+// its codes into bit planes in a 256-block staging area at its own end of
+// the ring (the planes are read back into registers before the compacted
+// blocks are written over them), so the tile of round r + 1 waiting at the
+// other end must leave 256 blocks free; a tile of more blocks than that is
+// stored one round early.
 template <bool BATCH>
-__host__ __device__ constexpr int defer_rounds() { return BATCH ? 0 : 1; }
-template <bool BATCH>
-__host__ __device__ constexpr int plane_bufs() { return defer_rounds<BATCH>() == 0 ? 1 : defer_rounds<BATCH>() + 1; }
-// per compute warp: [TMA boxes][plane buffers, 4 KB each].  A single field
-// takes one 8 KB box per tile; a batch has room for the row-class boxes of
-// fields whose rows are not 16-byte aligned (9 KB, see issue_class_boxes).
+__host__ __device__ constexpr int ring_blocks() { return BATCH ? 360 : 440; }
+constexpr int kStageBlocks = 256;               // one tile's bit planes (4 KB)
+static_assert(ring_blocks<true>() % 8 == 0 && ring_blocks<false>() % 8 == 0,
+              "ring rows of 8 blocks (128 bytes)");
+static_assert(ring_blocks<true>() >= kStageBlocks + 64, "a batch ring defers small tiles");
+// per compute warp: a TMA box (TMA launches).  A single field takes one 8 KB
+// box per tile; a batch has room for the row-class boxes of fields whose
+// rows are not 16-byte aligned (9 KB, see issue_class_boxes).  The boxes
+// come first (1024-byte aligned for the 128-byte swizzle), then the rings.
 template <bool BATCH>
 __host__ __device__ constexpr int box_bytes() { return BATCH ? 9216 : 8192; }
 template <bool BATCH>
-__host__ __device__ constexpr int box_stride() { return box_bytes<BATCH>() + plane_bufs<BATCH>() * 4096; }
+__host__ __device__ constexpr int ring_bytes() { return 16 * ring_blocks<BATCH>(); }
 constexpr int kHalf2D = 4096;                   // second x half of a 2-D box
 constexpr uint32_t kTileBoxBytes = 32 * 32 * 2 * 4;  // one tile (3-D: 2 planes; 2-D: 2 halves)
 // Row-class boxes: a field's rows (index R = y + Y z) in four classes by
@@ -124,10 +129,15 @@ struct __align__(16) WarpField {
 constexpr int kWarpFieldBytes = (int)((sizeof(WarpField) + 15) / 16 * 16);
 
 constexpr int kCompShBytes = (int)((sizeof(CompShared) + 15) / 16 * 16);
-constexpr int kCompSmemTma = kCompWarps * box_stride<false>() + kCompShBytes + 1024;
-constexpr int kCompSmemLdg = kCompWarps * plane_bufs<false>() * 4096 + kCompShBytes + 1024;
+// [boxes (TMA)][rings][CompShared][WarpField per compute warp (batches)]
+template <bool TMA, bool BATCH>
+__host__ __device__ constexpr int comp_area_bytes() {
+  return kCompWarps * ((TMA ? box_bytes<BATCH>() : 0) + ring_bytes<BATCH>());
+}
+constexpr int kCompSmemTma = comp_area_bytes<true, false>() + kCompShBytes + 1024;
+constexpr int kCompSmemLdg = comp_area_bytes<false, false>() + kCompShBytes + 1024;
 constexpr int kCompSmemBatch =
-    kCompWarps * box_stride<true>() + kCompShBytes + kCompWarps * kWarpFieldBytes + 1024;
+    comp_area_bytes<true, true>() + kCompShBytes + kCompWarps * kWarpFieldBytes + 1024;
 static_assert(kCompSmemTma <= 227 * 1024 && kCompSmemBatch <= 227 * 1024,
               "shared memory per block");
 static_assert(sizeof(CompressArgs) % 8 == 0 && sizeof(FieldRt) % 8 == 0, "copied as u64 words");
@@ -870,16 +880,26 @@ struct Pending {
   uint32_t T;          // tile index in its field (kNoTile: none; < 2^21)
   uint32_t field;      // its field (batches)
   uint64_t agg;        // (blocks << 32) | outliers
-  uint32_t F, P;       // lane b: flag byte and exclusive block rank of plane b
-  uint32_t round;      // the block round it belongs to (its plane buffer: round % 3)
+  uint32_t round;      // the block round it belongs to (its ring end: round & 1)
 };
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
+// a ring block's place: the 16-byte column within its 128-byte row XORed
+// with the row, so that lanes writing runs of blocks that start 8 apart
+// (dense planes) hit distinct banks
+__device__ __forceinline__ uint32_t ring_slot(uint32_t k) { return k ^ ((k >> 3) & 7u); }
+// the first block of a tile of n blocks at ring end e
+template <bool BATCH>
+__device__ __forceinline__ uint32_t ring_base(uint32_t e, uint32_t n) {
+  return e ? (uint32_t)ring_blocks<BATCH>() - n : 0u;
+}
+
 // Take a finished tile's exclusive prefix from the scan warp and store its
-// compacted blocks (Listing 2's copy: block (b, i) -> payload[PreSum]).
-template <int NDIM>
+// compacted blocks (Listing 2's copy: block (b, i) -> payload[PreSum]); the
+// blocks lie in rank order in the ring, so the copy is contiguous.
+template <int NDIM, bool BATCH>
 __device__ __forceinline__ void finish_tile(const CompressArgs &a, CompShared *sh,
-                                            const Pending &d, const uint32_t *pb,
+                                            const Pending &d, const uint4 *ring,
                                             const FieldRt &rt, int g, int wid) {
   SetScratch *cur = a.set_cur;
   const uint64_t n_tiles = a.n_chunks * kTilesPerChunk;
@@ -917,21 +937,16 @@ __device__ __forceinline__ void finish_tile(const CompressArgs &a, CompShared *s
     }
   }
   const uint32_t tile_nnz = (uint32_t)(d.agg >> 32);
+  const uint32_t base = ring_base<BATCH>(d.round & 1u, tile_nnz);
   uint8_t *const out = a.out;                        // read once: stores follow
-  uint64_t dst = pay + 16 * ((excl >> 32) + d.P);
-  if (pay + 16 * ((excl >> 32) + tile_nnz) <= a.out_capacity) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if ((d.F >> i) & 1u) {
-        const uint4 blk = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
-        __stcs(reinterpret_cast<uint4 *>(out + dst), blk);
-        dst += 16;
-      }
-    }
+  const uint64_t dst = pay + 16 * (excl >> 32);
+  if (dst + 16 * (uint64_t)tile_nnz <= a.out_capacity) {
+    for (uint32_t k = (uint32_t)g; k < tile_nnz; k += 32)
+      __stcs(reinterpret_cast<uint4 *>(out + dst + 16 * (uint64_t)k), ring[ring_slot(base + k)]);
   } else if (g == 0) {
     atomicOr(&cur->err, kErrCapacity);
   }
-  __syncwarp();                                      // plane buffer free again
+  __syncwarp();                                      // ring blocks free again
 }
 
 // The scan warp's ticket for block round r: a unit index from the launch's
@@ -1029,14 +1044,13 @@ __global__ void __launch_bounds__(kCompThreads, 1)
   const int g = threadIdx.x & 31, wid = threadIdx.x >> 5;
   grid_dependency_wait();                // a preceding range pass's result
   grid_launch_dependents();              // the launch after this one may be scheduled
-  constexpr int kDef = defer_rounds<BATCH>(), kBufs = plane_bufs<BATCH>();
-  // per compute warp: [TMA box 8 KB] (TMA only) [plane buffers]; then the
-  // block's CompShared; then (batches) one WarpField per compute warp
-  constexpr int stride = TMA ? box_stride<BATCH>() : kBufs * 4096;
-  constexpr int kPlaneOff = box_bytes<BATCH>();
-  CompShared *sh = reinterpret_cast<CompShared *>(smem + kCompWarps * stride);
+  // [TMA boxes] [rings] [CompShared] [WarpField per compute warp (batches)]
+  constexpr int kBox = TMA ? box_bytes<BATCH>() : 0;
+  constexpr int kRingOff = kCompWarps * kBox;
+  CompShared *sh = reinterpret_cast<CompShared *>(smem + comp_area_bytes<TMA, BATCH>());
   WarpField *wfield = reinterpret_cast<WarpField *>(
-      smem + kCompWarps * stride + kCompShBytes + (wid < kCompWarps ? wid : 0) * kWarpFieldBytes);
+      smem + comp_area_bytes<TMA, BATCH>() + kCompShBytes +
+      (wid < kCompWarps ? wid : 0) * kWarpFieldBytes);
 
   uint64_t n_units;
   FieldRt rt0{};
@@ -1070,8 +1084,8 @@ __global__ void __launch_bounds__(kCompThreads, 1)
   }
 
   // ---- compute warp
-  uint8_t *box = smem + wid * stride;
-  uint32_t *const pb0 = reinterpret_cast<uint32_t *>(box + (TMA ? kPlaneOff : 0));
+  uint8_t *box = smem + wid * kBox;
+  uint4 *const ring = reinterpret_cast<uint4 *>(smem + kRingOff + wid * ring_bytes<BATCH>());
   uint64_t *bar = &sh->box_bar[wid];
   // a unit's tile for this warp, and whether this warp computes it (the
   // unit exists, the tile lies in the field and the field can be quantised)
@@ -1126,10 +1140,12 @@ __global__ void __launch_bounds__(kCompThreads, 1)
     if (g == 0 && tma_of(cw)) issue(cw);
     __syncwarp();
   }
-  Pending prev1{kNoTile, 0, 0, 0, 0, 0};            // last round's tile
-  Pending prev2{kNoTile, 0, 0, 0, 0, 0};            // the round before's
-  // a pending tile's plane buffer: rounds cycle through the three
-  auto pb_of = [&](const Pending &d) { return pb0 + 1024 * (d.round % kBufs); };
+  Pending prev1{kNoTile, 0, 0, 0};                  // last round's tile (the other end)
+  Pending prev2{kNoTile, 0, 0, 0};                  // the round before's (this round's end)
+  auto finish = [&](Pending &d) {
+    finish_tile<NDIM, BATCH>(BATCH ? b.fields[d.field] : a0, sh, d, ring, rt_of(d.field), g, wid);
+    d.T = kNoTile;
+  };
   uint32_t cached = ~0u;                             // the field in wfield (batches)
   for (uint32_t r = 0; cw.u < n_units; ++r) {
     const int s = (int)(r % kRing);
@@ -1144,8 +1160,7 @@ __global__ void __launch_bounds__(kCompThreads, 1)
         atomicOr(&a0.set_cur->err, kErrTimeout);
     };
     uint64_t agg = 0;
-    uint32_t F = 0, P = 0;
-    uint32_t *pb = pb0 + 1024 * (r % kBufs);
+    const uint32_t e = r & 1u;                       // this round's end of the ring
     if (cw.run) {
       if constexpr (BATCH) {
         if (cw.field != cached) {                    // this warp's field changed
@@ -1228,24 +1243,26 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       narrow = !__any_sync(full, (o & ~0x4B00007Fu) != 0u);
       escape = __any_sync(full, (o & ~0x4B007FFFu) != 0u);
       }
-      // drain this round's plane buffer before anything below writes it
-      Pending &drain = kDef == 0 ? prev1 : prev2;
-      if (drain.T != kNoTile) {
-        const CompressArgs &a1 = BATCH ? b.fields[drain.field] : a0;
-        finish_tile<NDIM>(a1, sh, drain, pb_of(drain), rt_of(drain.field), g, wid);
-        drain.T = kNoTile;
-      }
+      // this end of the ring: store the tile of two rounds back that waits
+      // there, and make the last round's tile at the other end leave the
+      // staging area free
+      if (prev2.T != kNoTile) finish(prev2);
+      if (prev1.T != kNoTile &&
+          (uint32_t)(prev1.agg >> 32) > (uint32_t)(ring_blocks<BATCH>() - kStageBlocks))
+        finish(prev1);
+      uint32_t *const pb =
+          reinterpret_cast<uint32_t *>(ring + (e ? ring_blocks<BATCH>() - kStageBlocks : 0));
       uint32_t nout_lane = 0;
       if (!narrow && escape) {
         // rare: some |residual| needs more than 15 bits; recompute and repack
-        // with escapes out of line (through this round's plane buffer)
+        // with escapes out of line (through the staging area)
         nout_lane = escape_repack<NDIM, V, WHOLE, WIDE>(a, T, g, rt.p.ebx2_r, pb);
 #pragma unroll
         for (int i = 0; i < 32; ++i) w[i] = pb[32 * g + i];
         __syncwarp();
       }
 
-      // plane buffer: lane b collects plane b's 32 words (8 blocks); a
+      // staging area: lane b collects plane b's 32 words (8 blocks); a
       // narrow tile writes its 16 nonzero planes only
       if (narrow) {
         uint32_t u[16];
@@ -1262,15 +1279,17 @@ __global__ void __launch_bounds__(kCompThreads, 1)
         for (int b2 = 0; b2 < 32; ++b2) pb[32 * b2 + 4 * ((g >> 2) ^ (b2 & 7)) + (g & 3)] = w[b2];
       }
       __syncwarp();
+      uint4 blk[8];
+      uint32_t F = 0;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {                  // lane b: flag byte of plane b
-        const uint4 blk = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
-        F |= ((blk.x | blk.y | blk.z | blk.w) != 0u ? 1u : 0u) << i;
+      for (int i = 0; i < 8; ++i) {                  // lane b: plane b, its flag byte
+        blk[i] = *reinterpret_cast<const uint4 *>(pb + 32 * g + 4 * (i ^ (g & 7)));
+        F |= ((blk[i].x | blk[i].y | blk[i].z | blk[i].w) != 0u ? 1u : 0u) << i;
       }
       if (narrow && (g & 15) >= 7 && (g & 15) != 15) F = 0;   // rows not written
 
       const uint32_t pc = __popc(F);
-      P = pc;
+      uint32_t P = pc;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(full, P, o);
@@ -1281,32 +1300,36 @@ __global__ void __launch_bounds__(kCompThreads, 1)
       const uint32_t tile_nout = __reduce_add_sync(full, nout_lane);
       a.out[64 + T * 32 + g] = (uint8_t)F;           // Listing 1's flags
       agg = ((uint64_t)tile_nnz << 32) | tile_nout;
+      if (g == 0) {
+        sh->slot[s].agg[wid] = agg;
+        mbar_arrive(&sh->agg_bar[s]);
+      }
+      // the compacted blocks in rank order over the staging area, once
+      // every lane has read its plane
+      __syncwarp();
+      uint32_t k = ring_base<BATCH>(e, tile_nnz) + P;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if ((F >> i) & 1u) ring[ring_slot(k++)] = blk[i];
+      }
+      __syncwarp();
     } else {
       next_unit();                                   // no tile here this round
       if (g == 0 && tma_of(nw)) issue(nw);
+      if (g == 0) {
+        sh->slot[s].agg[wid] = 0;
+        mbar_arrive(&sh->agg_bar[s]);
+      }
     }
-    if (g == 0) {
-      sh->slot[s].agg[wid] = agg;
-      mbar_arrive(&sh->agg_bar[s]);
-    }
-    // a round without a tile drained nothing: store the tile that would
-    // have been drained now, so that at most kDef tiles stay pending
-    Pending &old = kDef == 0 ? prev1 : prev2;
-    if (old.T != kNoTile) {
-      const CompressArgs &a = BATCH ? b.fields[old.field] : a0;
-      finish_tile<NDIM>(a, sh, old, pb_of(old), rt_of(old.field), g, wid);
-      old.T = kNoTile;
-    }
-    if constexpr (kDef == 1) prev2 = prev1;
-    prev1 = Pending{cw.run ? (uint32_t)T : kNoTile, BATCH ? cw.field : 0u, agg, F, P, r};
+    // a round without a tile stored nothing: store the tile at this end now,
+    // so that at most two tiles stay pending
+    if (prev2.T != kNoTile) finish(prev2);
+    prev2 = prev1;
+    prev1 = Pending{cw.run ? (uint32_t)T : kNoTile, BATCH ? cw.field : 0u, agg, r};
     cw = nw;
   }
-  if (prev2.T != kNoTile)
-    finish_tile<NDIM>(BATCH ? b.fields[prev2.field] : a0, sh, prev2, pb_of(prev2),
-                      rt_of(prev2.field), g, wid);
-  if (prev1.T != kNoTile)
-    finish_tile<NDIM>(BATCH ? b.fields[prev1.field] : a0, sh, prev1, pb_of(prev1),
-                      rt_of(prev1.field), g, wid);
+  if (prev2.T != kNoTile) finish(prev2);
+  if (prev1.T != kNoTile) finish(prev1);
 }
 
 // ====================================================================

@@ -106,7 +106,7 @@ bool encode_field_tmap_pitch(int ndim, const uint64_t dims[3], uint64_t pitch, c
                              CUtensorMap *tm);
 // Tiles per look-back unit of a single-field compression (the compression
 // kernel's compute warps per block; fz_compress_impl.cuh checks the two agree).
-constexpr uint64_t kCompressUnitTiles = 14;
+constexpr uint64_t kCompressUnitTiles = 15;
 // look-back status words (one per unit of consecutive tiles) a compression
 // of n_tiles tiles uses and clears in the other set
 constexpr uint64_t compress_status_words(uint64_t n_tiles) {

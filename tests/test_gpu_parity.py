@@ -287,7 +287,7 @@ def test_corrupt_streams(codec, torch):
 def test_bounded_wait_times_out_and_recovers(codec, torch):
     """A unit that never publishes its look-back aggregate: the successors'
     bounded waits give up and the call reports FZ_ERR_TIMEOUT; the context
-    and the GPU stay usable.  The compressor's units are 14 tiles, the
+    and the GPU stay usable.  The compressor's units are 15 tiles, the
     decompressor's offsets pass takes 512 chunks per unit, so the second
     field spans two of those."""
     x = fields.grf((32, 128, 128), -3.0, 6).astype(np.float32)
