@@ -166,6 +166,35 @@ def particles1d(n: int = 1 << 24, seed: int = 5, zero_frac: float = 1e-4) -> np.
     return v
 
 
+def dense_sparse(ndim: int, seed: int) -> np.ndarray:
+    """A smooth field (sums of sines) with uniform noise of amplitude 200 in
+    one band of every four: 3-D (80, 512, 512), the noise on planes z with
+    (z // 2) % 4 == 0; 2-D (4096, 4800), on rows y with (y // 32) % 4 == 0.
+    At an absolute bound of 0.05 the noisy bands make nearly all bit-plane
+    blocks of their tiles nonzero and the smooth bands few, so dense and
+    sparse tiles alternate through a field of about 10,000 tiles, float32."""
+    rng = np.random.default_rng(seed)
+    if ndim == 3:
+        shape = (80, 512, 512)
+        z = np.arange(shape[0], dtype=np.float32)[:, None, None]
+        y = np.arange(shape[1], dtype=np.float32)[None, :, None]
+        x = np.arange(shape[2], dtype=np.float32)[None, None, :]
+        base = np.sin(0.011 * x) + np.cos(0.017 * y) + 0.5 * np.sin(0.023 * z)
+        noisy = (np.arange(shape[0]) // 2) % 4 == 0
+        out = np.broadcast_to(base, shape).astype(np.float32)
+        for k in np.flatnonzero(noisy):
+            out[k] += rng.uniform(-200.0, 200.0, shape[1:]).astype(np.float32)
+    else:
+        shape = (4096, 4800)
+        y = np.arange(shape[0], dtype=np.float32)[:, None]
+        x = np.arange(shape[1], dtype=np.float32)[None, :]
+        out = (np.sin(0.011 * x) + np.cos(0.017 * y)).astype(np.float32)
+        noisy = (np.arange(shape[0]) // 32) % 4 == 0
+        rows = np.flatnonzero(noisy)
+        out[rows] += rng.uniform(-200.0, 200.0, (rows.size, shape[1])).astype(np.float32)
+    return out
+
+
 def small_cases():
     """Small ragged shapes (numpy order) spanning several tiles/chunks."""
     return [

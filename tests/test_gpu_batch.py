@@ -122,6 +122,26 @@ def test_batch_equals_single_field_streams(codec, torch):
         b.close()
 
 
+def test_batch_dense_tiles_stored_a_round_early(codec, torch):
+    """A batch warp's ring has 360 blocks, so a waiting tile of more than
+    104 blocks is stored a round early, before the next tile is staged.
+    Large fields whose dense and sparse tiles alternate (both launches,
+    several rounds per warp) beside small fields of the usual mix: every
+    stream equals the oracle's."""
+    specs = [(fields.dense_sparse(3, 98), 3, "abs", 0.05),
+             (fields.dense_sparse(2, 99), 2, "abs", 0.05)] + _specs()[:6]
+    xs, outs, b = _make_batch(codec, torch, specs)
+    try:
+        sizes, sts = b.compress()
+        for i, (x, ndim, mode, eb) in enumerate(specs):
+            assert sts[i] == fz.OK, (i, sts[i])
+            st, o = oracle.compress(x, ndim, oracle.EB_ABS if mode == "abs" else oracle.EB_REL,
+                                    eb)
+            assert st == oracle.OK and outs[i][: sizes[i]].cpu().numpy().tobytes() == o, i
+    finally:
+        b.close()
+
+
 def test_batch_escapes_in_consecutive_rounds(codec, torch):
     """Fields with escapes in nearly every tile and several rounds of work
     per block: a warp repacks an escaped tile while its previous tile's

@@ -284,6 +284,28 @@ def test_corrupt_streams(codec, torch):
         assert oracle.decompress(bytes(bad))[0] == oracle.ERR_CORRUPT
 
 
+def _tile_blocks(stream, n_elems):
+    """compacted 16-byte blocks per tile: the set bits of its 32 flag bytes"""
+    b = np.frombuffer(stream, np.uint8)
+    nt = (n_elems + 2047) // 2048
+    return np.unpackbits(b[64:64 + 32 * nt].reshape(nt, 32), axis=1).sum(1)
+
+
+@pytest.mark.parametrize("ndim", [3, 2])
+def test_dense_tiles_stored_a_round_early(codec, torch, ndim):
+    """A compute warp keeps each tile's compacted blocks in its ring until
+    the tile's prefix arrives two rounds later, and stages the next tile's
+    bit planes in 256 blocks at the other end; a waiting tile of more than
+    184 blocks (of the ring's 440) is therefore stored a round early.  Fields
+    of about 10,000 tiles (several rounds per warp on the whole GPU) with
+    dense and sparse tiles alternating: byte parity with the oracle, and the
+    oracle's own stream shows both kinds in numbers."""
+    x = fields.dense_sparse(ndim, 96 + ndim)
+    g, _ = check_parity(codec, torch, x, ndim, fz.EB_ABS, 0.05)
+    nnz = _tile_blocks(g, x.size)
+    assert (nnz > 184).sum() >= 2000 and (nnz <= 104).sum() >= 2000
+
+
 def test_bounded_wait_times_out_and_recovers(codec, torch):
     """A unit that never publishes its look-back aggregate: the successors'
     bounded waits give up and the call reports FZ_ERR_TIMEOUT; the context
